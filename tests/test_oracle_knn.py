@@ -1,0 +1,64 @@
+"""Pins of the oracle's kNN (reading R1: exact float32 key, ties to the
+lower index, self included) against a scalar brute force and invariances."""
+import numpy as np
+import pytest
+
+import oracle as O
+
+
+def scalar_knn(P, k):
+    """Brute force, one scalar at a time: every operation rounded to float32,
+    then the first k of the (key, index) order."""
+    P = np.asarray(P, dtype=np.float32)
+    out = []
+    for q in range(len(P)):
+        keys = []
+        for j in range(len(P)):
+            dx = np.float32(P[q, 0]) - np.float32(P[j, 0])
+            dy = np.float32(P[q, 1]) - np.float32(P[j, 1])
+            dz = np.float32(P[q, 2]) - np.float32(P[j, 2])
+            key = np.float32(np.float32(np.float32(dx * dx) + np.float32(dy * dy)) + np.float32(dz * dz))
+            keys.append((float(key), j))
+        keys.sort()
+        out.append([j for _, j in keys[:k]])
+    return np.array(out, dtype=np.int32)
+
+
+def test_knn_matches_scalar_bruteforce_random():
+    rng = np.random.default_rng(7)
+    P = rng.normal(size=(70, 3)).astype(np.float32)
+    np.testing.assert_array_equal(O.knn(P, 16), scalar_knn(P, 16))
+
+
+def test_knn_ties_go_to_lower_index():
+    # integer grid: many exactly equal keys; duplicates too
+    g = np.array([[x, y, z] for x in range(4) for y in range(3) for z in range(3)], dtype=np.float32)
+    P = np.concatenate([g, g[:5]])          # rows 36..40 duplicate rows 0..4
+    ref = scalar_knn(P, 9)
+    got = O.knn(P, 9)
+    np.testing.assert_array_equal(got, ref)
+    # a duplicate's first neighbour is the lower-index copy (key 0, lower index)
+    assert got[36, 0] == 0 and got[36, 1] == 36
+    # among the 6 face neighbours of an interior grid point at key 1 the order is by index
+    q = 1 * 9 + 1 * 3 + 1   # (1, 1, 1)
+    ones = [j for j in got[q] if j != q and j < 36]
+    assert ones[:6] == sorted(ones[:6])
+
+
+def test_knn_self_first_for_distinct_points():
+    rng = np.random.default_rng(3)
+    P = rng.uniform(-1, 1, size=(200, 3)).astype(np.float32)
+    nb = O.knn(P, 16)
+    np.testing.assert_array_equal(nb[:, 0], np.arange(200))
+
+
+def test_knn_invariant_under_exact_shift():
+    rng = np.random.default_rng(11)
+    P = rng.integers(-8, 8, size=(150, 3)).astype(np.float32)
+    Q = P + np.float32(64.0)        # exact: small integers + 2^6
+    np.testing.assert_array_equal(O.knn(P, 16), O.knn(Q, 16))
+
+
+def test_knn_rejects_k_above_n():
+    with pytest.raises(ValueError):
+        O.knn(np.zeros((3, 3), np.float32), 4)
