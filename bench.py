@@ -1,0 +1,366 @@
+#!/usr/bin/env python3
+"""Benchmark of the registration hot path on GB300.
+
+One step = one whole registration of the benchmark workload through the C
+ABI: pack + validate both clouds, the kNN/curvature descriptor pass, the
+iterations (all-pairs force, combine, float64 pose update) and the moved
+template.  Default workload: 1,000,000 template x 1,000,000 reference points
+(8-ellipsoid surface with a 15% box-shaped outlier cluster), p = 2,
+g = aX aY s, k = 16, 50 iterations: 5e13 pair interactions per step.
+
+Prints one JSON line.  `value` is pair-interactions/s over the device-timed
+steps (inputs resident in HBM); `e2e` repeats the steps through the host
+entry points with pinned host buffers (host->device copies and the moved
+cloud's device->host copy inside the timed region).  `roofline` reports the
+force kernel against the FP32 issue peak (2 x 128 lanes x SMs x max clock);
+`cpu_baseline` times the FP64 oracle on a bounded sample on the host cores.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+FLOPS_PER_PAIR = 22          # counting convention of the per-pair work
+FP32_LANES_PER_SM = 128
+L2_FLUSH_BYTES = 256 << 20   # > 129 MB L2
+
+WORKLOADS = {
+    "large": dict(desc="1,000,000 template x 1,000,000 reference points, 8-ellipsoid surface, 15% box outlier "
+                       "cluster, rotation 60 deg, scale 1.1, p=2, g=aX*aY*s, k=16, 50 iterations",
+                  n=1_000_000, iters=50),
+    "scale": dict(desc="35,000 reference x 30,800 template points (5-ellipsoid surface, 20% slab removed, "
+                       "10% uniform outliers), p=2, k=16, 200 iterations", n=35_000, iters=200),
+    "tiny": dict(desc="1,000 x 1,000 points (3-ellipsoid surface, 50 deg about x), p=2, k=16, 100 iterations",
+                 n=1000, iters=100),
+}
+
+
+def make_pair(name):
+    from paper_1902_01061_gb300 import synth
+    if name == "large":
+        return synth.large_case()
+    if name == "scale":
+        return synth.scale_case()
+    return synth.tiny()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int | None):
+        self.proc = None
+        self.lines = []
+        self.gpu_index = gpu_index
+
+    def start(self):
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+        if self.gpu_index is not None:
+            cmd += ["-i", str(self.gpu_index)]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def gpu_index_for(local_rank: int):
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if vis:
+        items = [v.strip() for v in vis.split(",") if v.strip()]
+        if local_rank < len(items) and items[local_rank].isdigit():
+            return int(items[local_rank])
+        return None
+    return local_rank
+
+
+def profile_traffic():
+    """Per-launch DRAM bytes of the force kernel from the committed ncu summary,
+    or None when the kernel source changed since the counters were taken."""
+    path = os.path.join(ROOT, "profiles", "force_tile_kernel_large.md")
+    src = os.path.join(ROOT, "paper_1902_01061_gb300", "csrc", "force.cu")
+    if not (os.path.exists(path) and os.path.exists(src)):
+        return None, None
+    digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    traffic, tag = None, None
+    for line in open(path):
+        if line.startswith("traffic_bytes_per_launch_full_size:"):
+            traffic = float(line.split(":", 1)[1].split()[0])
+        if line.startswith("force_cu_sha256_16:"):
+            tag = line.split(":", 1)[1].strip()
+    return (traffic if tag == digest else None), digest
+
+
+def cpu_baseline(pair, p, g_mode, seconds=15.0):
+    """The FP64 oracle as it stands, on the host, for a bounded sample: the
+    iteration-0 force pass (Eq. 5) for a few template rows against every
+    reference point.  Curvatures are seeded synthetic values (timing only)."""
+    import numpy as np
+    import oracle as O
+    rng = np.random.default_rng(1234)
+    n, m = len(pair.X), len(pair.Y0)
+    aX = np.clip(rng.gamma(1.2, 0.015, size=n), 0, 0.33)
+    aY = np.clip(rng.gamma(1.2, 0.015, size=m), 0, 0.33)
+    sigma = O.sigma_auto(aX)
+    Y = pair.Y0.astype(np.float64)
+    probe = np.arange(4)
+    t0 = time.perf_counter()
+    O.forces_rows(Y, pair.X, aY, aX, sigma, p, g_mode, probe)
+    per_row = (time.perf_counter() - t0) / len(probe)
+    nrows = int(max(4, min(m, seconds / max(per_row, 1e-9))))
+    rows = np.sort(rng.choice(m, size=nrows, replace=False))
+    t0 = time.perf_counter()
+    O.forces_rows(Y, pair.X, aY, aX, sigma, p, g_mode, rows)
+    dt = time.perf_counter() - t0
+    return {"value": nrows * n / dt, "unit": "pair-interactions/s", "cores": 1, "kind": "oracle",
+            "sample": f"iteration-0 force pass (Eq. 5) of {nrows} template rows x {n} reference points "
+                      f"in float64 numpy, single thread, {dt:.1f} s"}
+
+
+def run_reference(args, ws, rank):
+    """The oracle arm: bounded samples of the same workload on the host cores."""
+    if rank != 0:
+        return 0
+    import numpy as np
+    import oracle as O
+    wl = WORKLOADS[args.workload]
+    pair = make_pair(args.workload)
+    n, m = len(pair.X), len(pair.Y0)
+    rng = np.random.default_rng(77)
+    aX = np.clip(rng.gamma(1.2, 0.015, size=n), 0, 0.33)
+    aY = np.clip(rng.gamma(1.2, 0.015, size=m), 0, 0.33)
+    sigma = O.sigma_auto(aX)
+    Y = pair.Y0.astype(np.float64)
+    rows_per_step = max(1, min(m, int(args.ref_rows)))
+    def step():
+        rows = np.sort(rng.choice(m, size=rows_per_step, replace=False))
+        O.forces_rows(Y, pair.X, aY, aX, sigma, 2.0, 1, rows)
+    for _ in range(args.warmup):
+        step()
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        step()
+        times.append(time.perf_counter() - t0)
+    mean = sum(times) / len(times)
+    value = rows_per_step * n / mean
+    line = {
+        "impl": "reference", "metric": "pair-interactions/s", "value": value, "unit": "pair-interactions/s",
+        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": mean * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": wl["desc"], "N": n, "M": m},
+        "cpu_baseline": {"value": value, "unit": "pair-interactions/s", "cores": 1, "kind": "oracle",
+                         "sample": f"each step: iteration-0 force pass of {rows_per_step} random template rows "
+                                   f"x {n} reference points, float64 numpy, single thread"},
+        "e2e": {"value": value, "unit": "pair-interactions/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=list(WORKLOADS), default="large")
+    ap.add_argument("--e2e-steps", type=int, default=None)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ref-rows", type=int, default=48)
+    args = ap.parse_args()
+    ws, rank, local = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, ws, rank)
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    from paper_1902_01061_gb300 import scgr
+
+    if not torch.cuda.is_available():
+        raise RuntimeError("bench.py needs a CUDA GPU")
+    torch.cuda.set_device(local)
+    if ws > 1:
+        dist.init_process_group("nccl")
+    scgr.load()                      # fails loudly if the CUDA library is missing
+    wl = WORKLOADS[args.workload]
+    pair = make_pair(args.workload)
+    n, m, iters = len(pair.X), len(pair.Y0), wl["iters"]
+    pairs_per_step = n * m * iters
+    dev = torch.device("cuda", local)
+    Xd = torch.from_numpy(pair.X).to(dev)
+    Yd = torch.from_numpy(pair.Y0).to(dev)
+    moved = torch.empty((m, 3), dtype=torch.float32, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    params = scgr.scgr_default_params(p=2.0, g_mode=1, k=16)
+    stream = torch.cuda.current_stream()
+    ctx = scgr.scgr_create(params, stream)
+    num_sms = torch.cuda.get_device_properties(dev).multi_processor_count
+
+    def step_device():
+        scgr.scgr_set_reference(ctx, Xd)
+        scgr.scgr_set_template(ctx, Yd)
+        scgr.scgr_compute_descriptors(ctx)
+        scgr.scgr_run(ctx, iters)
+        scgr.scgr_get_moved(ctx, moved)
+
+    for _ in range(args.warmup):
+        step_device()
+        scgr.scgr_get_result(ctx)
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(gpu_index_for(local))
+    scgr.scgr_set_force_timing(ctx, True)
+    launches0 = scgr.scgr_launch_count(ctx)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    wall0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.zero_()                # evict L2 between steps (outside the events)
+        ev[k][0].record(stream)
+        step_device()
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    clk = clocks.stop()
+    if ws > 1:
+        dist.barrier()
+    res = scgr.scgr_get_result(ctx)
+    launches = scgr.scgr_launch_count(ctx) - launches0
+    nforce, force_ms = scgr.scgr_get_force_timing(ctx)
+    scgr.scgr_set_force_timing(ctx, False)
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    ms_per_step = sum(step_ms) / len(step_ms)
+    if ws > 1:
+        t = torch.tensor([ms_per_step], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_per_step = float(t.item())
+    value = ws * pairs_per_step / (ms_per_step * 1e-3)
+    force_avg_ms = force_ms / max(nforce, 1)
+
+    # end to end through the host entry points (pinned host buffers)
+    e2e_steps = args.e2e_steps if args.e2e_steps is not None else args.steps
+    e2e = None
+    if e2e_steps > 0:
+        Xh = torch.from_numpy(pair.X).pin_memory().numpy()
+        Yh = torch.from_numpy(pair.Y0).pin_memory().numpy()
+        Mh = torch.empty((m, 3), dtype=torch.float32).pin_memory().numpy()
+        times = []
+        for _ in range(e2e_steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            scgr.scgr_set_reference_host(ctx, Xh)
+            scgr.scgr_set_template_host(ctx, Yh)
+            scgr.scgr_compute_descriptors(ctx)
+            scgr.scgr_run(ctx, iters)
+            scgr.scgr_get_moved_host(ctx, Mh)
+            scgr.scgr_get_result(ctx)
+            times.append(time.perf_counter() - t0)
+        e2e_s = sum(times) / len(times)
+        if ws > 1:
+            t = torch.tensor([e2e_s], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        e2e = {"value": ws * pairs_per_step / e2e_s, "unit": "pair-interactions/s",
+               "h2d_bytes_per_step": (n + m) * 12, "d2h_bytes_per_step": m * 12 + 8 * 13 + 8}
+    scgr.scgr_destroy(ctx)
+
+    if rank != 0:
+        if ws > 1:
+            dist.destroy_process_group()
+        return 0
+
+    sm_max_mhz = (clk or {}).get("sm_max_mhz") or 2070.0
+    sm_mhz = (clk or {}).get("sm_mhz")
+    peak_tflops = 2 * FP32_LANES_PER_SM * num_sms * sm_max_mhz * 1e6 / 1e12
+    achieved_tflops = FLOPS_PER_PAIR * n * m / (force_avg_ms * 1e-3) / 1e12
+    traffic, digest = profile_traffic()
+    roofline = {"bound": "alu", "achieved": achieved_tflops, "peak": peak_tflops, "unit": "TFLOP/s",
+                "frac": achieved_tflops / peak_tflops, "traffic": traffic,
+                "kernel": "force_tile_kernel", "flops_per_pair": FLOPS_PER_PAIR,
+                "force_launch_ms": force_avg_ms, "force_launches_timed": nforce,
+                "peak_basis": f"2 x {FP32_LANES_PER_SM} FP32 lanes x {num_sms} SMs x {sm_max_mhz:.0f} MHz (max clock)"}
+    if sm_mhz:
+        roofline["frac_at_measured_clock"] = achieved_tflops / (peak_tflops * sm_mhz / sm_max_mhz)
+    line = {
+        "metric": "pair-interactions/s at 1Mx1M" if args.workload == "large" else "pair-interactions/s",
+        "value": value, "unit": "pair-interactions/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "ms_per_iteration": ms_per_step / iters,
+        "pct_fp32_peak": 100.0 * roofline["frac"],
+        "config": {"workload": wl["desc"], "N": n, "M": m, "iterations": iters, "p": 2.0, "g_mode": 1,
+                   "k": 16, "pairs_per_step": pairs_per_step, "l2": "flushed between steps (256 MB write)",
+                   "parallelism": f"replicas x{ws}"},
+        "gpu_launches": launches,
+        "wall_s_timed_region": wall,
+        "pose": {"s": res.s, "iterations": res.iterations},
+        "clocks": clk,
+        "roofline": roofline,
+        "e2e": e2e,
+    }
+    if ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(pair, 2.0, 1)
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

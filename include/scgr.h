@@ -1,0 +1,199 @@
+/*
+ * scgr.h - C ABI of the GB300 shape-constrained gravitational registration
+ * library (method of Agarwal & Bhowmick, "3D Point Cloud Registration with
+ * Shape Constraint", arXiv 1902.01061).
+ *
+ * The library registers a rigid template cloud Y (M points) to a reference
+ * cloud X (N points) by translation, rotation and scale (Sec. I, problem
+ * statement), without colour, correspondences or topology.  Every reference
+ * point pulls every template point with a force weighted by the similarity of
+ * their local curvature descriptors (Eq. 2-5, Eq. 10, Eq. 11); the per-point
+ * forces give a displacement (Eq. 5.5), a Kabsch rotation (Eq. 6) and an
+ * eigenvalue-ratio scale (Sec. III-B, Eq. 8), applied by Eq. 9 each
+ * iteration with the gravitational-constant schedule of Eq. 12.
+ *
+ * Conventions (all calls):
+ *  - Points are float32, row-major [n][3] (x, y, z), row-vector convention:
+ *    the moved template is s * Y0 @ R + t (Eq. 9), R row-major 3x3 doubles.
+ *  - "_dev" pointers are CUDA device pointers on the context's device;
+ *    "_host" pointers are host memory (pageable or pinned).  The caller owns
+ *    every pointer it passes.  Inputs are copied into context-owned device
+ *    buffers before the call returns (stream-ordered on the context stream);
+ *    outputs are caller-allocated.  The context owns all workspace and frees
+ *    it in scgr_destroy.
+ *  - Every call returns a status; nothing throws or aborts across the ABI.
+ *    Kernels report through a device error word that is read at the next
+ *    synchronising call (scgr_get_result, scgr_get_state, scgr_sync); its
+ *    message is available from scgr_last_error until the next call on the
+ *    same context.
+ *  - Calls are enqueued on the stream given to scgr_create (NULL: the legacy
+ *    default stream) and return without synchronising unless stated.
+ *  - One context per host thread at a time; distinct contexts are independent.
+ */
+#ifndef SCGR_H
+#define SCGR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define SCGR_EXPORT __attribute__((visibility("default")))
+#else
+#define SCGR_EXPORT
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct scgr_ctx scgr_ctx; /* opaque; owns all device workspace */
+
+typedef enum {
+  SCGR_OK = 0,
+  SCGR_ERR_INVALID_ARG = 1, /* null pointer, bad size (n < k, m < 3), bad parameter */
+  SCGR_ERR_STATE = 2,       /* call out of order (e.g. run before descriptors) */
+  SCGR_ERR_NONFINITE = 3,   /* an input coordinate is NaN/Inf or |x| > 1e18 */
+  SCGR_ERR_OOM = 4,         /* device allocation failed */
+  SCGR_ERR_CUDA = 5,        /* a CUDA runtime call or a launch failed */
+  SCGR_ERR_TIMEOUT = 6,     /* a bounded device-side wait gave up */
+  SCGR_ERR_NUMERIC = 7      /* the step became non-finite (e.g. zero total weight) */
+} scgr_status;
+
+/* Method parameters (Sec. III, Sec. IV). */
+typedef struct {
+  int k;           /* neighbours per curvature descriptor, self included (>= 3; default 16) */
+  double p;        /* distance exponent of h(d) = d^p, Eq. 11, p >= 1 (default 1) */
+  double sigma;    /* RBF spread of Eq. 3; <= 0: population std of the reference curvatures */
+  int g_mode;      /* 0: g = s (equal weight, Sec. IV); 1: g = aX aY s (Eq. 10, default) */
+  double G1;       /* Eq. 12 (default 10000) */
+  int E;           /* Eq. 12 horizon; <= 0: the iteration count of the first scgr_run */
+  int step_mode;   /* 0: normalized step kappa = eta0 (G/G1) M / W (default); 1: literal Eq. 5.5,
+                      kappa = G time^2 */
+  double eta0;     /* normalized step fraction, 0 < eta0 (default 0.5) */
+  double time;     /* literal-mode time step of Eq. 5.5 (default 1) */
+  int scale_mode;  /* 0: c = sqrt(eX/eY) (default); 1: c = eX/eY as printed; 2: c = 1 (rigid) */
+  int use_graph;   /* 1: scgr_run captures its iteration loop in a CUDA graph and replays it */
+} scgr_params;
+
+/* Result of a registration (Eq. 6, Eq. 8, Eq. 9): moved = s * Y0 @ R + t. */
+typedef struct {
+  double R[9];          /* row-major, row-vector convention */
+  double t[3];
+  double s;
+  int iterations;       /* iterations run so far on this context */
+  int degenerate_steps; /* iterations whose cross-covariance had rank < 2 (rotation kept) */
+} scgr_result;
+
+/* Checkpoint of the iteration state (pose, position in the Eq. 12 schedule,
+ * and sigma).  scgr_set_state + scgr_run continues bit-identically. */
+typedef struct {
+  double R[9];
+  double t[3];
+  double s;
+  int iteration; /* next iteration index t of Eq. 12 */
+  int E;         /* Eq. 12 horizon in use (0: not fixed yet) */
+  int degenerate_steps;
+  double sigma;  /* RBF spread in use (read-only on set: must match the context's) */
+} scgr_state;
+
+/* Fill *out with the defaults listed above.  Returns INVALID_ARG on NULL. */
+SCGR_EXPORT scgr_status scgr_default_params(scgr_params* out);
+
+/* Create a context bound to the current CUDA device and `cuda_stream`
+ * (a cudaStream_t; NULL for the default stream).  *out is set to NULL on
+ * failure.  Parameters are validated here (k >= 3, p >= 1, eta0 > 0, ...). */
+SCGR_EXPORT scgr_status scgr_create(const scgr_params* params, void* cuda_stream, scgr_ctx** out);
+
+/* Release every device buffer of the context.  NULL is ignored. */
+SCGR_EXPORT void scgr_destroy(scgr_ctx* ctx);
+
+/* Text of the last error on this context ("" if none).  Valid until the next
+ * call on the same context.  NULL ctx: the last scgr_create failure. */
+SCGR_EXPORT const char* scgr_last_error(const scgr_ctx* ctx);
+
+/* Reference cloud X (Sec. II: absolute coordinates r^{Xj}), n >= k points.
+ * Copied and validated on device; a non-finite coordinate is reported as
+ * SCGR_ERR_NONFINITE at the next synchronising call.  Resets descriptors. */
+SCGR_EXPORT scgr_status scgr_set_reference(scgr_ctx* ctx, const float* xyz_dev, int64_t n);
+SCGR_EXPORT scgr_status scgr_set_reference_host(scgr_ctx* ctx, const float* xyz_host, int64_t n);
+
+/* Template cloud Y0, m >= max(k, 3) points.  Same rules as the reference.
+ * Resets descriptors and the pose to identity. */
+SCGR_EXPORT scgr_status scgr_set_template(scgr_ctx* ctx, const float* xyz_dev, int64_t m);
+SCGR_EXPORT scgr_status scgr_set_template_host(scgr_ctx* ctx, const float* xyz_host, int64_t m);
+
+/* One-time descriptor pass (Sec. III-A, Sec. IV): k-nearest neighbours of
+ * every point of X and of Y0 (exact float32 key (dx*dx+dy*dy)+dz*dz, no fused
+ * multiply-add, self included, ties to the lower index), the curvature
+ * a = lambda_min / (lambda_1+lambda_2+lambda_3) of each neighbourhood's
+ * covariance (float64), sigma, and the cloud statistics used by the scale
+ * model (means, covariances, largest eigenvalues).  Resets the pose to
+ * identity and the iteration counter to 0.  STATE if a cloud is missing. */
+SCGR_EXPORT scgr_status scgr_compute_descriptors(scgr_ctx* ctx);
+
+/* Enqueue `iterations` iterations (Eq. 5 - Eq. 12) on the context stream.
+ * Resumable: consecutive calls continue the schedule.  The pose stays on the
+ * device; no host synchronisation happens inside the loop.  STATE before
+ * descriptors; INVALID_ARG for iterations < 0. */
+SCGR_EXPORT scgr_status scgr_run(scgr_ctx* ctx, int iterations);
+
+/* Synchronise the stream, check the device error word and copy the pose. */
+SCGR_EXPORT scgr_status scgr_get_result(scgr_ctx* ctx, scgr_result* host_out);
+
+/* Moved template s * Y0 @ R + t (Eq. 9) as float32 [m][3].  Enqueued. */
+SCGR_EXPORT scgr_status scgr_get_moved(scgr_ctx* ctx, float* xyz_dev_out);
+/* Same into host memory; synchronises. */
+SCGR_EXPORT scgr_status scgr_get_moved_host(scgr_ctx* ctx, float* xyz_host_out);
+
+/* Descriptors of the reference (which = 0) or the template (which = 1):
+ * neighbour indices int32 [n][k] sorted by (key, index) and curvature
+ * float32 [n].  Either output may be NULL.  Enqueued.  STATE before
+ * descriptors. */
+SCGR_EXPORT scgr_status scgr_get_descriptors(scgr_ctx* ctx, int which, int32_t* knn_dev, float* a_dev);
+
+/* sigma in use and the float64 curvature of either cloud (a64_dev may be
+ * NULL; [n] doubles).  Synchronises. */
+SCGR_EXPORT scgr_status scgr_get_sigma(scgr_ctx* ctx, double* sigma_out);
+SCGR_EXPORT scgr_status scgr_get_curvature64(scgr_ctx* ctx, int which, double* a64_dev);
+
+/* Replace the curvature of the reference (which = 0) or the template
+ * (which = 1) by caller-supplied float64 values a64_dev [n] (each in [0, 1];
+ * non-finite values are rejected with SCGR_ERR_NONFINITE at the next
+ * synchronising call).  sigma is recomputed from the reference curvatures
+ * unless params.sigma > 0, the force records are rebuilt, and the pose and
+ * iteration counter are reset to identity / 0.  The neighbour lists are kept.
+ * For descriptors from another source (priors, a coarser neighbourhood) and
+ * for tests whose oracle cannot afford the neighbour search.  STATE before
+ * scgr_compute_descriptors. */
+SCGR_EXPORT scgr_status scgr_set_curvature(scgr_ctx* ctx, int which, const double* a64_dev);
+
+/* Forces at the current pose without updating it: per template point
+ * (fx, fy, fz, W) as float32 [m][4], where f is Eq. 5 without the factor G
+ * (f_i = -sum_j g(s_ij) h(d_ij) n_ij) and W_i = sum_j g(s_ij) d_ij^(p-1).
+ * Enqueued.  STATE before descriptors. */
+SCGR_EXPORT scgr_status scgr_forces(scgr_ctx* ctx, float* f4_dev);
+
+/* Checkpoint / resume of the iteration state.  Both synchronise. */
+SCGR_EXPORT scgr_status scgr_get_state(scgr_ctx* ctx, scgr_state* host_out);
+SCGR_EXPORT scgr_status scgr_set_state(scgr_ctx* ctx, const scgr_state* host_in);
+
+/* Wait for all work on the context stream and check the device error word. */
+SCGR_EXPORT scgr_status scgr_sync(scgr_ctx* ctx);
+
+/* Device timing of the all-pairs force kernel (diagnostic).  While enabled,
+ * every force-kernel launch enqueued outside graph capture is bracketed by
+ * CUDA events on the context stream.  scgr_set_force_timing(ctx, 1) enables
+ * and resets the tally, (ctx, 0) disables it.  scgr_get_force_timing
+ * synchronises and returns the number of timed launches and the sum of their
+ * durations in milliseconds since the last reset. */
+SCGR_EXPORT scgr_status scgr_set_force_timing(scgr_ctx* ctx, int enable);
+SCGR_EXPORT scgr_status scgr_get_force_timing(scgr_ctx* ctx, int64_t* launches, double* total_ms);
+
+/* Number of kernel launches this context has issued so far (diagnostic). */
+SCGR_EXPORT int64_t scgr_launch_count(const scgr_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SCGR_H */

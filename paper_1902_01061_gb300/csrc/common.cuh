@@ -1,0 +1,170 @@
+// Shared device-side declarations of the scgr CUDA library (sm_103a).
+//
+// Data layout in HBM (one context):
+//   X4, Y4      float4 [n] packed input clouds (x, y, z, 0), original frame
+//   knnX, knnY  int32 [n][k] neighbour lists sorted by (key, index)
+//   aX64, aY64  float64 [n] curvature (Sec. III-A), aX32/aY32 float32 copies
+//   Xr          float4 [npad] force-kernel reference record
+//               (x - xbar, y - ybar, z - zbar, |X'|^2), xbar = reference mean
+//   XA          float2 [npad] (a_hat = a * sqrt(log2 e) / sigma, L = log2 a or 0)
+//   Y0r         float4 [mpad] (Y0x, Y0y, Y0z, a_hat) template record
+//   partial     float4 [S][mpad] per-split (sum w, sum w X') of the force kernel
+//   blockpart   float64 [nblocks][13] per-block (F, W, T) of the combine kernel
+//   pose/stats  small float64 structs below
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+
+namespace scgr {
+
+constexpr int ERR_NONFINITE = 1;
+constexpr int ERR_NUMERIC = 2;
+constexpr int ERR_TIMEOUT = 4;
+
+// Iteration state kept on the device so that the whole loop runs without a
+// host round trip (and can be captured in a CUDA graph).
+struct DevPose {
+  double R[9];     // row-major, row-vector convention: Y = s Y0 R + t
+  double t[3];
+  double s;
+  double ybs[3];   // template mean minus reference mean at this pose
+  float A[9];      // float32 map used by the force kernel: Y' = Y0 A + b
+  float b[3];      //   with A = s R and b = t - xbar (frame centred on xbar)
+  int it;          // next iteration index of Eq. 12
+  int E;           // Eq. 12 horizon
+  int degenerate;  // iterations with a rank < 2 cross-covariance
+  int pad;
+};
+
+// Cloud statistics of the scale model (Sec. III-B) and sigma of Eq. 3.
+struct DevStats {
+  double xbar[3];
+  double CX[9];    // scatter sum_j (X_j - xbar)^T (X_j - xbar), unnormalised
+  double eX;       // largest eigenvalue of CX / N
+  double ybar0[3];
+  double S0[9];    // scatter sum_i (Y0_i - ybar0)^T (Y0_i - ybar0), unnormalised
+  double eY0;      // largest eigenvalue of S0 / M
+  double sigma;
+  double asum[2];  // sum of curvatures of X, Y0 (diagnostic)
+};
+
+// Method constants the finalize kernel needs (passed by value).
+struct StepParams {
+  double G1, eta0, time;
+  int step_mode, scale_mode;
+  int M;
+};
+
+// ---- fixed-order float64 reductions ------------------------------------
+constexpr int RED_THREADS = 256;
+constexpr int RED_MAX_BLOCKS = 1024;
+
+inline int red_blocks(int64_t n) {
+  int64_t b = (n + RED_THREADS - 1) / RED_THREADS;
+  if (b < 1) b = 1;
+  if (b > RED_MAX_BLOCKS) b = RED_MAX_BLOCKS;
+  return (int)b;
+}
+
+// Sum v[0..NV) over the block in a fixed tree order; thread 0 gets the result.
+template <int NV>
+__device__ __forceinline__ void block_sum(double (&v)[NV], double (*sh)[RED_THREADS]) {
+  const int t = threadIdx.x;
+#pragma unroll
+  for (int q = 0; q < NV; ++q) sh[q][t] = v[q];
+  __syncthreads();
+  for (int w = RED_THREADS / 2; w > 0; w >>= 1) {
+    if (t < w) {
+#pragma unroll
+      for (int q = 0; q < NV; ++q) sh[q][t] += sh[q][t + w];
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int q = 0; q < NV; ++q) v[q] = sh[q][0];
+}
+
+// Symmetric 3x3 eigenvalues by cyclic Jacobi rotations (float64), ascending.
+__host__ __device__ inline void sym3_eigenvalues(const double* Ain, double* lam) {
+  double a[3][3];
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 3; ++c) a[r][c] = 0.5 * (Ain[r * 3 + c] + Ain[c * 3 + r]);
+  for (int sweep = 0; sweep < 32; ++sweep) {
+    const double off = a[0][1] * a[0][1] + a[0][2] * a[0][2] + a[1][2] * a[1][2];
+    const double dia = a[0][0] * a[0][0] + a[1][1] * a[1][1] + a[2][2] * a[2][2];
+    if (off <= 1e-36 * dia || off == 0.0) break;
+    for (int pq = 0; pq < 3; ++pq) {
+      const int p = pq == 2 ? 1 : 0;
+      const int q = pq == 0 ? 1 : 2;
+      const double apq = a[p][q];
+      if (apq == 0.0) continue;
+      const double theta = (a[q][q] - a[p][p]) / (2.0 * apq);
+      double t;
+      if (fabs(theta) > 1e150) t = 0.5 / theta;
+      else t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+      const double c = 1.0 / sqrt(t * t + 1.0);
+      const double s = t * c;
+      const int r = 3 - p - q;
+      const double arp = a[r][p], arq = a[r][q];
+      a[p][p] -= t * apq;
+      a[q][q] += t * apq;
+      a[p][q] = a[q][p] = 0.0;
+      a[r][p] = a[p][r] = c * arp - s * arq;
+      a[r][q] = a[q][r] = s * arp + c * arq;
+    }
+  }
+  double l0 = a[0][0], l1 = a[1][1], l2 = a[2][2], tmp;
+  if (l0 > l1) { tmp = l0; l0 = l1; l1 = tmp; }
+  if (l1 > l2) { tmp = l1; l1 = l2; l2 = tmp; }
+  if (l0 > l1) { tmp = l0; l0 = l1; l1 = tmp; }
+  lam[0] = l0; lam[1] = l1; lam[2] = l2;
+}
+
+// ---- launchers (defined in the .cu files) --------------------------------
+struct Launch {
+  cudaStream_t stream;
+  int64_t* counter;  // incremented once per kernel launch
+};
+
+cudaError_t launch_pack(Launch L, const float* xyz, int64_t n, float4* out, int* err);
+cudaError_t launch_knn(Launch L, const float4* P, int n, int k, int32_t* out);
+cudaError_t launch_curvature(Launch L, const float4* P, const int32_t* nbr, int n, int k,
+                             double* a64, float* a32);
+// mean + scatter of a cloud: writes mean[3], scatter[9], lmax of scatter/n
+cudaError_t launch_cloud_stats(Launch L, const float4* P, int n, double* part, double* mean,
+                               double* scatter, double* lmax);
+// sigma = population std of a64 (1 if below 1e-12), or `sigma_user` if > 0
+cudaError_t launch_sigma(Launch L, const double* a64, int n, double sigma_user, double* part,
+                         double* sigma_out, double* asum_out);
+cudaError_t launch_check_curvature(Launch L, const double* a64, int n, float* a32, int* err);
+cudaError_t launch_records(Launch L, const float4* X4, const double* aX64, int n, int npad,
+                           const float4* Y4, const double* aY64, int m, int mpad, int g_mode,
+                           const DevStats* stats, float4* Xr, float2* XA, float4* Y0r);
+
+struct ForcePlan {
+  int P;          // template points per thread
+  int tpb;        // threads per block
+  int pmode;      // 1: p == 1, 2: p == 2, 3: p == 3, 0: general p
+  int tile_j;     // reference points per shared-memory tile
+  int splits;     // reference-range splits (grid.y)
+  int tiles_per_split;
+  int iblocks;    // grid.x
+};
+
+ForcePlan plan_force(int64_t m, int64_t npad, double p, int num_sms);
+int64_t force_mpad(int64_t m, const ForcePlan& fp);
+
+cudaError_t launch_force(Launch L, const ForcePlan& fp, const float4* Xr, const float2* XA,
+                         int ntiles, const float4* Y0r, int mpad, const DevPose* pose,
+                         float qexp, float4* partial);
+int combine_blocks(int64_t mpad);
+cudaError_t launch_combine(Launch L, const float4* partial, int S, int mpad, int m,
+                           const float4* Y0r, const double* aY64, int g_mode,
+                           const DevPose* pose, float4* f4out, double* blockpart);
+cudaError_t launch_pose_init(Launch L, DevPose* pose, const DevStats* stats, int E);
+cudaError_t launch_finalize(Launch L, const double* blockpart, int nblocks, DevPose* pose,
+                            const DevStats* stats, StepParams sp, int* err);
+cudaError_t launch_apply(Launch L, const float4* Y4, int m, const DevPose* pose, float* out);
+cudaError_t launch_pose_refresh(Launch L, DevPose* pose, const DevStats* stats);
+
+}  // namespace scgr

@@ -1,0 +1,340 @@
+// One-time descriptor pass (Sec. III-A, Sec. IV): input packing and
+// validation, k-nearest neighbours, curvature, cloud statistics of the scale
+// model (Sec. III-B), sigma of Eq. 3, and the records the force kernel reads.
+#include <cmath>
+#include <climits>
+
+#include "common.cuh"
+
+namespace scgr {
+
+static inline cudaError_t after_launch(Launch L) {
+  if (L.counter) ++*L.counter;
+  return cudaGetLastError();
+}
+
+// ---- pack + validate ----------------------------------------------------
+__global__ void pack_kernel(const float* __restrict__ xyz, int64_t n, float4* __restrict__ out,
+                            int* __restrict__ err) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float x = xyz[3 * i], y = xyz[3 * i + 1], z = xyz[3 * i + 2];
+  // |x| <= 1e18 keeps every squared-distance key finite in float32
+  const bool ok = isfinite(x) && isfinite(y) && isfinite(z) && fabsf(x) <= 1e18f &&
+                  fabsf(y) <= 1e18f && fabsf(z) <= 1e18f;
+  if (!ok) {
+    atomicOr(err, ERR_NONFINITE);
+    x = y = z = 0.f;
+  }
+  out[i] = make_float4(x, y, z, 0.f);
+}
+
+cudaError_t launch_pack(Launch L, const float* xyz, int64_t n, float4* out, int* err) {
+  if (n <= 0) return cudaSuccess;
+  const int tpb = 256;
+  pack_kernel<<<(unsigned)((n + tpb - 1) / tpb), tpb, 0, L.stream>>>(xyz, n, out, err);
+  return after_launch(L);
+}
+
+// ---- brute-force kNN ----------------------------------------------------
+// Each thread owns one query and keeps its KC best (key, index) pairs sorted
+// in registers.  Candidates are scanned in increasing index order, so a
+// candidate whose key equals the current KC-th key never displaces it: ties
+// go to the lower index.  The key is the float32 value
+// (dx*dx + dy*dy) + dz*dz with every operation rounded on its own
+// (__fmul_rn / __fadd_rn forbid contraction into fused multiply-adds).
+constexpr int KNN_TPB = 128;
+constexpr int KNN_TILE = 1024;
+
+template <int KC>
+__global__ void __launch_bounds__(KNN_TPB) knn_brute_kernel(const float4* __restrict__ P, int n,
+                                                            int k, int32_t* __restrict__ out) {
+  __shared__ float4 tile[KNN_TILE];
+  const int qi = blockIdx.x * KNN_TPB + threadIdx.x;
+  const float4 q = P[qi < n ? qi : n - 1];
+  float kd[KC];
+  int ki[KC];
+#pragma unroll
+  for (int m = 0; m < KC; ++m) {
+    kd[m] = INFINITY;
+    ki[m] = INT_MAX;
+  }
+  for (int base = 0; base < n; base += KNN_TILE) {
+    const int cnt = min(KNN_TILE, n - base);
+    __syncthreads();
+    for (int t = threadIdx.x; t < cnt; t += KNN_TPB) tile[t] = P[base + t];
+    __syncthreads();
+#pragma unroll 4
+    for (int jj = 0; jj < cnt; ++jj) {
+      const float4 c = tile[jj];
+      const float dx = __fsub_rn(q.x, c.x);
+      const float dy = __fsub_rn(q.y, c.y);
+      const float dz = __fsub_rn(q.z, c.z);
+      const float key = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+      if (key < kd[KC - 1]) {
+        kd[KC - 1] = key;
+        ki[KC - 1] = base + jj;
+#pragma unroll
+        for (int m = KC - 1; m > 0; --m) {
+          if (kd[m] < kd[m - 1]) {
+            const float tk = kd[m];
+            kd[m] = kd[m - 1];
+            kd[m - 1] = tk;
+            const int ti = ki[m];
+            ki[m] = ki[m - 1];
+            ki[m - 1] = ti;
+          }
+        }
+      }
+    }
+  }
+  if (qi < n) {
+#pragma unroll
+    for (int m = 0; m < KC; ++m)
+      if (m < k) out[(int64_t)qi * k + m] = ki[m];
+  }
+}
+
+cudaError_t launch_knn(Launch L, const float4* P, int n, int k, int32_t* out) {
+  const unsigned grid = (unsigned)((n + KNN_TPB - 1) / KNN_TPB);
+  if (k <= 8) knn_brute_kernel<8><<<grid, KNN_TPB, 0, L.stream>>>(P, n, k, out);
+  else if (k <= 16) knn_brute_kernel<16><<<grid, KNN_TPB, 0, L.stream>>>(P, n, k, out);
+  else knn_brute_kernel<32><<<grid, KNN_TPB, 0, L.stream>>>(P, n, k, out);
+  return after_launch(L);
+}
+
+// ---- curvature ----------------------------------------------------------
+// a = lambda_min / (lambda_1 + lambda_2 + lambda_3) of the 1/k covariance of
+// the k neighbours (float64); lambda_min clamped at 0; 0 for a zero trace.
+__global__ void curvature_kernel(const float4* __restrict__ P, const int32_t* __restrict__ nbr,
+                                 int n, int k, double* __restrict__ a64, float* __restrict__ a32) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int32_t* nb = nbr + (int64_t)i * k;
+  double mx = 0, my = 0, mz = 0;
+  for (int m = 0; m < k; ++m) {
+    const float4 c = P[nb[m]];
+    mx += c.x;
+    my += c.y;
+    mz += c.z;
+  }
+  mx /= k;
+  my /= k;
+  mz /= k;
+  double C[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+  for (int m = 0; m < k; ++m) {
+    const float4 c = P[nb[m]];
+    const double dx = c.x - mx, dy = c.y - my, dz = c.z - mz;
+    C[0] += dx * dx; C[1] += dx * dy; C[2] += dx * dz;
+    C[4] += dy * dy; C[5] += dy * dz; C[8] += dz * dz;
+  }
+  C[0] /= k; C[1] /= k; C[2] /= k; C[4] /= k; C[5] /= k; C[8] /= k;
+  C[3] = C[1]; C[6] = C[2]; C[7] = C[5];
+  double lam[3];
+  sym3_eigenvalues(C, lam);
+  const double tr = C[0] + C[4] + C[8];
+  const double a = tr > 0.0 ? fmax(lam[0], 0.0) / tr : 0.0;
+  a64[i] = a;
+  a32[i] = (float)a;
+}
+
+cudaError_t launch_curvature(Launch L, const float4* P, const int32_t* nbr, int n, int k,
+                             double* a64, float* a32) {
+  const int tpb = 128;
+  curvature_kernel<<<(n + tpb - 1) / tpb, tpb, 0, L.stream>>>(P, nbr, n, k, a64, a32);
+  return after_launch(L);
+}
+
+// ---- fixed-order float64 reductions ------------------------------------
+// Pass 1: per-block sums of an NV-vector per point (fixed grid, fixed order).
+struct SumXYZ {
+  const float4* P;
+  __device__ void operator()(int64_t i, double (&v)[3]) const {
+    const float4 c = P[i];
+    v[0] += c.x; v[1] += c.y; v[2] += c.z;
+  }
+};
+struct ScatterXYZ {
+  const float4* P;
+  const double* mean;
+  __device__ void operator()(int64_t i, double (&v)[6]) const {
+    const float4 c = P[i];
+    const double dx = c.x - mean[0], dy = c.y - mean[1], dz = c.z - mean[2];
+    v[0] += dx * dx; v[1] += dx * dy; v[2] += dx * dz;
+    v[3] += dy * dy; v[4] += dy * dz; v[5] += dz * dz;
+  }
+};
+struct SumA {
+  const double* a;
+  __device__ void operator()(int64_t i, double (&v)[1]) const { v[0] += a[i]; }
+};
+struct VarA {
+  const double* a;
+  const double* mean_sum;  // sum of a; mean = sum / n
+  double inv_n;
+  __device__ void operator()(int64_t i, double (&v)[1]) const {
+    const double d = a[i] - mean_sum[0] * inv_n;
+    v[0] += d * d;
+  }
+};
+
+template <int NV, class Fn>
+__global__ void __launch_bounds__(RED_THREADS) reduce_pass_kernel(int64_t n, Fn fn, double* part) {
+  __shared__ double sh[NV][RED_THREADS];
+  double v[NV];
+#pragma unroll
+  for (int q = 0; q < NV; ++q) v[q] = 0.0;
+  const int64_t stride = (int64_t)gridDim.x * RED_THREADS;
+  for (int64_t i = blockIdx.x * (int64_t)RED_THREADS + threadIdx.x; i < n; i += stride) fn(i, v);
+  block_sum<NV>(v, sh);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int q = 0; q < NV; ++q) part[blockIdx.x * NV + q] = v[q];
+  }
+}
+
+// Pass 2: one block sums the per-block partials in fixed order into out[NV].
+template <int NV>
+__global__ void __launch_bounds__(RED_THREADS) reduce_final_kernel(const double* part, int nb,
+                                                                   double* out) {
+  __shared__ double sh[NV][RED_THREADS];
+  double v[NV];
+#pragma unroll
+  for (int q = 0; q < NV; ++q) v[q] = 0.0;
+  for (int b = threadIdx.x; b < nb; b += RED_THREADS) {
+#pragma unroll
+    for (int q = 0; q < NV; ++q) v[q] += part[b * NV + q];
+  }
+  block_sum<NV>(v, sh);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int q = 0; q < NV; ++q) out[q] = v[q];
+  }
+}
+
+__global__ void mean_from_sum_kernel(double* mean, int64_t n) {
+  if (threadIdx.x == 0) {
+    mean[0] /= (double)n;
+    mean[1] /= (double)n;
+    mean[2] /= (double)n;
+  }
+}
+
+__global__ void scatter_finish_kernel(const double* s6, int64_t n, double* scatter, double* lmax) {
+  if (threadIdx.x != 0) return;
+  double S[9] = {s6[0], s6[1], s6[2], s6[1], s6[3], s6[4], s6[2], s6[4], s6[5]};
+  for (int q = 0; q < 9; ++q) scatter[q] = S[q];
+  double C[9];
+  for (int q = 0; q < 9; ++q) C[q] = S[q] / (double)n;
+  double lam[3];
+  sym3_eigenvalues(C, lam);
+  *lmax = lam[2];
+}
+
+cudaError_t launch_cloud_stats(Launch L, const float4* P, int n, double* part, double* mean,
+                               double* scatter, double* lmax) {
+  const int nb = red_blocks(n);
+  reduce_pass_kernel<3, SumXYZ><<<nb, RED_THREADS, 0, L.stream>>>(n, SumXYZ{P}, part);
+  reduce_final_kernel<3><<<1, RED_THREADS, 0, L.stream>>>(part, nb, mean);
+  mean_from_sum_kernel<<<1, 32, 0, L.stream>>>(mean, n);
+  // the 6 scatter sums go to part + RED_MAX_BLOCKS*6 .. as the final output slot
+  double* s6 = part + (size_t)RED_MAX_BLOCKS * 6;
+  reduce_pass_kernel<6, ScatterXYZ><<<nb, RED_THREADS, 0, L.stream>>>(n, ScatterXYZ{P, mean}, part);
+  reduce_final_kernel<6><<<1, RED_THREADS, 0, L.stream>>>(part, nb, s6);
+  scatter_finish_kernel<<<1, 32, 0, L.stream>>>(s6, n, scatter, lmax);
+  if (L.counter) *L.counter += 6;
+  return cudaGetLastError();
+}
+
+__global__ void sigma_finish_kernel(const double* sums, int64_t n, double sigma_user,
+                                    double* sigma_out, double* asum_out) {
+  if (threadIdx.x != 0) return;
+  if (asum_out) *asum_out = sums[0];
+  if (sigma_user > 0.0) {
+    *sigma_out = sigma_user;
+    return;
+  }
+  const double sd = sqrt(sums[1] / (double)n);
+  *sigma_out = sd >= 1e-12 ? sd : 1.0;
+}
+
+cudaError_t launch_sigma(Launch L, const double* a64, int n, double sigma_user, double* part,
+                         double* sigma_out, double* asum_out) {
+  const int nb = red_blocks(n);
+  double* sums = part + (size_t)RED_MAX_BLOCKS * 6 + 8;  // [0]: sum a, [1]: sum (a - mean)^2
+  reduce_pass_kernel<1, SumA><<<nb, RED_THREADS, 0, L.stream>>>(n, SumA{a64}, part);
+  reduce_final_kernel<1><<<1, RED_THREADS, 0, L.stream>>>(part, nb, sums);
+  reduce_pass_kernel<1, VarA><<<nb, RED_THREADS, 0, L.stream>>>(n, VarA{a64, sums, 1.0 / n}, part);
+  reduce_final_kernel<1><<<1, RED_THREADS, 0, L.stream>>>(part, nb, sums + 1);
+  sigma_finish_kernel<<<1, 32, 0, L.stream>>>(sums, n, sigma_user, sigma_out, asum_out);
+  if (L.counter) *L.counter += 5;
+  return cudaGetLastError();
+}
+
+// ---- caller-supplied curvature --------------------------------------------
+__global__ void check_curvature_kernel(const double* __restrict__ a64, int n, float* __restrict__ a32,
+                                       int* __restrict__ err) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double a = a64[i];
+  if (!(a >= 0.0 && a <= 1.0)) atomicOr(err, ERR_NONFINITE);
+  a32[i] = (float)a;
+}
+
+cudaError_t launch_check_curvature(Launch L, const double* a64, int n, float* a32, int* err) {
+  check_curvature_kernel<<<(n + 255) / 256, 256, 0, L.stream>>>(a64, n, a32, err);
+  return after_launch(L);
+}
+
+// ---- force-kernel records ----------------------------------------------
+// s_ij = exp(-(aX - aY)^2 / sigma^2) = 2^(-(a_hat_X - a_hat_Y)^2) with
+// a_hat = a * sqrt(log2 e) / sigma (Eq. 3).  In the mode g = aX aY s (Eq. 10)
+// the factor aX enters the exponent as L = log2 aX and aY multiplies the
+// per-point sums; in the mode g = s, L = 0 and the aY factor is 1.
+// Reference coordinates are shifted by the reference mean so that
+// |X'|^2 + |Y'|^2 - 2 X'.Y' loses little to cancellation.  Padding records
+// carry L = -inf, so their weight is exactly 0.
+__global__ void records_kernel(const float4* __restrict__ X4, const double* __restrict__ aX64,
+                               int n, int npad, const float4* __restrict__ Y4,
+                               const double* __restrict__ aY64, int m, int mpad, int g_mode,
+                               const DevStats* __restrict__ st, float4* __restrict__ Xr,
+                               float2* __restrict__ XA, float4* __restrict__ Y0r) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const double kscale = sqrt(1.4426950408889634) / st->sigma;  // sqrt(log2 e) / sigma
+  if (i < npad) {
+    if (i < n) {
+      const float4 c = X4[i];
+      const float x = (float)((double)c.x - st->xbar[0]);
+      const float y = (float)((double)c.y - st->xbar[1]);
+      const float z = (float)((double)c.z - st->xbar[2]);
+      const double nn = (double)x * x + (double)y * y + (double)z * z;
+      Xr[i] = make_float4(x, y, z, (float)nn);
+      const double a = aX64[i];
+      const float L = g_mode == 1 ? (a > 0.0 ? (float)log2(a) : -INFINITY) : 0.f;
+      XA[i] = make_float2((float)(a * kscale), L);
+    } else {
+      Xr[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+      XA[i] = make_float2(0.f, -INFINITY);
+    }
+  }
+  if (i < mpad) {
+    if (i < m) {
+      const float4 c = Y4[i];
+      Y0r[i] = make_float4(c.x, c.y, c.z, (float)(aY64[i] * kscale));
+    } else {
+      Y0r[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+  }
+}
+
+cudaError_t launch_records(Launch L, const float4* X4, const double* aX64, int n, int npad,
+                           const float4* Y4, const double* aY64, int m, int mpad, int g_mode,
+                           const DevStats* stats, float4* Xr, float2* XA, float4* Y0r) {
+  const int tpb = 256;
+  const int tot = npad > mpad ? npad : mpad;
+  records_kernel<<<(tot + tpb - 1) / tpb, tpb, 0, L.stream>>>(X4, aX64, n, npad, Y4, aY64, m, mpad,
+                                                              g_mode, stats, Xr, XA, Y0r);
+  return after_launch(L);
+}
+
+}  // namespace scgr

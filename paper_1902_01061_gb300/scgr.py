@@ -1,0 +1,311 @@
+"""Thin ctypes binding of libscgr.so (include/scgr.h).
+
+Argument marshalling only: every step of the method runs in the CUDA
+library.  Functions keep the C names; device arrays are torch CUDA tensors
+(float32 [n, 3] contiguous for clouds), host arrays are numpy arrays.  There
+is no CPU fallback: if the library is not built, the first call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import POINTER, Structure, c_char_p, c_double, c_float, c_int, c_int32, c_int64, c_void_p
+
+import numpy as np
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libscgr.so")
+
+SCGR_OK = 0
+STATUS_NAMES = {
+    0: "SCGR_OK", 1: "SCGR_ERR_INVALID_ARG", 2: "SCGR_ERR_STATE", 3: "SCGR_ERR_NONFINITE",
+    4: "SCGR_ERR_OOM", 5: "SCGR_ERR_CUDA", 6: "SCGR_ERR_TIMEOUT", 7: "SCGR_ERR_NUMERIC",
+}
+
+# every symbol include/scgr.h declares (checked by the CPU test-suite)
+EXPORTED = (
+    "scgr_default_params", "scgr_create", "scgr_destroy", "scgr_last_error",
+    "scgr_set_reference", "scgr_set_reference_host", "scgr_set_template", "scgr_set_template_host",
+    "scgr_compute_descriptors", "scgr_run", "scgr_get_result", "scgr_get_moved",
+    "scgr_get_moved_host", "scgr_get_descriptors", "scgr_get_sigma", "scgr_get_curvature64",
+    "scgr_forces", "scgr_get_state", "scgr_set_state", "scgr_sync", "scgr_launch_count",
+    "scgr_set_curvature", "scgr_set_force_timing", "scgr_get_force_timing",
+)
+
+
+class scgr_params(Structure):
+    _fields_ = [("k", c_int), ("p", c_double), ("sigma", c_double), ("g_mode", c_int),
+                ("G1", c_double), ("E", c_int), ("step_mode", c_int), ("eta0", c_double),
+                ("time", c_double), ("scale_mode", c_int), ("use_graph", c_int)]
+
+
+class scgr_result(Structure):
+    _fields_ = [("R", c_double * 9), ("t", c_double * 3), ("s", c_double),
+                ("iterations", c_int), ("degenerate_steps", c_int)]
+
+    def as_numpy(self):
+        return (np.array(self.R[:]).reshape(3, 3), np.array(self.t[:]), float(self.s))
+
+
+class scgr_state(Structure):
+    _fields_ = [("R", c_double * 9), ("t", c_double * 3), ("s", c_double),
+                ("iteration", c_int), ("E", c_int), ("degenerate_steps", c_int),
+                ("sigma", c_double)]
+
+
+class ScgrError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+_lib = None
+
+
+def load():
+    """Load libscgr.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_1902_01061_gb300.build.build()")
+    L = ctypes.CDLL(LIB_PATH)
+    S = c_int
+    ctx = c_void_p
+    sig = {
+        "scgr_default_params": (S, [POINTER(scgr_params)]),
+        "scgr_create": (S, [POINTER(scgr_params), c_void_p, POINTER(c_void_p)]),
+        "scgr_destroy": (None, [ctx]),
+        "scgr_last_error": (c_char_p, [ctx]),
+        "scgr_set_reference": (S, [ctx, c_void_p, c_int64]),
+        "scgr_set_reference_host": (S, [ctx, c_void_p, c_int64]),
+        "scgr_set_template": (S, [ctx, c_void_p, c_int64]),
+        "scgr_set_template_host": (S, [ctx, c_void_p, c_int64]),
+        "scgr_compute_descriptors": (S, [ctx]),
+        "scgr_run": (S, [ctx, c_int]),
+        "scgr_get_result": (S, [ctx, POINTER(scgr_result)]),
+        "scgr_get_moved": (S, [ctx, c_void_p]),
+        "scgr_get_moved_host": (S, [ctx, c_void_p]),
+        "scgr_get_descriptors": (S, [ctx, c_int, c_void_p, c_void_p]),
+        "scgr_get_sigma": (S, [ctx, POINTER(c_double)]),
+        "scgr_get_curvature64": (S, [ctx, c_int, c_void_p]),
+        "scgr_forces": (S, [ctx, c_void_p]),
+        "scgr_get_state": (S, [ctx, POINTER(scgr_state)]),
+        "scgr_set_state": (S, [ctx, POINTER(scgr_state)]),
+        "scgr_sync": (S, [ctx]),
+        "scgr_launch_count": (c_int64, [ctx]),
+        "scgr_set_curvature": (S, [ctx, c_int, c_void_p]),
+        "scgr_set_force_timing": (S, [ctx, c_int]),
+        "scgr_get_force_timing": (S, [ctx, POINTER(c_int64), POINTER(c_double)]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+def _check(status: int, ctx=None):
+    if status != SCGR_OK:
+        msg = load().scgr_last_error(ctx)
+        raise ScgrError(status, msg.decode() if msg else "")
+
+
+def _dev_ptr(t, dtype_name: str, shape_tail=None) -> int:
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("expected a CUDA tensor")
+    if str(t.dtype) != f"torch.{dtype_name}":
+        raise TypeError(f"expected dtype {dtype_name}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    if shape_tail is not None and tuple(t.shape[1:]) != tuple(shape_tail):
+        raise ValueError(f"expected shape [n, {shape_tail}], got {tuple(t.shape)}")
+    return t.data_ptr()
+
+
+def _host_f32(a) -> np.ndarray:
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    if a.ndim != 2 or a.shape[1] != 3:
+        raise ValueError("expected a [n, 3] array")
+    return a
+
+
+# ---- the C entry points, same names ---------------------------------------
+
+def scgr_default_params(**overrides) -> scgr_params:
+    p = scgr_params()
+    _check(load().scgr_default_params(ctypes.byref(p)))
+    for k, v in overrides.items():
+        if not hasattr(p, k):
+            raise AttributeError(k)
+        setattr(p, k, v)
+    return p
+
+
+def scgr_create(params: scgr_params | None = None, stream=None) -> c_void_p:
+    """stream: a torch.cuda.Stream, a raw cudaStream_t int, or None for the
+    current torch stream."""
+    L = load()
+    if params is None:
+        params = scgr_default_params()
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream().cuda_stream
+    elif hasattr(stream, "cuda_stream"):
+        stream = stream.cuda_stream
+    out = c_void_p()
+    st = L.scgr_create(ctypes.byref(params), c_void_p(stream), ctypes.byref(out))
+    _check(st, None)
+    return out
+
+
+def scgr_destroy(ctx) -> None:
+    load().scgr_destroy(ctx)
+
+
+def scgr_last_error(ctx) -> str:
+    m = load().scgr_last_error(ctx)
+    return m.decode() if m else ""
+
+
+def scgr_set_reference(ctx, xyz) -> None:
+    _check(load().scgr_set_reference(ctx, _dev_ptr(xyz, "float32", (3,)), xyz.shape[0]), ctx)
+
+
+def scgr_set_template(ctx, xyz) -> None:
+    _check(load().scgr_set_template(ctx, _dev_ptr(xyz, "float32", (3,)), xyz.shape[0]), ctx)
+
+
+def scgr_set_reference_host(ctx, xyz) -> None:
+    a = _host_f32(xyz)
+    _check(load().scgr_set_reference_host(ctx, a.ctypes.data, a.shape[0]), ctx)
+
+
+def scgr_set_template_host(ctx, xyz) -> None:
+    a = _host_f32(xyz)
+    _check(load().scgr_set_template_host(ctx, a.ctypes.data, a.shape[0]), ctx)
+
+
+def scgr_compute_descriptors(ctx) -> None:
+    _check(load().scgr_compute_descriptors(ctx), ctx)
+
+
+def scgr_run(ctx, iterations: int) -> None:
+    _check(load().scgr_run(ctx, int(iterations)), ctx)
+
+
+def scgr_get_result(ctx) -> scgr_result:
+    r = scgr_result()
+    _check(load().scgr_get_result(ctx, ctypes.byref(r)), ctx)
+    return r
+
+
+def scgr_get_moved(ctx, out) -> None:
+    _check(load().scgr_get_moved(ctx, _dev_ptr(out, "float32", (3,))), ctx)
+
+
+def scgr_get_moved_host(ctx, out: np.ndarray) -> None:
+    if out.dtype != np.float32 or not out.flags.c_contiguous or out.ndim != 2 or out.shape[1] != 3:
+        raise ValueError("out must be a contiguous float32 [m, 3] array")
+    _check(load().scgr_get_moved_host(ctx, out.ctypes.data), ctx)
+
+
+def scgr_get_descriptors(ctx, which: int, knn_out=None, a_out=None) -> None:
+    kp = _dev_ptr(knn_out, "int32") if knn_out is not None else None
+    ap = _dev_ptr(a_out, "float32") if a_out is not None else None
+    _check(load().scgr_get_descriptors(ctx, which, kp, ap), ctx)
+
+
+def scgr_get_curvature64(ctx, which: int, out) -> None:
+    _check(load().scgr_get_curvature64(ctx, which, _dev_ptr(out, "float64")), ctx)
+
+
+def scgr_get_sigma(ctx) -> float:
+    v = c_double()
+    _check(load().scgr_get_sigma(ctx, ctypes.byref(v)), ctx)
+    return v.value
+
+
+def scgr_set_curvature(ctx, which: int, a64) -> None:
+    _check(load().scgr_set_curvature(ctx, which, _dev_ptr(a64, "float64")), ctx)
+
+
+def scgr_set_force_timing(ctx, enable: bool) -> None:
+    _check(load().scgr_set_force_timing(ctx, 1 if enable else 0), ctx)
+
+
+def scgr_get_force_timing(ctx):
+    n = c_int64()
+    ms = c_double()
+    _check(load().scgr_get_force_timing(ctx, ctypes.byref(n), ctypes.byref(ms)), ctx)
+    return int(n.value), float(ms.value)
+
+
+def scgr_forces(ctx, f4_out) -> None:
+    _check(load().scgr_forces(ctx, _dev_ptr(f4_out, "float32", (4,))), ctx)
+
+
+def scgr_get_state(ctx) -> scgr_state:
+    s = scgr_state()
+    _check(load().scgr_get_state(ctx, ctypes.byref(s)), ctx)
+    return s
+
+
+def scgr_set_state(ctx, state: scgr_state) -> None:
+    _check(load().scgr_set_state(ctx, ctypes.byref(state)), ctx)
+
+
+def scgr_sync(ctx) -> None:
+    _check(load().scgr_sync(ctx), ctx)
+
+
+def scgr_launch_count(ctx) -> int:
+    return int(load().scgr_launch_count(ctx))
+
+
+# ---- convenience wrapper ----------------------------------------------------
+
+class Registration:
+    """Owns one context.  `register(X, Y0, iterations)` runs the whole method
+    on device tensors and returns (R, t, s) as numpy float64."""
+
+    def __init__(self, params: scgr_params | None = None, stream=None, **overrides):
+        if params is None:
+            params = scgr_default_params(**overrides)
+        self.params = params
+        self.ctx = scgr_create(params, stream)
+
+    def close(self):
+        if self.ctx is not None:
+            scgr_destroy(self.ctx)
+            self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_clouds(self, X, Y0):
+        self.m = int(Y0.shape[0])
+        scgr_set_reference(self.ctx, X)
+        scgr_set_template(self.ctx, Y0)
+        scgr_compute_descriptors(self.ctx)
+
+    def register(self, X, Y0, iterations: int):
+        self.set_clouds(X, Y0)
+        scgr_run(self.ctx, iterations)
+        return scgr_get_result(self.ctx).as_numpy()
+
+    def forces(self):
+        import torch
+        f4 = torch.empty((self.m, 4), dtype=torch.float32, device="cuda")
+        scgr_forces(self.ctx, f4)
+        return f4

@@ -1,0 +1,260 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle on the
+same seeded inputs.  kNN indices bit-exact; curvature within 1e-6 relative
+(+1e-12 absolute); forces within 1e-5 relative L2; pose after I iterations
+within 0.5 degrees, 1e-3 of the bounding-box diagonal and 1e-5 relative scale."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_1902_01061_gb300 import scgr, synth
+from tests.gpu_helpers import Gpu, rel_l2, rot_err_deg
+
+pytestmark = pytest.mark.gpu
+
+FORCE_TOL = 1e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib(scgr_lib):
+    return scgr_lib
+
+
+def grid_cloud():
+    g = np.array([[x, y, z] for x in range(10) for y in range(10) for z in range(10)], np.float32) * 0.25
+    return np.concatenate([g, g[:40]])          # exact ties and duplicates
+
+
+def knn_cases():
+    rng = np.random.default_rng(21)
+    tiny = synth.tiny()
+    sc = synth.scale_case()
+    return {
+        "tiny": (tiny.X, tiny.Y0, 16),
+        "ragged2500": (sc.X[synth.subsample(sc.X, 2500, 1)], sc.Y0[synth.subsample(sc.Y0, 2049, 2)], 16),
+        "grid_ties": (grid_cloud(), grid_cloud()[::-1].copy(), 16),
+        "k5": (rng.normal(size=(300, 3)).astype(np.float32), rng.normal(size=(301, 3)).astype(np.float32), 5),
+        "k32": (tiny.X, tiny.Y0, 32),
+        "n_eq_k": (tiny.X[:16], tiny.Y0[:16], 16),
+    }
+
+
+@pytest.mark.parametrize("name", list(knn_cases().keys()))
+def test_knn_bit_exact_and_curvature(name):
+    X, Y0, k = knn_cases()[name]
+    with Gpu(X, Y0, k=k) as g:
+        for which, P in ((0, X), (1, Y0)):
+            ref = O.knn(P, k)
+            got = g.knn(which)
+            np.testing.assert_array_equal(got, ref)
+            a_ref = O.curvature(P, ref)
+            a_got = g.curv64(which)
+            np.testing.assert_allclose(a_got, a_ref, rtol=1e-6, atol=1e-12)
+        aX = O.curvature(X, O.knn(X, k))
+        assert g.sigma() == pytest.approx(O.sigma_auto(aX), rel=1e-9)
+
+
+def force_check(g, X, Y0, aX, aY, sigma, p, g_mode, rows=None):
+    f4 = g.forces()
+    fr, Wr = O.forces_rows(Y0, X, aY, aX, sigma, p, g_mode, rows)
+    sel = slice(None) if rows is None else rows
+    ef = rel_l2(f4[sel, :3], fr)
+    eW = rel_l2(f4[sel, 3], Wr)
+    assert ef <= FORCE_TOL, (ef, eW)
+    assert eW <= FORCE_TOL, (ef, eW)
+    return ef, eW
+
+
+@pytest.mark.parametrize("p,g_mode", [(2.0, 1), (1.0, 1), (3.0, 1), (1.5, 1), (2.0, 0), (1.0, 0)])
+def test_forces_iteration0_tiny(p, g_mode):
+    case = synth.tiny()
+    with Gpu(case.X, case.Y0, p=p, g_mode=g_mode) as g:
+        d = O.descriptors(case.X, case.Y0, O.Params(p=p, g_mode=g_mode))
+        force_check(g, case.X, case.Y0, d["aX"], d["aY"], d["sigma"], p, g_mode)
+
+
+@pytest.mark.parametrize("n,m", [(3000, 2777), (5000, 20), (257, 1500), (16, 16)])
+def test_forces_ragged_sizes(n, m):
+    sc = synth.scale_case()
+    X = sc.X[synth.subsample(sc.X, n, 3)]
+    Y0 = sc.Y0[synth.subsample(sc.Y0, m, 4)]
+    with Gpu(X, Y0, p=2.0) as g:
+        d = O.descriptors(X, Y0, O.Params(p=2.0))
+        force_check(g, X, Y0, d["aX"], d["aY"], d["sigma"], 2.0, 1)
+
+
+def synthetic_curvatures(n, seed):
+    # seeded curvature values shaped like the surface variation of the
+    # synthetic clouds: mostly small, a tail up to ~0.3
+    rng = np.random.default_rng(seed)
+    return np.clip(rng.gamma(1.2, 0.015, size=n), 0.0, 0.33)
+
+
+@pytest.mark.parametrize("n,m,p", [(2000, 80_000, 2.0), (2000, 320_000, 2.0), (1500, 320_000, 1.5)])
+def test_forces_block_shapes_sampled_rows(n, m, p):
+    """Template sizes that select 2 and 4 points per thread; descriptors are
+    supplied (seeded) on both sides, forces checked on sampled rows."""
+    rng = np.random.default_rng(5)
+    big = synth.large_case(n=max(n, m) + 10)
+    X = big.X[:n].copy()
+    Y0 = big.Y0[:m].copy()
+    aX = synthetic_curvatures(n, 1)
+    aY = synthetic_curvatures(m, 2)
+    with Gpu(X, Y0, p=p) as g:
+        g.set_curvature(0, aX)
+        g.set_curvature(1, aY)
+        rows = np.sort(rng.choice(m, size=300, replace=False))
+        force_check(g, X, Y0, aX, aY, O.sigma_auto(aX), p, 1, rows)
+
+
+def test_forces_full_size_sampled_rows():
+    """The benchmark workload (1M x 1M, p = 2, g = aX aY s) in the launch
+    configuration the benchmark uses: kNN checked at sampled queries, forces
+    at sampled template rows (seeded descriptors on both sides)."""
+    case = synth.large_case()
+    rng = np.random.default_rng(9)
+    with Gpu(case.X, case.Y0, p=2.0) as g:
+        # exact kNN at sampled queries of both clouds (brute force in numpy)
+        for which, P in ((0, case.X), (1, case.Y0)):
+            knn = g.knn(which)
+            for q in rng.choice(len(P), size=6, replace=False):
+                dx = P[q, 0] - P[:, 0]
+                dy = P[q, 1] - P[:, 1]
+                dz = P[q, 2] - P[:, 2]
+                key = (dx * dx + dy * dy) + dz * dz
+                order = np.lexsort((np.arange(len(P)), key))[:16]
+                np.testing.assert_array_equal(knn[q], order)
+        aX = synthetic_curvatures(len(case.X), 11)
+        aY = synthetic_curvatures(len(case.Y0), 12)
+        g.set_curvature(0, aX)
+        g.set_curvature(1, aY)
+        rows = np.sort(rng.choice(len(case.Y0), size=48, replace=False))
+        force_check(g, case.X, case.Y0, aX, aY, O.sigma_auto(aX), 2.0, 1, rows)
+
+
+def pose_check(res, ores, diag, rot_tol=0.5, t_tol=1e-3, s_tol=1e-5):
+    R, t, s = res.as_numpy()
+    assert rot_err_deg(R, ores["R"]) <= rot_tol
+    assert np.linalg.norm(t - ores["t"]) <= t_tol * diag
+    assert abs(s - ores["s"]) <= s_tol * abs(ores["s"])
+
+
+@pytest.mark.parametrize("which,p,iters", [("mild", 1.0, 100), ("tiny", 1.0, 100), ("tiny", 2.0, 30)])
+def test_pose_parity_after_iterations(which, p, iters):
+    case = synth.mild() if which == "mild" else synth.tiny()
+    prm = O.Params(p=p)
+    ores = O.register(case.X, case.Y0, prm, iterations=iters)
+    with Gpu(case.X, case.Y0, p=p) as g:
+        res = g.run(iters)
+        assert res.iterations == iters
+        pose_check(res, ores, synth.bbox_diag(case.X))
+        moved = g.moved()
+        np.testing.assert_allclose(moved, ores["Y"], atol=1e-3 * synth.bbox_diag(case.X))
+
+
+def test_pose_parity_scale_case_subsample():
+    sc = synth.scale_case()
+    X = sc.X[synth.subsample(sc.X, 3000, 7)]
+    Y0 = sc.Y0[synth.subsample(sc.Y0, 2640, 8)]
+    ores = O.register(X, Y0, O.Params(), iterations=40)
+    with Gpu(X, Y0) as g:
+        pose_check(g.run(40), ores, synth.bbox_diag(X))
+
+
+def test_literal_step_and_scale_modes():
+    case = synth.mild(n=600)
+    for kw in (dict(step_mode=1, time=1e-3, G1=1.0), dict(scale_mode=1), dict(scale_mode=2), dict(E=7, eta0=0.3)):
+        ores = O.register(case.X, case.Y0, O.Params(**kw), iterations=12)
+        with Gpu(case.X, case.Y0, **kw) as g:
+            pose_check(g.run(12), ores, synth.bbox_diag(case.X))
+
+
+def test_moved_matches_pose():
+    case = synth.mild(n=700)
+    with Gpu(case.X, case.Y0) as g:
+        R, t, s = g.run(10).as_numpy()
+        np.testing.assert_allclose(g.moved(), s * case.Y0.astype(np.float64) @ R + t, rtol=0, atol=1e-6)
+
+
+def test_host_path_equals_device_path():
+    case = synth.mild(n=900)
+    with Gpu(case.X, case.Y0) as g:
+        ref = g.run(15)
+        ref_moved = g.moved()
+    ctx = scgr.scgr_create(scgr.scgr_default_params())
+    try:
+        scgr.scgr_set_reference_host(ctx, case.X)
+        scgr.scgr_set_template_host(ctx, case.Y0)
+        scgr.scgr_compute_descriptors(ctx)
+        scgr.scgr_run(ctx, 15)
+        res = scgr.scgr_get_result(ctx)
+        out = np.empty((len(case.Y0), 3), np.float32)
+        scgr.scgr_get_moved_host(ctx, out)
+    finally:
+        scgr.scgr_destroy(ctx)
+    assert list(res.R) == list(ref.R) and list(res.t) == list(ref.t) and res.s == ref.s
+    np.testing.assert_array_equal(out, ref_moved)
+
+
+def test_checkpoint_resume_and_determinism():
+    case = synth.mild(n=800)
+    with Gpu(case.X, case.Y0, E=20) as g:
+        g.run(8)
+        st = scgr.scgr_get_state(g.ctx)
+        a = g.run(12)
+    with Gpu(case.X, case.Y0, E=20) as g:
+        b = g.run(20)
+    with Gpu(case.X, case.Y0, E=20) as g:
+        scgr.scgr_set_state(g.ctx, st)
+        c = g.run(12)
+    for r in (b, c):
+        assert list(r.R) == list(a.R) and list(r.t) == list(a.t) and r.s == a.s and r.iterations == 20
+
+
+def test_graph_replay_equals_eager():
+    case = synth.mild(n=800)
+    with Gpu(case.X, case.Y0) as g:
+        a = g.run(25)
+        n_eager = scgr.scgr_launch_count(g.ctx)
+    with Gpu(case.X, case.Y0, use_graph=1) as g:
+        b = g.run(25)
+        assert scgr.scgr_launch_count(g.ctx) == n_eager
+    assert list(a.R) == list(b.R) and list(a.t) == list(b.t) and a.s == b.s
+
+
+def test_force_timing_counts_launches():
+    case = synth.mild(n=500)
+    with Gpu(case.X, case.Y0) as g:
+        scgr.scgr_set_force_timing(g.ctx, True)
+        before = scgr.scgr_launch_count(g.ctx)
+        g.run(7)
+        n, ms = scgr.scgr_get_force_timing(g.ctx)
+        assert n == 7 and ms > 0.0
+        assert scgr.scgr_launch_count(g.ctx) - before == 21
+
+
+def test_errors_are_reported_not_raised_on_device():
+    case = synth.mild(n=300)
+    ctx = scgr.scgr_create(scgr.scgr_default_params())
+    try:
+        with pytest.raises(scgr.ScgrError) as e:
+            scgr.scgr_run(ctx, 1)
+        assert e.value.status == 2                      # STATE
+        with pytest.raises(scgr.ScgrError) as e:
+            scgr.scgr_set_reference(ctx, torch.zeros((5, 3), dtype=torch.float32, device="cuda"))
+        assert e.value.status == 1                      # fewer than k points
+        X = case.X.copy()
+        X[17, 1] = np.nan
+        scgr.scgr_set_reference(ctx, torch.from_numpy(X).cuda())
+        with pytest.raises(scgr.ScgrError) as e:
+            scgr.scgr_sync(ctx)
+        assert e.value.status == 3                      # NONFINITE
+        scgr.scgr_set_reference(ctx, torch.from_numpy(case.X).cuda())
+        scgr.scgr_set_template(ctx, torch.from_numpy(case.Y0).cuda())
+        scgr.scgr_compute_descriptors(ctx)
+        scgr.scgr_run(ctx, 3)
+        assert scgr.scgr_get_result(ctx).iterations == 3
+    finally:
+        scgr.scgr_destroy(ctx)
