@@ -189,6 +189,33 @@ SCGR_EXPORT scgr_status scgr_sync(scgr_ctx* ctx);
 SCGR_EXPORT scgr_status scgr_set_force_timing(scgr_ctx* ctx, int enable);
 SCGR_EXPORT scgr_status scgr_get_force_timing(scgr_ctx* ctx, int64_t* launches, double* total_ms);
 
+/* Allocation-free force evaluation.  The paper has no counterpart: this entry
+ * point exists for callers that cannot allocate device memory - hosts whose
+ * device memory is owned by another allocator (a framework's caching pool,
+ * a fixed budget on an embedded robot) and real-time loops that cannot take
+ * cudaMalloc's latency or the device-wide synchronisation a cudaFree can
+ * cause.  It needs no context.
+ *
+ * Computes what scgr_forces computes at the identity pose - per template
+ * point (fx, fy, fz, W) as float32 [m][4] - for the caller's clouds
+ * x_dev [n][3], y_dev [m][3] (float32) and curvatures ax_dev [n], ay_dev [m]
+ * (float64, each in [0, 1]).  sigma <= 0 selects the population std of ax;
+ * p >= 1; g_mode as in scgr_params.  All intermediate buffers live in one
+ * file-scope device array of fixed size (about 25 MB, held by every GPU that
+ * loads the library until the process exits); nothing is allocated.
+ *
+ * Limits: 1 <= n, m <= 131072 points; larger sizes return
+ * SCGR_ERR_INVALID_ARG.  A non-finite coordinate or a curvature outside
+ * [0, 1] returns SCGR_ERR_NONFINITE.  The call runs on `cuda_stream` and
+ * synchronises it before returning.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress, with that device current);
+ * make that first call before any stream capture.  Every call shares the
+ * array, so calls that overlap on the GPU (other streams, other host
+ * threads) race and must be serialised by the caller. */
+SCGR_EXPORT scgr_status scgr_forces_static(const float* x_dev, int64_t n, const float* y_dev, int64_t m,
+                                           const double* ax_dev, const double* ay_dev, double sigma,
+                                           double p, int g_mode, float* f4_dev, void* cuda_stream);
+
 /* Number of kernel launches this context has issued so far (diagnostic). */
 SCGR_EXPORT int64_t scgr_launch_count(const scgr_ctx* ctx);
 

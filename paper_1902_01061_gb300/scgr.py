@@ -28,7 +28,7 @@ EXPORTED = (
     "scgr_compute_descriptors", "scgr_run", "scgr_get_result", "scgr_get_moved",
     "scgr_get_moved_host", "scgr_get_descriptors", "scgr_get_sigma", "scgr_get_curvature64",
     "scgr_forces", "scgr_get_state", "scgr_set_state", "scgr_sync", "scgr_launch_count",
-    "scgr_set_curvature", "scgr_set_force_timing", "scgr_get_force_timing",
+    "scgr_set_curvature", "scgr_set_force_timing", "scgr_get_force_timing", "scgr_forces_static",
 )
 
 
@@ -96,6 +96,8 @@ def load():
         "scgr_set_curvature": (S, [ctx, c_int, c_void_p]),
         "scgr_set_force_timing": (S, [ctx, c_int]),
         "scgr_get_force_timing": (S, [ctx, POINTER(c_int64), POINTER(c_double)]),
+        "scgr_forces_static": (S, [c_void_p, c_int64, c_void_p, c_int64, c_void_p, c_void_p, c_double,
+                                   c_double, c_int, c_void_p, c_void_p]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -240,6 +242,24 @@ def scgr_get_force_timing(ctx):
     ms = c_double()
     _check(load().scgr_get_force_timing(ctx, ctypes.byref(n), ctypes.byref(ms)), ctx)
     return int(n.value), float(ms.value)
+
+
+def scgr_forces_static(x, y, ax, ay, f4_out, sigma: float = 0.0, p: float = 1.0, g_mode: int = 1,
+                       stream=None) -> None:
+    """Allocation-free force evaluation (no context): for callers that cannot
+    allocate device memory.  x [n,3] / y [m,3] float32, ax [n] / ay [m]
+    float64, f4_out [m,4] float32, all CUDA tensors; at most 131072 points
+    per cloud; synchronises the stream."""
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream().cuda_stream
+    elif hasattr(stream, "cuda_stream"):
+        stream = stream.cuda_stream
+    st = load().scgr_forces_static(_dev_ptr(x, "float32", (3,)), x.shape[0], _dev_ptr(y, "float32", (3,)),
+                                   y.shape[0], _dev_ptr(ax, "float64"), _dev_ptr(ay, "float64"), float(sigma),
+                                   float(p), int(g_mode), _dev_ptr(f4_out, "float32", (4,)), c_void_p(stream))
+    if st != SCGR_OK:
+        raise ScgrError(st, "scgr_forces_static failed")
 
 
 def scgr_forces(ctx, f4_out) -> None:
