@@ -43,6 +43,8 @@ WORKLOADS = {
                   n=1_000_000, iters=50),
     "scale": dict(desc="35,000 reference x 30,800 template points (5-ellipsoid surface, 20% slab removed, "
                        "10% uniform outliers), p=2, k=16, 200 iterations", n=35_000, iters=200),
+    "mid": dict(desc="320,000 template x 320,000 reference points from the large-case generator, p=2, k=16, "
+                     "5 iterations (small case for profiler captures)", n=320_000, iters=5),
     "tiny": dict(desc="1,000 x 1,000 points (3-ellipsoid surface, 50 deg about x), p=2, k=16, 100 iterations",
                  n=1000, iters=100),
 }
@@ -54,6 +56,8 @@ def make_pair(name):
         return synth.large_case()
     if name == "scale":
         return synth.scale_case()
+    if name == "mid":
+        return synth.large_case(n=320_000)
     return synth.tiny()
 
 

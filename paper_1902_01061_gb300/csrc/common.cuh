@@ -4,9 +4,11 @@
 //   X4, Y4      float4 [n] packed input clouds (x, y, z, 0), original frame
 //   knnX, knnY  int32 [n][k] neighbour lists sorted by (key, index)
 //   aX64, aY64  float64 [n] curvature (Sec. III-A), aX32/aY32 float32 copies
-//   Xr          float4 [npad] force-kernel reference record
-//               (x - xbar, y - ybar, z - zbar, |X'|^2), xbar = reference mean
-//   XA          float2 [npad] (a_hat = a * sqrt(log2 e) / sigma, L = log2 a or 0)
+//   Xr          float [npad/TJ][4][TJ] force-kernel reference records, tile-major
+//               structure-of-arrays: x', y', z' (frame centred on the reference
+//               mean) and |X'|^2 for each tile of FORCE_TJ points
+//   XA          float [npad/TJ][2][TJ]: a_hat = a * sqrt(log2 e) / sigma and
+//               -L (L = log2 aX, or 0 in the mode g = s)
 //   Y0r         float4 [mpad] (Y0x, Y0y, Y0z, a_hat) template record
 //   partial     float4 [S][mpad] per-split (sum w, sum w X') of the force kernel
 //   blockpart   float64 [nblocks][13] per-block (F, W, T) of the combine kernel
@@ -141,6 +143,10 @@ cudaError_t launch_records(Launch L, const float4* X4, const double* aX64, int n
                            const float4* Y4, const double* aY64, int m, int mpad, int g_mode,
                            const DevStats* stats, float4* Xr, float2* XA, float4* Y0r);
 
+// Reference points per shared-memory tile of the force kernel; npad is a
+// multiple of it.
+constexpr int FORCE_TJ = 256;
+
 struct ForcePlan {
   int P;          // template points per thread
   int tpb;        // threads per block
@@ -166,5 +172,13 @@ cudaError_t launch_finalize(Launch L, const double* blockpart, int nblocks, DevP
                             const DevStats* stats, StepParams sp, int* err);
 cudaError_t launch_apply(Launch L, const float4* Y4, int m, const DevPose* pose, float* out);
 cudaError_t launch_pose_refresh(Launch L, DevPose* pose, const DevStats* stats);
+
+cudaError_t launch_pose_from7(Launch L, const double* pose7_dev, DevPose* ps, const DevStats* st);
+cudaError_t launch_adjoint_combine(Launch L, const float4* partial, int S, int mpad, int m, const float4* Y0r,
+                                   const double* aY64, int g_mode, const DevPose* ps, float* grad_xyz,
+                                   double* blockpart);
+cudaError_t launch_column_sum13(Launch L, const double* part, int nb, double* out);
+cudaError_t launch_adjoint_finish(Launch L, const double* tot, const double* pose7_dev, const DevPose* ps,
+                                  double* grad7);
 
 }  // namespace scgr

@@ -289,32 +289,41 @@ cudaError_t launch_check_curvature(Launch L, const double* a64, int n, float* a3
 // ---- force-kernel records ----------------------------------------------
 // s_ij = exp(-(aX - aY)^2 / sigma^2) = 2^(-(a_hat_X - a_hat_Y)^2) with
 // a_hat = a * sqrt(log2 e) / sigma (Eq. 3).  In the mode g = aX aY s (Eq. 10)
-// the factor aX enters the exponent as L = log2 aX and aY multiplies the
-// per-point sums; in the mode g = s, L = 0 and the aY factor is 1.
-// Reference coordinates are shifted by the reference mean so that
-// |X'|^2 + |Y'|^2 - 2 X'.Y' loses little to cancellation.  Padding records
-// carry L = -inf, so their weight is exactly 0.
+// the factor aX enters the exponent as L = log2 aX (stored negated, -L >= 0)
+// and aY multiplies the per-point sums; in the mode g = s, L = 0 and the aY
+// factor is 1.  Reference coordinates are shifted by the reference mean so
+// that |X'|^2 + |Y'|^2 - 2 X'.Y' loses little to cancellation.  The records
+// are written tile-major as structure-of-arrays (FORCE_TJ points per tile).
+// Padding records carry -L = +inf, so their weight is exactly 0.
 __global__ void records_kernel(const float4* __restrict__ X4, const double* __restrict__ aX64,
                                int n, int npad, const float4* __restrict__ Y4,
                                const double* __restrict__ aY64, int m, int mpad, int g_mode,
-                               const DevStats* __restrict__ st, float4* __restrict__ Xr,
-                               float2* __restrict__ XA, float4* __restrict__ Y0r) {
+                               const DevStats* __restrict__ st, float* __restrict__ Xr,
+                               float* __restrict__ XA, float4* __restrict__ Y0r) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const double kscale = sqrt(1.4426950408889634) / st->sigma;  // sqrt(log2 e) / sigma
   if (i < npad) {
+    const size_t t = (size_t)(i / FORCE_TJ), r = (size_t)(i % FORCE_TJ);
+    float* xr = Xr + t * 4 * FORCE_TJ + r;
+    float* xa = XA + t * 2 * FORCE_TJ + r;
     if (i < n) {
       const float4 c = X4[i];
       const float x = (float)((double)c.x - st->xbar[0]);
       const float y = (float)((double)c.y - st->xbar[1]);
       const float z = (float)((double)c.z - st->xbar[2]);
       const double nn = (double)x * x + (double)y * y + (double)z * z;
-      Xr[i] = make_float4(x, y, z, (float)nn);
+      xr[0] = x;
+      xr[FORCE_TJ] = y;
+      xr[2 * FORCE_TJ] = z;
+      xr[3 * FORCE_TJ] = (float)nn;
       const double a = aX64[i];
-      const float L = g_mode == 1 ? (a > 0.0 ? (float)log2(a) : -INFINITY) : 0.f;
-      XA[i] = make_float2((float)(a * kscale), L);
+      const float nL = g_mode == 1 ? (a > 0.0 ? (float)(-log2(a)) : INFINITY) : 0.f;
+      xa[0] = (float)(a * kscale);
+      xa[FORCE_TJ] = nL;
     } else {
-      Xr[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-      XA[i] = make_float2(0.f, -INFINITY);
+      xr[0] = xr[FORCE_TJ] = xr[2 * FORCE_TJ] = xr[3 * FORCE_TJ] = 0.f;
+      xa[0] = 0.f;
+      xa[FORCE_TJ] = INFINITY;
     }
   }
   if (i < mpad) {
@@ -332,8 +341,9 @@ cudaError_t launch_records(Launch L, const float4* X4, const double* aX64, int n
                            const DevStats* stats, float4* Xr, float2* XA, float4* Y0r) {
   const int tpb = 256;
   const int tot = npad > mpad ? npad : mpad;
-  records_kernel<<<(tot + tpb - 1) / tpb, tpb, 0, L.stream>>>(X4, aX64, n, npad, Y4, aY64, m, mpad,
-                                                              g_mode, stats, Xr, XA, Y0r);
+  records_kernel<<<(tot + tpb - 1) / tpb, tpb, 0, L.stream>>>(
+      X4, aX64, n, npad, Y4, aY64, m, mpad, g_mode, stats, reinterpret_cast<float*>(Xr),
+      reinterpret_cast<float*>(XA), Y0r);
   return after_launch(L);
 }
 

@@ -8,16 +8,22 @@
 // f_i = aY (sum_j w X_j - Y_i sum_j w) is formed afterwards in float64.
 //
 // Per pair (float32): d^2 = |X'|^2 + |Y'|^2 - 2 X'.Y' (one add, three FMAs),
-// the similarity-and-aX factor 2^(L - (a_hat_X - a_hat_Y)^2) (one add, one
-// FMA, one ex2), the distance factor (sqrt for p = 2, folded into the ex2
-// exponent through lg2 for general p), and four accumulations.  ex2 and the
-// distance MUFU op are the only special-function instructions.
+// the similarity-and-aX factor 2^-(u^2 - L), u = a_hat_X - a_hat_Y (one sub,
+// one FMA, one ex2), the distance factor (sqrt for p = 2, folded into the ex2
+// exponent through lg2 for general p), and four accumulations.
+//
+// The FP32 arithmetic runs on packed pairs (Blackwell add/sub/mul/fma
+// .f32x2): each instruction handles reference points j and j+1 for one
+// template point, so a pair costs 5.5 FP32-pipe issue slots plus its two
+// special-function (MUFU) operations, and the MUFU unit becomes the limit.
+// Reference tiles are stored tile-major as structure-of-arrays
+// (x, y, z, |X'|^2 | a_hat, -L), so a 128-bit shared-memory broadcast delivers
+// four consecutive points of one field.
 //
 // Layout of the work: grid.x covers template points (P per thread, TPB
 // threads), grid.y splits the reference range so that the grid has many
-// waves on 152 SMs.  Reference tiles of TJ points are staged in shared
-// memory and read as broadcasts.  Each tile's sums are accumulated in plain
-// float32 and then added to the running per-point sums with Kahan
+// waves on 152 SMs.  Each tile's sums are accumulated in plain float32 (two
+// lanes per point) and then added to the running per-point sums with Kahan
 // compensation; each split writes its per-point partial (float4) and the
 // combine kernel adds the splits in a fixed order in float64, so results are
 // deterministic.
@@ -27,9 +33,40 @@
 
 namespace scgr {
 
-__device__ __forceinline__ float ex2_approx(float x) {
+typedef unsigned long long u64;  // two packed float32 lanes: low = point j, high = point j+1
+
+__device__ __forceinline__ u64 pk2(float lo, float hi) {
+  u64 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ void upk2(u64 v, float& lo, float& hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ u64 add2(u64 a, u64 b) {
+  u64 d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ u64 sub2(u64 a, u64 b) {
+  u64 d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ u64 mul2(u64 a, u64 b) {
+  u64 d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ u64 fma2(u64 a, u64 b, u64 c) {
+  u64 d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+// 2^-x
+__device__ __forceinline__ float ex2_neg(float x) {
   float y;
-  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  asm("{ .reg .f32 t; neg.f32 t, %1; ex2.approx.ftz.f32 %0, t; }" : "=f"(y) : "f"(x));
   return y;
 }
 __device__ __forceinline__ float lg2_approx(float x) {
@@ -59,13 +96,50 @@ __device__ __forceinline__ void kahan_add(float& s, float& c, float x) {
   s = t;
 }
 
+// One packed pair update: reference points (j, j+1) against one template point.
+template <int PM>
+__device__ __forceinline__ void pair2(u64 xv, u64 yv, u64 zv, u64 nv, u64 av, u64 lv, u64 mx, u64 my,
+                                      u64 mz, u64 ny, u64 ah, u64 nq, u64& W, u64& Sx, u64& Sy, u64& Sz) {
+  u64 d2 = add2(nv, ny);
+  d2 = fma2(xv, mx, d2);
+  d2 = fma2(yv, my, d2);
+  d2 = fma2(zv, mz, d2);
+  const u64 u = sub2(av, ah);
+  const u64 ep = fma2(u, u, lv);  // u^2 - L >= 0; the weight is 2^-ep times the distance factor
+  u64 w;
+  if (PM == 1) {
+    float e0, e1;
+    upk2(ep, e0, e1);
+    w = pk2(ex2_neg(e0), ex2_neg(e1));
+  } else if (PM == 2) {
+    float e0, e1, q0, q1;
+    upk2(ep, e0, e1);
+    upk2(d2, q0, q1);
+    w = mul2(pk2(ex2_neg(e0), ex2_neg(e1)), pk2(sqrt_approx(fabsf(q0)), sqrt_approx(fabsf(q1))));
+  } else if (PM == 3) {
+    float e0, e1;
+    upk2(ep, e0, e1);
+    w = mul2(pk2(ex2_neg(e0), ex2_neg(e1)), d2);
+  } else {
+    float q0, q1;
+    upk2(d2, q0, q1);
+    const u64 t = fma2(nq, pk2(lg2_approx(fabsf(q0)), lg2_approx(fabsf(q1))), ep);  // ep - q log2 d^2
+    float t0, t1;
+    upk2(t, t0, t1);
+    w = pk2(ex2_neg(t0), ex2_neg(t1));
+  }
+  W = add2(W, w);
+  Sx = fma2(w, xv, Sx);
+  Sy = fma2(w, yv, Sy);
+  Sz = fma2(w, zv, Sz);
+}
+
 template <int P, int PM, int TPB, int TJ, int MINB>
 __global__ void __launch_bounds__(TPB, MINB)
-    force_tile_kernel(const float4* __restrict__ Xr, const float2* __restrict__ XA, int ntiles,
+    force_tile_kernel(const float* __restrict__ Xr, const float* __restrict__ XA, int ntiles,
                       int tiles_per_split, const float4* __restrict__ Y0r, int mpad,
                       const DevPose* __restrict__ pose, float qexp, float4* __restrict__ partial) {
-  __shared__ float4 sX[TJ];
-  __shared__ float2 sA[TJ];
+  __shared__ __align__(16) float sT[6][TJ];
   const int tid = threadIdx.x;
   const int ibase = blockIdx.x * (TPB * P);
   const int split = blockIdx.y;
@@ -76,18 +150,20 @@ __global__ void __launch_bounds__(TPB, MINB)
 #pragma unroll
   for (int q = 0; q < 3; ++q) b[q] = pose->b[q];
 
-  float m2x[P], m2y[P], m2z[P], nY[P], ah[P];
+  u64 mx[P], my[P], mz[P], ny[P], ah[P];
 #pragma unroll
   for (int q = 0; q < P; ++q) {
     const float4 y0 = Y0r[ibase + q * TPB + tid];
     float yx, yy, yz;
     template_point(y0, A, b, yx, yy, yz);
-    m2x[q] = -2.f * yx;
-    m2y[q] = -2.f * yy;
-    m2z[q] = -2.f * yz;
-    nY[q] = fmaf(yz, yz, fmaf(yy, yy, yx * yx));
-    ah[q] = y0.w;
+    const float n = fmaf(yz, yz, fmaf(yy, yy, yx * yx));
+    mx[q] = pk2(-2.f * yx, -2.f * yx);
+    my[q] = pk2(-2.f * yy, -2.f * yy);
+    mz[q] = pk2(-2.f * yz, -2.f * yz);
+    ny[q] = pk2(n, n);
+    ah[q] = pk2(y0.w, y0.w);
   }
+  const u64 nq = pk2(-qexp, -qexp);
 
   float hW[P], hx[P], hy[P], hz[P];  // running sums
   float cW[P], cx[P], cy[P], cz[P];  // Kahan compensations
@@ -101,51 +177,47 @@ __global__ void __launch_bounds__(TPB, MINB)
   const int t1 = min(ntiles, t0 + tiles_per_split);
   for (int t = t0; t < t1; ++t) {
     __syncthreads();
+    {
+      const float4* g4 = reinterpret_cast<const float4*>(Xr + (size_t)t * 4 * TJ);
+      const float4* a4 = reinterpret_cast<const float4*>(XA + (size_t)t * 2 * TJ);
+      float4* s4 = reinterpret_cast<float4*>(&sT[0][0]);
 #pragma unroll
-    for (int u = tid; u < TJ; u += TPB) {
-      sX[u] = Xr[(size_t)t * TJ + u];
-      sA[u] = XA[(size_t)t * TJ + u];
+      for (int u = tid; u < TJ; u += TPB) s4[u] = g4[u];                 // rows 0..3
+#pragma unroll
+      for (int u = tid; u < TJ / 2; u += TPB) s4[TJ + u] = a4[u];        // rows 4..5
     }
     __syncthreads();
 
-    float aW[P], ax[P], ay[P], az[P];
+    u64 aW[P], ax[P], ay[P], az[P];
 #pragma unroll
-    for (int q = 0; q < P; ++q) aW[q] = ax[q] = ay[q] = az[q] = 0.f;
+    for (int q = 0; q < P; ++q) aW[q] = ax[q] = ay[q] = az[q] = 0ull;  // +0.0f in both lanes
 
 #pragma unroll 2
-    for (int jj = 0; jj < TJ; ++jj) {
-      const float4 xr = sX[jj];
-      const float2 xa = sA[jj];
+    for (int jq = 0; jq < TJ; jq += 4) {
+      const ulonglong2 X = *reinterpret_cast<const ulonglong2*>(&sT[0][jq]);
+      const ulonglong2 Yv = *reinterpret_cast<const ulonglong2*>(&sT[1][jq]);
+      const ulonglong2 Z = *reinterpret_cast<const ulonglong2*>(&sT[2][jq]);
+      const ulonglong2 N = *reinterpret_cast<const ulonglong2*>(&sT[3][jq]);
+      const ulonglong2 Av = *reinterpret_cast<const ulonglong2*>(&sT[4][jq]);
+      const ulonglong2 Lv = *reinterpret_cast<const ulonglong2*>(&sT[5][jq]);
 #pragma unroll
-      for (int q = 0; q < P; ++q) {
-        float d2 = xr.w + nY[q];
-        d2 = fmaf(xr.x, m2x[q], d2);
-        d2 = fmaf(xr.y, m2y[q], d2);
-        d2 = fmaf(xr.z, m2z[q], d2);
-        const float u = xa.x - ah[q];
-        const float e = fmaf(-u, u, xa.y);
-        float w;
-        if (PM == 1) {
-          w = ex2_approx(e);
-        } else if (PM == 2) {
-          w = ex2_approx(e) * sqrt_approx(fabsf(d2));
-        } else if (PM == 3) {
-          w = ex2_approx(e) * fabsf(d2);
-        } else {
-          w = ex2_approx(fmaf(qexp, lg2_approx(fabsf(d2)), e));
-        }
-        aW[q] += w;
-        ax[q] = fmaf(w, xr.x, ax[q]);
-        ay[q] = fmaf(w, xr.y, ay[q]);
-        az[q] = fmaf(w, xr.z, az[q]);
-      }
+      for (int q = 0; q < P; ++q)
+        pair2<PM>(X.x, Yv.x, Z.x, N.x, Av.x, Lv.x, mx[q], my[q], mz[q], ny[q], ah[q], nq, aW[q], ax[q], ay[q], az[q]);
+#pragma unroll
+      for (int q = 0; q < P; ++q)
+        pair2<PM>(X.y, Yv.y, Z.y, N.y, Av.y, Lv.y, mx[q], my[q], mz[q], ny[q], ah[q], nq, aW[q], ax[q], ay[q], az[q]);
     }
 #pragma unroll
     for (int q = 0; q < P; ++q) {
-      kahan_add(hW[q], cW[q], aW[q]);
-      kahan_add(hx[q], cx[q], ax[q]);
-      kahan_add(hy[q], cy[q], ay[q]);
-      kahan_add(hz[q], cz[q], az[q]);
+      float l0, l1;
+      upk2(aW[q], l0, l1);
+      kahan_add(hW[q], cW[q], l0 + l1);
+      upk2(ax[q], l0, l1);
+      kahan_add(hx[q], cx[q], l0 + l1);
+      upk2(ay[q], l0, l1);
+      kahan_add(hy[q], cy[q], l0 + l1);
+      upk2(az[q], l0, l1);
+      kahan_add(hz[q], cz[q], l0 + l1);
     }
   }
 
@@ -156,14 +228,19 @@ __global__ void __launch_bounds__(TPB, MINB)
 }
 
 // ---- planning --------------------------------------------------------------
-constexpr int FORCE_TJ = 256;
 
+static int force_blocks_per_sm(const ForcePlan& fp);
+
+// Work split: template points per thread by size, then the number of
+// reference splits S that fills whole waves of resident blocks.  All blocks
+// do (almost) the same work, so the last wave's fill decides the tail: pick
+// the smallest S in [S_lo, S_hi] whose grid fills its last wave to >= 99%
+// (else the best fill seen).
 ForcePlan plan_force(int64_t m, int64_t npad, double p, int num_sms) {
   ForcePlan fp;
   fp.pmode = (p == 1.0) ? 1 : (p == 2.0) ? 2 : (p == 3.0) ? 3 : 0;
   fp.tile_j = FORCE_TJ;
   fp.tpb = 256;
-  // points per thread: the largest that still gives every SM work
   if (m >= (int64_t)num_sms * 2 * 256 * 4) fp.P = 4;
   else if (m >= (int64_t)num_sms * 256 * 2) fp.P = 2;
   else fp.P = 1;
@@ -171,15 +248,29 @@ ForcePlan plan_force(int64_t m, int64_t npad, double p, int num_sms) {
   const int64_t per_block = (int64_t)fp.tpb * fp.P;
   fp.iblocks = (int)((m + per_block - 1) / per_block);
   const int ntiles = (int)(npad / FORCE_TJ);
-  // aim for >= 16 waves of 2 resident blocks per SM, split the reference
-  // range to get there, but keep >= 4 tiles per split
-  const int64_t target = (int64_t)num_sms * 2 * 16;
-  int64_t S = (target + fp.iblocks - 1) / fp.iblocks;
-  int64_t Smax = ntiles / 4 > 0 ? ntiles / 4 : 1;
-  if (S > Smax) S = Smax;
-  if (S > 64) S = 64;
-  if (S < 1) S = 1;
-  fp.tiles_per_split = (int)((ntiles + S - 1) / S);
+  const int64_t slots = (int64_t)num_sms * force_blocks_per_sm(fp);
+  // at least 8 waves when the reference range allows it, at most 64 splits,
+  // and at least 4 tiles per split
+  int64_t S_lo = (8 * slots + fp.iblocks - 1) / fp.iblocks;
+  int64_t S_hi = ntiles / 4 > 0 ? ntiles / 4 : 1;
+  if (S_hi > 64) S_hi = 64;
+  if (S_lo > S_hi) S_lo = S_hi;
+  if (S_lo < 1) S_lo = 1;
+  int64_t best_S = S_lo;
+  double best_fill = -1.0;
+  for (int64_t S = S_lo; S <= S_hi; ++S) {
+    const int64_t tps = (ntiles + S - 1) / S;
+    const int64_t splits = (ntiles + tps - 1) / tps;
+    const int64_t total = fp.iblocks * splits;
+    const int64_t waves = (total + slots - 1) / slots;
+    const double fill = (double)total / (double)(waves * slots);
+    if (fill > best_fill + 1e-12) {
+      best_fill = fill;
+      best_S = S;
+    }
+    if (fill >= 0.99) break;
+  }
+  fp.tiles_per_split = (int)((ntiles + best_S - 1) / best_S);
   fp.splits = (ntiles + fp.tiles_per_split - 1) / fp.tiles_per_split;
   return fp;
 }
@@ -197,7 +288,8 @@ static void launch_force_t(cudaStream_t st, const ForcePlan& fp, const float4* X
                            const DevPose* pose, float qexp, float4* partial) {
   dim3 grid(fp.iblocks, fp.splits);
   force_tile_kernel<P, PM, TPB, FORCE_TJ, 2><<<grid, TPB, 0, st>>>(
-      Xr, XA, ntiles, fp.tiles_per_split, Y0r, mpad, pose, qexp, partial);
+      reinterpret_cast<const float*>(Xr), reinterpret_cast<const float*>(XA), ntiles,
+      fp.tiles_per_split, Y0r, mpad, pose, qexp, partial);
 }
 
 template <int PM>
@@ -210,6 +302,33 @@ static void launch_force_pm(cudaStream_t st, const ForcePlan& fp, const float4* 
     else launch_force_t<1, PM, 256>(st, fp, Xr, XA, ntiles, Y0r, mpad, pose, qexp, partial);
   } else {
     launch_force_t<1, PM, 128>(st, fp, Xr, XA, ntiles, Y0r, mpad, pose, qexp, partial);
+  }
+}
+
+template <int PM>
+static int blocks_per_sm_pm(const ForcePlan& fp) {
+  int nb = 0;
+  cudaError_t e;
+  if (fp.tpb == 256) {
+    if (fp.P == 4) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, force_tile_kernel<4, PM, 256, FORCE_TJ, 2>, 256, 0);
+    else if (fp.P == 2) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, force_tile_kernel<2, PM, 256, FORCE_TJ, 2>, 256, 0);
+    else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, force_tile_kernel<1, PM, 256, FORCE_TJ, 2>, 256, 0);
+  } else {
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, force_tile_kernel<1, PM, 128, FORCE_TJ, 2>, 128, 0);
+  }
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return 2;
+  }
+  return nb > 0 ? nb : 1;
+}
+
+static int force_blocks_per_sm(const ForcePlan& fp) {
+  switch (fp.pmode) {
+    case 1: return blocks_per_sm_pm<1>(fp);
+    case 2: return blocks_per_sm_pm<2>(fp);
+    case 3: return blocks_per_sm_pm<3>(fp);
+    default: return blocks_per_sm_pm<0>(fp);
   }
 }
 
