@@ -145,6 +145,21 @@ def profile_traffic():
     return (traffic if tag == digest else None), digest
 
 
+def measured_peaks(scgr, num_sms, sm_mhz):
+    """Unit throughputs measured by the library's microbenchmark at the
+    current clock: FP32 lane-FMAs and MUFU results per clock per SM."""
+    names = ["ffma", "ffma2_f32x2", "mufu_ex2", "mufu_sqrt", "mufu_lg2"]
+    out = {}
+    for kind, name in enumerate(names):
+        ops, ms = scgr.scgr_microbench(kind)
+        per_clk_sm = ops / (ms * 1e-3) / (num_sms * sm_mhz * 1e6)
+        out[name] = {"per_clk_per_sm": per_clk_sm, "ms": ms}
+        if kind <= 1:
+            out[name]["tflops"] = 2 * ops / (ms * 1e-3) / 1e12
+    out["clock_mhz_assumed"] = sm_mhz
+    return out
+
+
 def cpu_baseline(pair, p, g_mode, seconds=15.0):
     """The FP64 oracle as it stands, on the host, for a bounded sample: the
     iteration-0 force pass (Eq. 5) for a few template rows against every
@@ -169,6 +184,74 @@ def cpu_baseline(pair, p, g_mode, seconds=15.0):
     return {"value": nrows * n / dt, "unit": "pair-interactions/s", "cores": 1, "kind": "oracle",
             "sample": f"iteration-0 force pass (Eq. 5) of {nrows} template rows x {n} reference points "
                       f"in float64 numpy, single thread, {dt:.1f} s"}
+
+
+def bench_batch(args, scgr, torch, dev, steps, warmup):
+    """Batched registrations/s on 512 pairs (log-uniform 500-20,000 points,
+    rotation <= 90 deg, scale 0.7-1.4, 0-15% outliers), 100 iterations in one
+    CUDA graph, against one call per pair (same parameters, graph per pair)."""
+    import numpy as np
+    from paper_1902_01061_gb300 import synth
+    pairs = synth.batch_case()
+    iters = 100
+    ro = np.cumsum([0] + [len(pp.X) for pp in pairs]).astype(np.int64)
+    to = np.cumsum([0] + [len(pp.Y0) for pp in pairs]).astype(np.int64)
+    Xc = torch.from_numpy(np.concatenate([pp.X for pp in pairs])).to(dev)
+    Yc = torch.from_numpy(np.concatenate([pp.Y0 for pp in pairs])).to(dev)
+    pair_work = int(sum(len(pp.X) * len(pp.Y0) for pp in pairs))
+    params = scgr.scgr_default_params(p=2.0, g_mode=1, k=16, use_graph=1)
+    stream = torch.cuda.current_stream()
+    ctx = scgr.scgr_create(params, stream)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def one_batch():
+        scgr.scgr_batch_run(ctx, ro, Xc, to, Yc, iters)
+
+    for _ in range(warmup):
+        one_batch()
+    times = []
+    l0 = scgr.scgr_launch_count(ctx)
+    for _ in range(steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        one_batch()                      # synchronises (results copied to the host)
+        times.append(time.perf_counter() - t0)
+    batch_launches = (scgr.scgr_launch_count(ctx) - l0) // max(steps, 1)
+    batch_s = sum(times) / len(times)
+    scgr.scgr_destroy(ctx)
+
+    # one call per pair, same method parameters, eager launches (capturing a
+    # graph per pair costs more than it saves at 100 iterations)
+    ctx1 = scgr.scgr_create(scgr.scgr_default_params(p=2.0, g_mode=1, k=16), stream)
+    views = [(Xc[ro[i]:ro[i + 1]], Yc[to[i]:to[i + 1]]) for i in range(len(pairs))]
+
+    def per_pair():
+        for xv, yv in views:
+            scgr.scgr_set_reference(ctx1, xv)
+            scgr.scgr_set_template(ctx1, yv)
+            scgr.scgr_compute_descriptors(ctx1)
+            scgr.scgr_run(ctx1, iters)
+            scgr.scgr_get_result(ctx1)
+
+    per_pair()                           # warm (graph instantiation for each size)
+    flush.zero_()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    per_pair()
+    single_s = time.perf_counter() - t0
+    scgr.scgr_destroy(ctx1)
+    return {"workload": "512 pairs, 500-20,000 points log-uniform, rotation <= 90 deg, scale 0.7-1.4, "
+                        "0-15% outliers, p=2, k=16, 100 iterations in one CUDA graph",
+            "npairs": len(pairs), "points": int(ro[-1] + to[-1]), "pair_interactions_per_iteration": pair_work,
+            "registrations_per_s": len(pairs) / batch_s, "ms_per_batch": batch_s * 1e3,
+            "pair_interactions_per_s": pair_work * iters / batch_s,
+            "launches_per_batch": int(batch_launches),
+            "one_call_per_pair_registrations_per_s": len(pairs) / single_s,
+            "speedup_vs_one_call_per_pair": single_s / batch_s,
+            "one_call_per_pair": "scgr_set_reference/template + compute_descriptors + run(100) + get_result "
+                                 "per pair, eager launches",
+            "timing": "host wall clock around each synchronising call, L2 flushed before each"}
 
 
 def run_reference(args, ws, rank):
@@ -222,6 +305,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-rows", type=int, default=48)
+    ap.add_argument("--no-batch", action="store_true", help="skip the 512-pair batched leg")
     args = ap.parse_args()
     ws, rank, local = dist_env()
     if args.impl == "reference":
@@ -323,6 +407,9 @@ def main():
         e2e = {"value": ws * pairs_per_step / e2e_s, "unit": "pair-interactions/s",
                "h2d_bytes_per_step": (n + m) * 12, "d2h_bytes_per_step": m * 12 + 8 * 13 + 8}
     scgr.scgr_destroy(ctx)
+    batch = None
+    if ws == 1 and not args.no_batch:
+        batch = bench_batch(args, scgr, torch, dev, args.steps, args.warmup)
 
     if rank != 0:
         if ws > 1:
@@ -357,7 +444,9 @@ def main():
         "clocks": clk,
         "roofline": roofline,
         "e2e": e2e,
+        "batch": batch,
     }
+    line["peaks_measured"] = measured_peaks(scgr, num_sms, sm_mhz or sm_max_mhz)
     if ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(pair, 2.0, 1)
     print(json.dumps(line), flush=True)

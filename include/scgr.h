@@ -124,7 +124,9 @@ SCGR_EXPORT scgr_status scgr_set_template_host(scgr_ctx* ctx, const float* xyz_h
 
 /* One-time descriptor pass (Sec. III-A, Sec. IV): k-nearest neighbours of
  * every point of X and of Y0 (exact float32 key (dx*dx+dy*dy)+dz*dz, no fused
- * multiply-add, self included, ties to the lower index), the curvature
+ * multiply-add, self included, ties to the lower index; brute force for
+ * small clouds, an exact uniform-grid search for large ones, which waits once
+ * for the bounding box), the curvature
  * a = lambda_min / (lambda_1+lambda_2+lambda_3) of each neighbourhood's
  * covariance (float64), sigma, and the cloud statistics used by the scale
  * model (means, covariances, largest eigenvalues).  Resets the pose to
@@ -173,6 +175,20 @@ SCGR_EXPORT scgr_status scgr_set_curvature(scgr_ctx* ctx, int which, const doubl
  * Enqueued.  STATE before descriptors. */
 SCGR_EXPORT scgr_status scgr_forces(scgr_ctx* ctx, float* f4_dev);
 
+/* Differentiation form.  The shape-weighted potential
+ *   U = sum_i sum_j g(s_ij) d_ij^(p+1) / (p+1)
+ * whose negative gradient with respect to Y_i is the force of Eq. 5 (Eq. 3,
+ * Eq. 10, Eq. 11; descriptors held fixed), evaluated at the pose
+ * pose7 = (omega[3], t[3], s): Y = s * Y0 @ R + t with R = exp([omega]_x)^T
+ * (axis-angle, row-vector convention).  Optional outputs: grad_pose7 (host,
+ * 7 doubles: dU/domega, dU/dt, dU/ds) and grad_xyz_dev (device float32
+ * [m][3]: dU/dY0).  The gradient pass recomputes the pair tiles of the force
+ * kernel (no N x M storage); sums are float64 in a fixed order.  The
+ * registration pose is not touched.  Synchronises.  STATE before
+ * descriptors; INVALID_ARG for a non-finite pose or s <= 0. */
+SCGR_EXPORT scgr_status scgr_potential(scgr_ctx* ctx, const double pose7[7], double* U_out,
+                                       double* grad_pose7, float* grad_xyz_dev);
+
 /* Checkpoint / resume of the iteration state.  Both synchronise. */
 SCGR_EXPORT scgr_status scgr_get_state(scgr_ctx* ctx, scgr_state* host_out);
 SCGR_EXPORT scgr_status scgr_set_state(scgr_ctx* ctx, const scgr_state* host_in);
@@ -215,6 +231,69 @@ SCGR_EXPORT scgr_status scgr_get_force_timing(scgr_ctx* ctx, int64_t* launches, 
 SCGR_EXPORT scgr_status scgr_forces_static(const float* x_dev, int64_t n, const float* y_dev, int64_t m,
                                            const double* ax_dev, const double* ay_dev, double sigma,
                                            double p, int g_mode, float* f4_dev, void* cuda_stream);
+
+/* Batching form: npairs independent registrations of uneven sizes in one
+ * call, with the context's parameters.  Pair p's reference is rows
+ * [ref_off[p], ref_off[p+1]) of ref_xyz_dev and its template rows
+ * [tmp_off[p], tmp_off[p+1]) of tmp_xyz_dev (float32 [.][3] device arrays;
+ * ref_off/tmp_off are host int64 arrays of npairs + 1 offsets starting at 0).
+ * Descriptors for all clouds run in one launch per stage; each iteration is
+ * three launches for all pairs (force work items sorted longest first, a
+ * per-pair fixed-order combine, one float64 finalize block per pair); with
+ * params.use_graph the iteration loop is captured in a CUDA graph and
+ * replayed.  results_host[p] receives pair p's pose (as scgr_get_result).
+ * The single-registration state of the context is not touched.
+ * Synchronises.  INVALID_ARG for bad offsets (a reference with fewer than k
+ * points, a template with fewer than max(k, 3)). */
+SCGR_EXPORT scgr_status scgr_batch_run(scgr_ctx* ctx, int npairs, const int64_t* ref_off_host,
+                                       const float* ref_xyz_dev, const int64_t* tmp_off_host,
+                                       const float* tmp_xyz_dev, int iterations, scgr_result* results_host);
+
+/* Template-row sharding of one registration over several processes (one
+ * GPU each).  scgr_set_row_range restricts the force pass of this context
+ * to template rows [row0, row0 + rows) (call after scgr_set_template and
+ * before scgr_compute_descriptors; statistics still use the whole template).
+ * An iteration is then split in two: scgr_step_partials computes this
+ * rank's 13 float64 partial sums (total force F[3], total weight W, moment
+ * T[3][3] = sum_i f_i (Y_i - ybar)^T over its rows; synchronises), the caller
+ * adds the ranks' partials in a fixed order (an all-reduce of 13 doubles),
+ * and scgr_step_apply(totals) performs the pose update (Eq. 5.5 - Eq. 12) from
+ * the totals (synchronises).  Ranks that apply identical totals hold
+ * identical poses.  Stepwise iteration needs params.E > 0.  With a row range
+ * set, scgr_run and scgr_potential return STATE and scgr_forces writes the
+ * range's rows only ([rows][4]). */
+SCGR_EXPORT scgr_status scgr_set_row_range(scgr_ctx* ctx, int64_t row0, int64_t rows);
+SCGR_EXPORT scgr_status scgr_step_partials(scgr_ctx* ctx, double out13[13]);
+SCGR_EXPORT scgr_status scgr_step_apply(scgr_ctx* ctx, const double tot13[13]);
+
+/* Tuning knobs (set by the autotuner; defaults are sensible). */
+#define SCGR_TUNE_BATCH_CHUNK_TILES 1 /* reference tiles (256 points) per batched work item, default 16 */
+#define SCGR_TUNE_KNN_GRID_MIN 2      /* clouds of at least this many points use the exact grid kNN
+                                         (default 65536; 0: always); the result is identical */
+#define SCGR_TUNE_FORCE_P 3           /* force kernel template points per thread: 0 auto, 1, 2, 4 */
+#define SCGR_TUNE_FORCE_TPB 4         /* force kernel threads per block: 0 auto, 128, 256 */
+#define SCGR_TUNE_FORCE_SPLITS 5      /* force kernel reference splits: 0 auto (wave-filling), >= 1 */
+#define SCGR_TUNE_REUSE_POSE_FREE 6   /* 1 (default): for p = 1, whose pair weights do not depend on the
+                                         pose, scgr_run computes the force sums once per call and reuses
+                                         them in its later iterations (bit-identical); 0: every iteration */
+/* Set one knob.  A force-plan knob re-plans at once when descriptors exist
+ * (records and workspace are rebuilt; descriptors and pose are kept),
+ * otherwise at scgr_compute_descriptors.  INVALID_ARG for an unknown key or
+ * value. */
+SCGR_EXPORT scgr_status scgr_set_tuning(scgr_ctx* ctx, int key, int value);
+/* The force plan in use: out = {points per thread, threads per block,
+ * reference splits, template blocks}.  STATE before descriptors. */
+SCGR_EXPORT scgr_status scgr_get_plan(scgr_ctx* ctx, int out[4]);
+
+/* Throughput microbenchmark of the units that bound the force kernel (no
+ * paper counterpart; roofline evidence).  kind: 0 scalar FFMA, 1 packed
+ * fma.f32x2, 2 MUFU ex2, 3 MUFU sqrt, 4 MUFU lg2.  Runs `blocks` x 256
+ * threads (8 x the SM count fills the GPU) on the caller's scratch out_dev
+ * (blocks x 256 floats); returns the FP32 lane operations (a packed FMA
+ * counts 2) or special-function results of one launch and the best device
+ * time (ms) of three launches.  Synchronises the stream. */
+SCGR_EXPORT scgr_status scgr_microbench(int kind, int blocks, float* out_dev, void* cuda_stream,
+                                        int64_t* lane_ops, double* ms);
 
 /* Number of kernel launches this context has issued so far (diagnostic). */
 SCGR_EXPORT int64_t scgr_launch_count(const scgr_ctx* ctx);

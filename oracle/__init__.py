@@ -31,6 +31,8 @@ Functions and their pins (the tests under ``tests/test_oracle_*.py``):
                        including the reflection case.
 * ``scale_factor``   - Sec. III-B / Eq. 8 with R8; pinned to one-step recovery
                        of a scaled copy.
+* ``partial_sums`` / ``update_from_totals`` - the iteration split at the
+                       13 totals (for row sharding); pinned to ``step_once``.
 * ``register``       - the whole iteration (Eq. 5-12); pinned to the fixed
                        point at the aligned pose and to recovery of known
                        synthetic transforms.
@@ -54,4 +56,6 @@ from .scgr_oracle import (  # noqa: F401
     polar,
     register,
     step_once,
+    partial_sums,
+    update_from_totals,
 )

@@ -340,6 +340,40 @@ def step_once(Y, X, desc, prm: Params, it: int, E: int, eX: float):
     return Ynext, info
 
 
+def partial_sums(Y, X, desc, prm: Params, rows):
+    """Sums over the template rows `rows` at the current template Y: total
+    force F (3), total weight W and the moment T = sum_i f_i (Y_i - ybar)^T
+    (3x3, ybar the mean of the whole template).  Adding the sums of a
+    partition of the rows gives the totals of one iteration (Eq. 5, 5.5, 6)."""
+    Y = np.asarray(Y, dtype=np.float64)
+    f, Wi = forces_rows(Y, X, desc["aY"], desc["aX"], desc["sigma"], prm.p, prm.g_mode, rows)
+    ybar = Y.mean(axis=0)
+    T = f.T @ (Y[rows] - ybar)
+    return np.concatenate([f.sum(axis=0), [Wi.sum()], T.reshape(9)])
+
+
+def update_from_totals(Y, totals, prm: Params, it: int, E: int, eX: float):
+    """The update of `step_once` computed from the 13 totals of
+    `partial_sums`: with Y_D = Y_c + delta - d, C^ = Y_D^T Y_c = Y_c^T Y_c + kappa T."""
+    Y = np.asarray(Y, dtype=np.float64)
+    totals = np.asarray(totals, dtype=np.float64)
+    F, W, T = totals[:3], float(totals[3]), totals[4:].reshape(3, 3)
+    M = len(Y)
+    G = g_schedule(it, prm.G1, E)
+    if prm.step_mode == 0:
+        kappa = prm.eta0 * (G / prm.G1) * M / W if W > 0 else 0.0
+    else:
+        kappa = G * prm.time ** 2
+    dvec = kappa * F / M
+    mu = Y.mean(axis=0)
+    Yc = Y - mu
+    Chat = Yc.T @ Yc + kappa * T
+    Rinc, degenerate = kabsch(Chat)
+    _, _, eY = cloud_stats(Y)
+    c = scale_factor(eX, eY, prm.scale_mode)
+    return c * Yc @ Rinc + mu + dvec, dict(c=c, Rinc=Rinc, mu=mu, d=dvec, degenerate=degenerate)
+
+
 def register(X, Y0, prm: Params | None = None, iterations: int = 100, desc=None,
              keep_history: bool = False, record_forces_at=()):
     """Run the method: descriptors once (R14), then `iterations` updates.

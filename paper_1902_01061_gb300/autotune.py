@@ -1,0 +1,143 @@
+"""Autotuner of the force kernel's tile shape and the batched work-item size.
+
+Candidates are timed on the caller's inputs through the C ABI, with CUDA
+events around each force launch on the library's own stream
+(scgr_set_force_timing).  The winner is cached in a JSON file keyed by GPU
+name, a power-of-two size bucket and the distance-exponent mode, so that a
+later registration of a similar size picks it up with `apply_cached`.
+Cache file: $SCGR_TUNE_CACHE, else ~/.cache/scgr/tune.json.
+"""
+from __future__ import annotations
+
+import json
+import math
+import os
+import time
+
+from . import scgr
+
+SINGLE_CANDIDATES = [(P, tpb, 0) for P in (1, 2, 4) for tpb in (128, 256)]
+BATCH_CHUNKS = (4, 8, 16, 32)
+
+
+def cache_path() -> str:
+    return os.environ.get("SCGR_TUNE_CACHE", os.path.join(os.path.expanduser("~"), ".cache", "scgr", "tune.json"))
+
+
+def _load() -> dict:
+    try:
+        with open(cache_path()) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def _store(key: str, value: dict) -> None:
+    data = _load()
+    data[key] = value
+    path = cache_path()
+    os.makedirs(os.path.dirname(path), exist_ok=True)
+    tmp = path + f".{os.getpid()}.tmp"
+    with open(tmp, "w") as f:
+        json.dump(data, f, indent=1, sort_keys=True)
+    os.replace(tmp, path)
+
+
+def _bucket(v: int) -> int:
+    return int(round(math.log2(max(int(v), 1))))
+
+
+def _pmode(p: float) -> str:
+    return {1.0: "p1", 2.0: "p2", 3.0: "p3"}.get(float(p), "pgen")
+
+
+def single_key(gpu: str, n: int, m: int, p: float) -> str:
+    return f"{gpu}|single|n2^{_bucket(n)}|m2^{_bucket(m)}|{_pmode(p)}"
+
+
+def batch_key(gpu: str, npairs: int, work: int, p: float) -> str:
+    return f"{gpu}|batch|pairs2^{_bucket(npairs)}|work2^{_bucket(work)}|{_pmode(p)}"
+
+
+def gpu_name() -> str:
+    import torch
+    return torch.cuda.get_device_name()
+
+
+def time_forces(ctx, m: int, reps: int = 3) -> float:
+    """Mean device time (ms) of the force kernel over `reps` force
+    evaluations of a context with m template rows."""
+    import torch
+    f4 = torch.empty((m, 4), dtype=torch.float32, device="cuda")
+    scgr.scgr_forces(ctx, f4)                      # warm
+    scgr.scgr_set_force_timing(ctx, True)
+    try:
+        for _ in range(reps):
+            scgr.scgr_forces(ctx, f4)
+        n, ms = scgr.scgr_get_force_timing(ctx)
+    finally:
+        scgr.scgr_set_force_timing(ctx, False)
+    return ms / max(n, 1)
+
+
+def tune_single(ctx, n: int, m: int, p: float, candidates=None, reps: int = 3, store: bool = True) -> dict:
+    """Time each (P, threads, splits) candidate on a context whose descriptors
+    are computed; leave the best in place and return it."""
+    results = []
+    for P, tpb, splits in candidates or SINGLE_CANDIDATES:
+        scgr.scgr_set_tuning(ctx, scgr.SCGR_TUNE_FORCE_P, P)
+        scgr.scgr_set_tuning(ctx, scgr.SCGR_TUNE_FORCE_TPB, tpb)
+        scgr.scgr_set_tuning(ctx, scgr.SCGR_TUNE_FORCE_SPLITS, splits)
+        results.append((time_forces(ctx, m, reps), P, tpb, splits, scgr.scgr_get_plan(ctx)))
+    results.sort(key=lambda r: r[0])
+    best_ms, P, tpb, splits, plan = results[0]
+    scgr.scgr_set_tuning(ctx, scgr.SCGR_TUNE_FORCE_P, P)
+    scgr.scgr_set_tuning(ctx, scgr.SCGR_TUNE_FORCE_TPB, tpb)
+    scgr.scgr_set_tuning(ctx, scgr.SCGR_TUNE_FORCE_SPLITS, splits)
+    best = {"P": P, "tpb": tpb, "splits": splits, "ms": best_ms, "plan": plan,
+            "tried": [{"P": r[1], "tpb": r[2], "splits": r[3], "ms": r[0]} for r in results],
+            "when": time.strftime("%Y-%m-%d %H:%M:%S")}
+    if store:
+        _store(single_key(gpu_name(), n, m, p), best)
+    return best
+
+
+def tune_batch(ctx, ref_off, ref_xyz, tmp_off, tmp_xyz, p: float, iterations: int = 3, store: bool = True) -> dict:
+    """Time scgr_batch_run for each work-item chunk length; leave the best."""
+    import numpy as np
+    import torch
+    ro = np.asarray(ref_off, dtype=np.int64)
+    to = np.asarray(tmp_off, dtype=np.int64)
+    work = int(np.sum(np.diff(ro) * np.diff(to)))
+    results = []
+    for ct in BATCH_CHUNKS:
+        scgr.scgr_set_tuning(ctx, scgr.SCGR_TUNE_BATCH_CHUNK_TILES, ct)
+        scgr.scgr_batch_run(ctx, ro, ref_xyz, to, tmp_xyz, 1)           # warm
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        scgr.scgr_batch_run(ctx, ro, ref_xyz, to, tmp_xyz, iterations)
+        results.append((time.perf_counter() - t0, ct))
+    results.sort()
+    best_s, ct = results[0]
+    scgr.scgr_set_tuning(ctx, scgr.SCGR_TUNE_BATCH_CHUNK_TILES, ct)
+    best = {"chunk_tiles": ct, "s": best_s, "iterations": iterations,
+            "tried": [{"chunk_tiles": c, "s": t} for t, c in results], "when": time.strftime("%Y-%m-%d %H:%M:%S")}
+    if store:
+        _store(batch_key(gpu_name(), len(ro) - 1, work, p), best)
+    return best
+
+
+def apply_cached_single(ctx, n: int, m: int, p: float) -> dict | None:
+    hit = _load().get(single_key(gpu_name(), n, m, p))
+    if hit:
+        scgr.scgr_set_tuning(ctx, scgr.SCGR_TUNE_FORCE_P, hit["P"])
+        scgr.scgr_set_tuning(ctx, scgr.SCGR_TUNE_FORCE_TPB, hit["tpb"])
+        scgr.scgr_set_tuning(ctx, scgr.SCGR_TUNE_FORCE_SPLITS, hit["splits"])
+    return hit
+
+
+def apply_cached_batch(ctx, npairs: int, work: int, p: float) -> dict | None:
+    hit = _load().get(batch_key(gpu_name(), npairs, work, p))
+    if hit:
+        scgr.scgr_set_tuning(ctx, scgr.SCGR_TUNE_BATCH_CHUNK_TILES, hit["chunk_tiles"])
+    return hit

@@ -7,6 +7,7 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <algorithm>
 #include <string>
 #include <vector>
 
@@ -33,6 +34,7 @@ struct scgr_ctx {
   int num_sms = 0;
   std::string err;
   int64_t n = 0, m = 0, npad = 0, mpad = 0;
+  int64_t row0 = 0, rows = -1;  // template rows whose forces this context computes (rows < 0: all)
   bool have_X = false, have_Y = false, have_desc = false;
   int E_host = 0;          // Eq. 12 horizon in use (0: not fixed yet)
   int iterations = 0;      // iterations enqueued since the descriptors
@@ -43,6 +45,8 @@ struct scgr_ctx {
   DevBuf X4, Y4, stage, knnX, knnY, aX64, aY64, aX32, aY32, Xr, XA, Y0r, partial, blockpart,
       moved_stage;
   DevPose* pose = nullptr;
+  DevPose* pose_eval = nullptr;  // pose of a potential / gradient evaluation
+  double* aux = nullptr;         // [0,13) forward sums, [16,29) adjoint sums, [32,39) grad7, [48,55) pose7
   DevStats* stats = nullptr;
   int* errword = nullptr;
   double* red = nullptr;   // reduction scratch
@@ -53,6 +57,17 @@ struct scgr_ctx {
   bool capturing = false;
   cudaStream_t cap_stream = nullptr;  // capture / replay stream (never the legacy stream)
   cudaEvent_t join_in = nullptr, join_out = nullptr;
+
+  // batch workspace
+  DevBuf bX4, bY4, bknnX, bknnY, baX64, baY64, baX32, baY32, bXr, bXA, bY0r, bpartial, bblockpart,
+      bpairs, bitems, bcpair, btabX, btabY, bxoff, byoff, bstats, bposes;
+  int batch_chunk_tiles = 16;   // reference tiles per batched work item (tunable)
+  int64_t knn_grid_min = 65536; // clouds with at least this many points use the grid kNN (tunable)
+  ForceTuning ftune;            // force-plan overrides (tunable)
+  int reuse_pose_free = 1;      // p = 1: one force pass per scgr_run (tunable)
+  DevBuf gcell, gcount, gstart, gcursor, gblock, gsorted, gsidx, gbb;
+  cudaGraph_t bgraph = nullptr;
+  cudaGraphExec_t bgexec = nullptr;
 
   // force-kernel timing (diagnostic)
   bool timing = false;
@@ -196,12 +211,66 @@ scgr_status collect_timing(scgr_ctx* c) {
   return SCGR_OK;
 }
 
+// k nearest neighbours of one cloud: brute force below knn_grid_min points,
+// the exact grid search above (one host synchronisation for the box).
+scgr_status knn_cloud(scgr_ctx* c, const float4* P, int n, int32_t* out) {
+  const int k = c->prm.k;
+  if ((int64_t)n < c->knn_grid_min) {
+    SCGR_CK(c, launch_knn(c->L(), P, n, k, out));
+    return SCGR_OK;
+  }
+  SCGR_CK(c, ensure(c->gbb, sizeof(float) * (256 * 6 + 8)));
+  float* part = (float*)c->gbb.p;
+  SCGR_CK(c, launch_bbox(c->L(), P, n, part, part + 256 * 6));
+  float bb[6];
+  SCGR_CK(c, cudaMemcpyAsync(bb, part + 256 * 6, sizeof(bb), cudaMemcpyDeviceToHost, c->stream));
+  SCGR_CK(c, cudaStreamSynchronize(c->stream));
+  const GridSpec gs = make_grid_spec(bb, n);
+  const int64_t ncell = grid_cells(gs);
+  SCGR_CK(c, ensure(c->gcell, (size_t)n * sizeof(int)));
+  SCGR_CK(c, ensure(c->gcount, (size_t)ncell * sizeof(int)));
+  SCGR_CK(c, ensure(c->gcursor, (size_t)ncell * sizeof(int)));
+  SCGR_CK(c, ensure(c->gstart, (size_t)(ncell + 1) * sizeof(int)));
+  SCGR_CK(c, ensure(c->gblock, (size_t)((ncell + 1023) / 1024 + 1) * sizeof(int)));
+  SCGR_CK(c, ensure(c->gsorted, (size_t)n * sizeof(float4)));
+  SCGR_CK(c, ensure(c->gsidx, (size_t)n * sizeof(int)));
+  SCGR_CK(c, launch_knn_grid(c->L(), P, n, k, gs, (int*)c->gcell.p, (int*)c->gcount.p, (int*)c->gstart.p,
+                             (int*)c->gcursor.p, (int*)c->gblock.p, (float4*)c->gsorted.p, (int*)c->gsidx.p, out));
+  return SCGR_OK;
+}
+
+void drop_graph(scgr_ctx* c);
+
+// Recompute the force plan (after a tuning change) and the buffers and
+// template records that depend on it; descriptors and pose are kept.
+scgr_status replan(scgr_ctx* c) {
+  const int64_t mloc = c->rows >= 0 ? c->rows : c->m;
+  c->fp = plan_force(mloc, c->npad, c->prm.p, c->num_sms, c->ftune);
+  c->mpad = force_mpad(mloc, c->fp);
+  SCGR_CK(c, ensure(c->Y0r, (size_t)c->mpad * sizeof(float4)));
+  SCGR_CK(c, ensure(c->partial, (size_t)c->fp.splits * c->mpad * sizeof(float4)));
+  SCGR_CK(c, ensure(c->blockpart, (size_t)combine_blocks(c->mpad) * 13 * sizeof(double)));
+  SCGR_CK(c, launch_records(c->L(), (const float4*)c->X4.p, (const double*)c->aX64.p, (int)c->n, (int)c->npad,
+                            (const float4*)c->Y4.p + c->row0, (const double*)c->aY64.p + c->row0, (int)mloc,
+                            (int)c->mpad, c->prm.g_mode, c->stats, (float4*)c->Xr.p, (float2*)c->XA.p,
+                            (float4*)c->Y0r.p));
+  drop_graph(c);
+  return SCGR_OK;
+}
+
+// For p = 1 the pair weight aX s_ij d^0 does not depend on the pose, so the
+// force kernel's per-split sums (sum w, sum w X') are the same in every
+// iteration: the first iteration of a run computes them and the others reuse
+// them (bit-identical results, O(M) work per later iteration).
 scgr_status enqueue_iterations(scgr_ctx* c, int iters) {
   const int nb = combine_blocks(c->mpad);
   const StepParams sp = step_params(c);
+  const bool pose_free = c->fp.pmode == 1 && c->reuse_pose_free;
   for (int t = 0; t < iters; ++t) {
-    scgr_status fs = force_launch(c);
-    if (fs != SCGR_OK) return fs;
+    if (!(pose_free && t > 0)) {
+      scgr_status fs = force_launch(c);
+      if (fs != SCGR_OK) return fs;
+    }
     SCGR_CK(c, launch_combine(c->L(), (const float4*)c->partial.p, c->fp.splits, (int)c->mpad, (int)c->m,
                               (const float4*)c->Y0r.p, (const double*)c->aY64.p, c->prm.g_mode, c->pose,
                               nullptr, (double*)c->blockpart.p));
@@ -253,6 +322,8 @@ scgr_status scgr_create(const scgr_params* params, void* cuda_stream, scgr_ctx**
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
   if (e == cudaSuccess) e = cudaMalloc((void**)&c->pose, sizeof(DevPose));
   if (e == cudaSuccess) e = cudaMalloc((void**)&c->stats, sizeof(DevStats));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&c->pose_eval, sizeof(DevPose));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&c->aux, sizeof(double) * 64);
   if (e == cudaSuccess) e = cudaMalloc((void**)&c->errword, sizeof(int));
   if (e == cudaSuccess) e = cudaMalloc((void**)&c->red, sizeof(double) * (RED_MAX_BLOCKS * 6 + 32));
   if (e == cudaSuccess) e = cudaMemsetAsync(c->errword, 0, sizeof(int), c->stream);
@@ -282,10 +353,18 @@ void scgr_destroy(scgr_ctx* c) {
   }
   if (c->join_in) cudaEventDestroy(c->join_in);
   if (c->join_out) cudaEventDestroy(c->join_out);
+  if (c->bgexec) cudaGraphExecDestroy(c->bgexec);
+  if (c->bgraph) cudaGraphDestroy(c->bgraph);
   DevBuf* bufs[] = {&c->X4, &c->Y4, &c->stage, &c->knnX, &c->knnY, &c->aX64, &c->aY64, &c->aX32,
-                    &c->aY32, &c->Xr, &c->XA, &c->Y0r, &c->partial, &c->blockpart, &c->moved_stage};
+                    &c->aY32, &c->Xr, &c->XA, &c->Y0r, &c->partial, &c->blockpart, &c->moved_stage,
+                    &c->bX4, &c->bY4, &c->bknnX, &c->bknnY, &c->baX64, &c->baY64, &c->baX32, &c->baY32,
+                    &c->bXr, &c->bXA, &c->bY0r, &c->bpartial, &c->bblockpart, &c->bpairs, &c->bitems,
+                    &c->bcpair, &c->btabX, &c->btabY, &c->bxoff, &c->byoff, &c->bstats, &c->bposes,
+                    &c->gcell, &c->gcount, &c->gstart, &c->gcursor, &c->gblock, &c->gsorted, &c->gsidx, &c->gbb};
   for (DevBuf* b : bufs) release(*b);
   if (c->pose) cudaFree(c->pose);
+  if (c->pose_eval) cudaFree(c->pose_eval);
+  if (c->aux) cudaFree(c->aux);
   if (c->stats) cudaFree(c->stats);
   if (c->errword) cudaFree(c->errword);
   if (c->red) cudaFree(c->red);
@@ -326,8 +405,10 @@ scgr_status scgr_compute_descriptors(scgr_ctx* c) {
   Launch L = c->L();
   const float4* X4 = (const float4*)c->X4.p;
   const float4* Y4 = (const float4*)c->Y4.p;
-  SCGR_CK(c, launch_knn(L, X4, n, k, (int32_t*)c->knnX.p));
-  SCGR_CK(c, launch_knn(L, Y4, m, k, (int32_t*)c->knnY.p));
+  scgr_status ks = knn_cloud(c, X4, n, (int32_t*)c->knnX.p);
+  if (ks != SCGR_OK) return ks;
+  ks = knn_cloud(c, Y4, m, (int32_t*)c->knnY.p);
+  if (ks != SCGR_OK) return ks;
   SCGR_CK(c, launch_curvature(L, X4, (const int32_t*)c->knnX.p, n, k, (double*)c->aX64.p, (float*)c->aX32.p));
   SCGR_CK(c, launch_curvature(L, Y4, (const int32_t*)c->knnY.p, m, k, (double*)c->aY64.p, (float*)c->aY32.p));
   DevStats* st = c->stats;
@@ -335,15 +416,17 @@ scgr_status scgr_compute_descriptors(scgr_ctx* c) {
   SCGR_CK(c, launch_cloud_stats(L, Y4, m, c->red, st->ybar0, st->S0, &st->eY0));
   SCGR_CK(c, launch_sigma(L, (const double*)c->aX64.p, n, c->prm.sigma, c->red, &st->sigma, &st->asum[0]));
   c->npad = (c->n + 255) / 256 * 256;
-  c->fp = plan_force(c->m, c->npad, c->prm.p, c->num_sms);
-  c->mpad = force_mpad(c->m, c->fp);
+  const int64_t mloc = c->rows >= 0 ? c->rows : c->m;
+  c->fp = plan_force(mloc, c->npad, c->prm.p, c->num_sms, c->ftune);
+  c->mpad = force_mpad(mloc, c->fp);
   SCGR_CK(c, ensure(c->Xr, (size_t)c->npad * sizeof(float4)));
   SCGR_CK(c, ensure(c->XA, (size_t)c->npad * sizeof(float2)));
   SCGR_CK(c, ensure(c->Y0r, (size_t)c->mpad * sizeof(float4)));
   SCGR_CK(c, ensure(c->partial, (size_t)c->fp.splits * c->mpad * sizeof(float4)));
   SCGR_CK(c, ensure(c->blockpart, (size_t)combine_blocks(c->mpad) * 13 * sizeof(double)));
-  SCGR_CK(c, launch_records(L, X4, (const double*)c->aX64.p, n, (int)c->npad, Y4, (const double*)c->aY64.p, m,
-                            (int)c->mpad, c->prm.g_mode, st, (float4*)c->Xr.p, (float2*)c->XA.p, (float4*)c->Y0r.p));
+  SCGR_CK(c, launch_records(L, X4, (const double*)c->aX64.p, n, (int)c->npad, Y4 + c->row0,
+                            (const double*)c->aY64.p + c->row0, (int)mloc, (int)c->mpad, c->prm.g_mode, st,
+                            (float4*)c->Xr.p, (float2*)c->XA.p, (float4*)c->Y0r.p));
   c->E_host = c->prm.E > 0 ? c->prm.E : 0;
   SCGR_CK(c, launch_pose_init(L, c->pose, st, c->E_host));
   c->iterations = 0;
@@ -356,6 +439,7 @@ scgr_status scgr_run(scgr_ctx* c, int iters) {
   c->err.clear();
   if (iters < 0) return fail(c, SCGR_ERR_INVALID_ARG, "iterations < 0");
   if (!c->have_desc) return fail(c, SCGR_ERR_STATE, "compute descriptors first");
+  if (c->rows >= 0) return fail(c, SCGR_ERR_STATE, "a row range is set: iterate with scgr_step_partials/scgr_step_apply");
   if (iters == 0) return SCGR_OK;
   if (c->E_host <= 0) {
     c->E_host = iters;
@@ -395,7 +479,7 @@ scgr_status scgr_run(scgr_ctx* c, int iters) {
     SCGR_CK(c, cudaGraphLaunch(c->gexec, c->cap_stream));
     SCGR_CK(c, cudaEventRecord(c->join_out, c->cap_stream));
     SCGR_CK(c, cudaStreamWaitEvent(c->stream, c->join_out, 0));
-    c->launches += 3 * (int64_t)iters;
+    c->launches += (c->fp.pmode == 1 && c->reuse_pose_free) ? 2 * (int64_t)iters + 1 : 3 * (int64_t)iters;
   } else {
     scgr_status st = enqueue_iterations(c, iters);
     if (st != SCGR_OK) return st;
@@ -486,8 +570,9 @@ scgr_status scgr_forces(scgr_ctx* c, float* f4_dev) {
   if (!c->have_desc) return fail(c, SCGR_ERR_STATE, "compute descriptors first");
   scgr_status fs = force_launch(c);
   if (fs != SCGR_OK) return fs;
-  SCGR_CK(c, launch_combine(c->L(), (const float4*)c->partial.p, c->fp.splits, (int)c->mpad, (int)c->m,
-                            (const float4*)c->Y0r.p, (const double*)c->aY64.p, c->prm.g_mode, c->pose,
+  const int mloc = (int)(c->rows >= 0 ? c->rows : c->m);
+  SCGR_CK(c, launch_combine(c->L(), (const float4*)c->partial.p, c->fp.splits, (int)c->mpad, mloc,
+                            (const float4*)c->Y0r.p, (const double*)c->aY64.p + c->row0, c->prm.g_mode, c->pose,
                             (float4*)f4_dev, (double*)c->blockpart.p));
   return SCGR_OK;
 }
@@ -581,6 +666,319 @@ scgr_status scgr_set_state(scgr_ctx* c, const scgr_state* in) {
   SCGR_CK(c, cudaStreamSynchronize(c->stream));
   drop_graph(c);
   return SCGR_OK;
+}
+
+scgr_status scgr_potential(scgr_ctx* c, const double pose7[7], double* U_out, double* grad_pose7,
+                           float* grad_xyz_dev) {
+  if (!c || !pose7 || !U_out) return fail(c, SCGR_ERR_INVALID_ARG, "NULL argument");
+  c->err.clear();
+  if (!c->have_desc) return fail(c, SCGR_ERR_STATE, "compute descriptors first");
+  for (int q = 0; q < 7; ++q)
+    if (!std::isfinite(pose7[q])) return fail(c, SCGR_ERR_INVALID_ARG, "non-finite pose");
+  if (!(pose7[6] > 0.0)) return fail(c, SCGR_ERR_INVALID_ARG, "scale must be > 0");
+  if (c->rows >= 0) return fail(c, SCGR_ERR_STATE, "the potential needs the whole template (a row range is set)");
+  Launch L = c->L();
+  double* d7 = c->aux + 48;
+  SCGR_CK(c, cudaMemcpyAsync(d7, pose7, 7 * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  SCGR_CK(c, launch_pose_from7(L, d7, c->pose_eval, c->stats));
+  const int ntiles = (int)(c->npad / c->fp.tile_j);
+  const int nb = combine_blocks(c->mpad);
+  // forward: the force kernel with the distance exponent p + 1 accumulates
+  // sum_j g d^(p+1); U = sum_i aY_i (that sum) / (p + 1)
+  ForcePlan fu = c->fp;
+  const double eU = c->prm.p + 1.0;
+  fu.pmode = (eU == 2.0) ? 3 : 0;
+  SCGR_CK(c, launch_force(L, fu, (const float4*)c->Xr.p, (const float2*)c->XA.p, ntiles, (const float4*)c->Y0r.p,
+                          (int)c->mpad, c->pose_eval, (float)(0.5 * eU), (float4*)c->partial.p));
+  SCGR_CK(c, launch_combine(L, (const float4*)c->partial.p, fu.splits, (int)c->mpad, (int)c->m,
+                            (const float4*)c->Y0r.p, (const double*)c->aY64.p, c->prm.g_mode, c->pose_eval,
+                            nullptr, (double*)c->blockpart.p));
+  SCGR_CK(c, launch_column_sum13(L, (const double*)c->blockpart.p, nb, c->aux));
+  if (grad_pose7 || grad_xyz_dev) {
+    // adjoint: recompute the pair tiles at the same pose for G_i = -f_i
+    SCGR_CK(c, launch_force(L, c->fp, (const float4*)c->Xr.p, (const float2*)c->XA.p, ntiles,
+                            (const float4*)c->Y0r.p, (int)c->mpad, c->pose_eval, c->qexp, (float4*)c->partial.p));
+    SCGR_CK(c, launch_adjoint_combine(L, (const float4*)c->partial.p, c->fp.splits, (int)c->mpad, (int)c->m,
+                                      (const float4*)c->Y0r.p, (const double*)c->aY64.p, c->prm.g_mode,
+                                      c->pose_eval, grad_xyz_dev, (double*)c->blockpart.p));
+    SCGR_CK(c, launch_column_sum13(L, (const double*)c->blockpart.p, nb, c->aux + 16));
+    SCGR_CK(c, launch_adjoint_finish(L, c->aux + 16, d7, c->pose_eval, c->aux + 32));
+  }
+  double h[40];
+  SCGR_CK(c, cudaMemcpyAsync(h, c->aux, 40 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  SCGR_CK(c, cudaStreamSynchronize(c->stream));
+  *U_out = h[3] / eU;
+  if (grad_pose7)
+    for (int q = 0; q < 7; ++q) grad_pose7[q] = h[32 + q];
+  return read_error_word(c);
+}
+
+scgr_status scgr_set_row_range(scgr_ctx* c, int64_t row0, int64_t rows) {
+  if (!c) return SCGR_ERR_INVALID_ARG;
+  c->err.clear();
+  if (!c->have_Y) return fail(c, SCGR_ERR_STATE, "set the template first");
+  if (row0 < 0 || rows < 1 || row0 + rows > c->m) return fail(c, SCGR_ERR_INVALID_ARG, "row range outside the template");
+  c->row0 = row0;
+  c->rows = rows;
+  c->have_desc = false;
+  return SCGR_OK;
+}
+
+scgr_status scgr_step_partials(scgr_ctx* c, double out13[13]) {
+  if (!c || !out13) return fail(c, SCGR_ERR_INVALID_ARG, "NULL argument");
+  c->err.clear();
+  if (!c->have_desc) return fail(c, SCGR_ERR_STATE, "compute descriptors first");
+  if (c->E_host <= 0) return fail(c, SCGR_ERR_STATE, "set params.E for stepwise iteration");
+  const int mloc = (int)(c->rows >= 0 ? c->rows : c->m);
+  scgr_status fs = force_launch(c);
+  if (fs != SCGR_OK) return fs;
+  SCGR_CK(c, launch_combine(c->L(), (const float4*)c->partial.p, c->fp.splits, (int)c->mpad, mloc,
+                            (const float4*)c->Y0r.p, (const double*)c->aY64.p + c->row0, c->prm.g_mode, c->pose,
+                            nullptr, (double*)c->blockpart.p));
+  SCGR_CK(c, launch_column_sum13(c->L(), (const double*)c->blockpart.p, combine_blocks(c->mpad), c->aux));
+  SCGR_CK(c, cudaMemcpyAsync(out13, c->aux, 13 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  SCGR_CK(c, cudaStreamSynchronize(c->stream));
+  return read_error_word(c);
+}
+
+scgr_status scgr_step_apply(scgr_ctx* c, const double tot13[13]) {
+  if (!c || !tot13) return fail(c, SCGR_ERR_INVALID_ARG, "NULL argument");
+  c->err.clear();
+  if (!c->have_desc) return fail(c, SCGR_ERR_STATE, "compute descriptors first");
+  if (c->E_host <= 0) return fail(c, SCGR_ERR_STATE, "set params.E for stepwise iteration");
+  for (int q = 0; q < 13; ++q)
+    if (!std::isfinite(tot13[q])) return fail(c, SCGR_ERR_INVALID_ARG, "non-finite totals");
+  SCGR_CK(c, cudaMemcpyAsync(c->aux + 16, tot13, 13 * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  SCGR_CK(c, launch_finalize(c->L(), c->aux + 16, 1, c->pose, c->stats, step_params(c), c->errword));
+  SCGR_CK(c, cudaStreamSynchronize(c->stream));
+  c->iterations += 1;
+  return read_error_word(c);
+}
+
+scgr_status scgr_get_plan(scgr_ctx* c, int out[4]) {
+  if (!c || !out) return fail(c, SCGR_ERR_INVALID_ARG, "NULL argument");
+  c->err.clear();
+  if (!c->have_desc) return fail(c, SCGR_ERR_STATE, "compute descriptors first");
+  out[0] = c->fp.P;
+  out[1] = c->fp.tpb;
+  out[2] = c->fp.splits;
+  out[3] = c->fp.iblocks;
+  return SCGR_OK;
+}
+
+scgr_status scgr_set_tuning(scgr_ctx* c, int key, int value) {
+  if (!c) return SCGR_ERR_INVALID_ARG;
+  c->err.clear();
+  if (key == SCGR_TUNE_FORCE_P) {
+    if (value != 0 && value != 1 && value != 2 && value != 4) return fail(c, SCGR_ERR_INVALID_ARG, "P must be 0, 1, 2 or 4");
+    c->ftune.P = value;
+    return c->have_desc ? replan(c) : SCGR_OK;
+  }
+  if (key == SCGR_TUNE_FORCE_TPB) {
+    if (value != 0 && value != 128 && value != 256) return fail(c, SCGR_ERR_INVALID_ARG, "threads per block must be 0, 128 or 256");
+    c->ftune.tpb = value;
+    return c->have_desc ? replan(c) : SCGR_OK;
+  }
+  if (key == SCGR_TUNE_FORCE_SPLITS) {
+    if (value < 0 || value > 4096) return fail(c, SCGR_ERR_INVALID_ARG, "splits must be in [0, 4096]");
+    c->ftune.splits = value;
+    return c->have_desc ? replan(c) : SCGR_OK;
+  }
+  if (key == SCGR_TUNE_REUSE_POSE_FREE) {
+    if (value != 0 && value != 1) return fail(c, SCGR_ERR_INVALID_ARG, "value must be 0 or 1");
+    c->reuse_pose_free = value;
+    drop_graph(c);
+    return SCGR_OK;
+  }
+  if (key == SCGR_TUNE_KNN_GRID_MIN) {
+    if (value < 0) return fail(c, SCGR_ERR_INVALID_ARG, "grid threshold must be >= 0");
+    c->knn_grid_min = value;
+    return SCGR_OK;
+  }
+  if (key == SCGR_TUNE_BATCH_CHUNK_TILES) {
+    if (value < 1 || value > 4096) return fail(c, SCGR_ERR_INVALID_ARG, "chunk tiles must be in [1, 4096]");
+    c->batch_chunk_tiles = value;
+    return SCGR_OK;
+  }
+  return fail(c, SCGR_ERR_INVALID_ARG, "unknown tuning key");
+}
+
+scgr_status scgr_batch_run(scgr_ctx* c, int npairs, const int64_t* ref_off, const float* ref_xyz_dev,
+                           const int64_t* tmp_off, const float* tmp_xyz_dev, int iterations,
+                           scgr_result* results) {
+  if (!c) return SCGR_ERR_INVALID_ARG;
+  c->err.clear();
+  if (npairs < 1 || !ref_off || !tmp_off || !ref_xyz_dev || !tmp_xyz_dev || !results)
+    return fail(c, SCGR_ERR_INVALID_ARG, "NULL argument or npairs < 1");
+  if (iterations < 0) return fail(c, SCGR_ERR_INVALID_ARG, "iterations < 0");
+  const int k = c->prm.k;
+  if (ref_off[0] != 0 || tmp_off[0] != 0) return fail(c, SCGR_ERR_INVALID_ARG, "offsets must start at 0");
+  for (int p = 0; p < npairs; ++p) {
+    if (ref_off[p + 1] - ref_off[p] < k) return fail(c, SCGR_ERR_INVALID_ARG, "a reference has fewer than k points");
+    if (tmp_off[p + 1] - tmp_off[p] < std::max(k, 3)) return fail(c, SCGR_ERR_INVALID_ARG, "a template has fewer than max(k, 3) points");
+  }
+  const int64_t Ntot = ref_off[npairs], Mtot = tmp_off[npairs];
+  if (Ntot >= (int64_t(1) << 30) || Mtot >= (int64_t(1) << 30)) return fail(c, SCGR_ERR_INVALID_ARG, "too many points");
+
+  // ---- host plan: per-pair geometry, work items (longest first), tables
+  const int CT = c->batch_chunk_tiles;
+  const int FB = 128;  // template points per batched force block
+  std::vector<BatchPair> pairs(npairs);
+  std::vector<int4> items;
+  std::vector<int> cpair;
+  std::vector<int2> tabX, tabY;
+  int64_t xt = 0, yb = 0, pb = 0;
+  int cb = 0;
+  for (int p = 0; p < npairs; ++p) {
+    BatchPair& bp = pairs[p];
+    bp.x0 = ref_off[p];
+    bp.n = ref_off[p + 1] - ref_off[p];
+    bp.y0 = tmp_off[p];
+    bp.m = tmp_off[p + 1] - tmp_off[p];
+    bp.ntiles = (int)((bp.n + FORCE_TJ - 1) / FORCE_TJ);
+    bp.xtile0 = xt;
+    xt += bp.ntiles;
+    bp.mpad = (bp.m + 255) / 256 * 256;
+    bp.ybase = yb;
+    yb += bp.mpad;
+    bp.chunks = (bp.ntiles + CT - 1) / CT;
+    bp.pbase = pb;
+    pb += (int64_t)bp.chunks * bp.mpad;
+    bp.cblk0 = cb;
+    bp.ncblk = (int)(bp.mpad / 256);
+    cb += bp.ncblk;
+    for (int q = 0; q < bp.ncblk; ++q) cpair.push_back(p);
+    const int fblocks = (int)((bp.m + FB - 1) / FB);
+    for (int b = 0; b < fblocks; ++b)
+      for (int ch = 0; ch < bp.chunks; ++ch) {
+        const int tiles = std::min(CT, bp.ntiles - ch * CT);
+        const int pts = (int)std::min<int64_t>(FB, bp.m - (int64_t)b * FB);
+        items.push_back(make_int4(p, b, ch, tiles * pts));
+      }
+    for (int64_t q0 = 0; q0 < bp.n; q0 += 128) tabX.push_back(make_int2(p, (int)q0));
+    for (int64_t q0 = 0; q0 < bp.m; q0 += 128) tabY.push_back(make_int2(p, (int)q0));
+  }
+  std::stable_sort(items.begin(), items.end(), [](const int4& a, const int4& b) { return a.w > b.w; });
+  std::vector<int64_t> xoff(ref_off, ref_off + npairs + 1), yoff(tmp_off, tmp_off + npairs + 1);
+
+  // ---- device buffers
+  SCGR_CK(c, ensure(c->bX4, (size_t)Ntot * sizeof(float4)));
+  SCGR_CK(c, ensure(c->bY4, (size_t)Mtot * sizeof(float4)));
+  SCGR_CK(c, ensure(c->bknnX, (size_t)Ntot * k * sizeof(int32_t)));
+  SCGR_CK(c, ensure(c->bknnY, (size_t)Mtot * k * sizeof(int32_t)));
+  SCGR_CK(c, ensure(c->baX64, (size_t)Ntot * sizeof(double)));
+  SCGR_CK(c, ensure(c->baY64, (size_t)Mtot * sizeof(double)));
+  SCGR_CK(c, ensure(c->baX32, (size_t)Ntot * sizeof(float)));
+  SCGR_CK(c, ensure(c->baY32, (size_t)Mtot * sizeof(float)));
+  SCGR_CK(c, ensure(c->bXr, (size_t)xt * FORCE_TJ * sizeof(float4)));
+  SCGR_CK(c, ensure(c->bXA, (size_t)xt * FORCE_TJ * sizeof(float2)));
+  SCGR_CK(c, ensure(c->bY0r, (size_t)yb * sizeof(float4)));
+  SCGR_CK(c, ensure(c->bpartial, (size_t)pb * sizeof(float4)));
+  SCGR_CK(c, ensure(c->bblockpart, (size_t)cb * 13 * sizeof(double)));
+  SCGR_CK(c, ensure(c->bpairs, pairs.size() * sizeof(BatchPair)));
+  SCGR_CK(c, ensure(c->bitems, items.size() * sizeof(int4)));
+  SCGR_CK(c, ensure(c->bcpair, cpair.size() * sizeof(int)));
+  SCGR_CK(c, ensure(c->btabX, tabX.size() * sizeof(int2)));
+  SCGR_CK(c, ensure(c->btabY, tabY.size() * sizeof(int2)));
+  SCGR_CK(c, ensure(c->bxoff, xoff.size() * sizeof(int64_t)));
+  SCGR_CK(c, ensure(c->byoff, yoff.size() * sizeof(int64_t)));
+  SCGR_CK(c, ensure(c->bstats, (size_t)npairs * sizeof(DevStats)));
+  SCGR_CK(c, ensure(c->bposes, (size_t)npairs * sizeof(DevPose)));
+  cudaStream_t st = c->stream;
+  SCGR_CK(c, cudaMemcpyAsync(c->bpairs.p, pairs.data(), pairs.size() * sizeof(BatchPair), cudaMemcpyHostToDevice, st));
+  SCGR_CK(c, cudaMemcpyAsync(c->bitems.p, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice, st));
+  SCGR_CK(c, cudaMemcpyAsync(c->bcpair.p, cpair.data(), cpair.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+  SCGR_CK(c, cudaMemcpyAsync(c->btabX.p, tabX.data(), tabX.size() * sizeof(int2), cudaMemcpyHostToDevice, st));
+  SCGR_CK(c, cudaMemcpyAsync(c->btabY.p, tabY.data(), tabY.size() * sizeof(int2), cudaMemcpyHostToDevice, st));
+  SCGR_CK(c, cudaMemcpyAsync(c->bxoff.p, xoff.data(), xoff.size() * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+  SCGR_CK(c, cudaMemcpyAsync(c->byoff.p, yoff.data(), yoff.size() * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+
+  // ---- descriptors for every cloud, in one launch per stage
+  Launch L = c->L();
+  const BatchPair* dpairs = (const BatchPair*)c->bpairs.p;
+  SCGR_CK(c, launch_pack(L, ref_xyz_dev, Ntot, (float4*)c->bX4.p, c->errword));
+  SCGR_CK(c, launch_pack(L, tmp_xyz_dev, Mtot, (float4*)c->bY4.p, c->errword));
+  SCGR_CK(c, launch_knn_multi(L, (const float4*)c->bX4.p, (const int64_t*)c->bxoff.p, (const int2*)c->btabX.p,
+                              (int)tabX.size(), k, (int32_t*)c->bknnX.p));
+  SCGR_CK(c, launch_knn_multi(L, (const float4*)c->bY4.p, (const int64_t*)c->byoff.p, (const int2*)c->btabY.p,
+                              (int)tabY.size(), k, (int32_t*)c->bknnY.p));
+  SCGR_CK(c, launch_curvature(L, (const float4*)c->bX4.p, (const int32_t*)c->bknnX.p, (int)Ntot, k,
+                              (double*)c->baX64.p, (float*)c->baX32.p));
+  SCGR_CK(c, launch_curvature(L, (const float4*)c->bY4.p, (const int32_t*)c->bknnY.p, (int)Mtot, k,
+                              (double*)c->baY64.p, (float*)c->baY32.p));
+  SCGR_CK(c, launch_stats_multi(L, (const float4*)c->bX4.p, (const float4*)c->bY4.p, (const double*)c->baX64.p,
+                                dpairs, npairs, c->prm.sigma, (DevStats*)c->bstats.p));
+  SCGR_CK(c, launch_records_multi(L, (const float4*)c->bX4.p, (const double*)c->baX64.p, (const float4*)c->bY4.p,
+                                  (const double*)c->baY64.p, dpairs, npairs, c->prm.g_mode,
+                                  (const DevStats*)c->bstats.p, (float4*)c->bXr.p, (float2*)c->bXA.p,
+                                  (float4*)c->bY0r.p));
+  const int E = c->prm.E > 0 ? c->prm.E : std::max(iterations, 1);
+  SCGR_CK(c, launch_pose_init_multi(L, (DevPose*)c->bposes.p, (const DevStats*)c->bstats.p, npairs, E));
+
+  // ---- iterations: three launches per iteration for all pairs
+  StepParams sp = step_params(c);
+  const int pmode = (c->prm.p == 1.0) ? 1 : (c->prm.p == 2.0) ? 2 : (c->prm.p == 3.0) ? 3 : 0;
+  auto enqueue = [&](Launch LL) -> scgr_status {
+    for (int t = 0; t < iterations; ++t) {
+      SCGR_CK(c, launch_force_batch(LL, pmode, (int)items.size(), (const int4*)c->bitems.p, dpairs,
+                                    (const float4*)c->bXr.p, (const float2*)c->bXA.p, (const float4*)c->bY0r.p,
+                                    (const DevPose*)c->bposes.p, c->qexp, (float4*)c->bpartial.p, CT));
+      SCGR_CK(c, launch_combine_batch(LL, cb, (const int*)c->bcpair.p, dpairs, (const float4*)c->bpartial.p,
+                                      (const float4*)c->bY0r.p, (const double*)c->baY64.p, c->prm.g_mode,
+                                      (const DevPose*)c->bposes.p, (double*)c->bblockpart.p));
+      SCGR_CK(c, launch_finalize_multi(LL, (const double*)c->bblockpart.p, dpairs, npairs, (DevPose*)c->bposes.p,
+                                       (const DevStats*)c->bstats.p, sp, c->errword));
+    }
+    return SCGR_OK;
+  };
+  if (iterations > 0) {
+    if (c->prm.use_graph) {
+      if (!c->cap_stream) {
+        SCGR_CK(c, cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+        SCGR_CK(c, cudaEventCreateWithFlags(&c->join_in, cudaEventDisableTiming));
+        SCGR_CK(c, cudaEventCreateWithFlags(&c->join_out, cudaEventDisableTiming));
+      }
+      if (c->bgexec) cudaGraphExecDestroy(c->bgexec);
+      if (c->bgraph) cudaGraphDestroy(c->bgraph);
+      c->bgexec = nullptr;
+      c->bgraph = nullptr;
+      SCGR_CK(c, cudaEventRecord(c->join_in, c->stream));
+      SCGR_CK(c, cudaStreamWaitEvent(c->cap_stream, c->join_in, 0));
+      const int64_t before = c->launches;
+      cudaError_t e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
+      scgr_status stq = SCGR_OK;
+      cudaGraph_t g = nullptr;
+      if (e == cudaSuccess) {
+        stq = enqueue(Launch{c->cap_stream, &c->launches});
+        e = cudaStreamEndCapture(c->cap_stream, &g);
+      }
+      c->launches = before;
+      if (stq != SCGR_OK) { if (g) cudaGraphDestroy(g); return stq; }
+      if (e != cudaSuccess) return cuda_fail(c, e, "batch graph capture");
+      c->bgraph = g;
+      SCGR_CK(c, cudaGraphInstantiate(&c->bgexec, c->bgraph, 0));
+      SCGR_CK(c, cudaGraphLaunch(c->bgexec, c->cap_stream));
+      SCGR_CK(c, cudaEventRecord(c->join_out, c->cap_stream));
+      SCGR_CK(c, cudaStreamWaitEvent(c->stream, c->join_out, 0));
+      c->launches += 3 * (int64_t)iterations;
+    } else {
+      scgr_status stq = enqueue(L);
+      if (stq != SCGR_OK) return stq;
+    }
+  }
+
+  // ---- results
+  std::vector<DevPose> hp(npairs);
+  SCGR_CK(c, cudaMemcpyAsync(hp.data(), c->bposes.p, (size_t)npairs * sizeof(DevPose), cudaMemcpyDeviceToHost, st));
+  SCGR_CK(c, cudaStreamSynchronize(st));
+  for (int p = 0; p < npairs; ++p) {
+    std::memcpy(results[p].R, hp[p].R, sizeof(results[p].R));
+    std::memcpy(results[p].t, hp[p].t, sizeof(results[p].t));
+    results[p].s = hp[p].s;
+    results[p].iterations = hp[p].it;
+    results[p].degenerate_steps = hp[p].degenerate;
+  }
+  return read_error_word(c);
 }
 
 int64_t scgr_launch_count(const scgr_ctx* c) { return c ? c->launches : -1; }

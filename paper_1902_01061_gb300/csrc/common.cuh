@@ -122,6 +122,27 @@ __host__ __device__ inline void sym3_eigenvalues(const double* Ain, double* lam)
   lam[0] = l0; lam[1] = l1; lam[2] = l2;
 }
 
+// One registration pair of a batch: where its points, padded records,
+// partial sums and combine blocks live in the concatenated buffers.
+struct BatchPair {
+  int64_t x0, n;     // reference points [x0, x0 + n) of the concatenated reference cloud
+  int64_t y0, m;     // template points [y0, y0 + m)
+  int64_t xtile0;    // first force tile of this pair's reference records
+  int64_t ybase;     // first padded template slot
+  int64_t pbase;     // first per-chunk partial slot
+  int64_t mpad;      // padded template slots (multiple of 256)
+  int ntiles;        // reference tiles of FORCE_TJ points
+  int chunks;        // reference chunks (one partial per chunk and template point)
+  int cblk0, ncblk;  // combine blocks [cblk0, cblk0 + ncblk) of 256 template slots
+};
+
+// Uniform grid of the exact grid kNN: origin, cell edge, cells per axis.
+struct GridSpec {
+  double o[3];
+  double h, inv_h;
+  int g[3];
+};
+
 // ---- launchers (defined in the .cu files) --------------------------------
 struct Launch {
   cudaStream_t stream;
@@ -138,6 +159,19 @@ cudaError_t launch_cloud_stats(Launch L, const float4* P, int n, double* part, d
 // sigma = population std of a64 (1 if below 1e-12), or `sigma_user` if > 0
 cudaError_t launch_sigma(Launch L, const double* a64, int n, double sigma_user, double* part,
                          double* sigma_out, double* asum_out);
+cudaError_t launch_knn_multi(Launch L, const float4* P, const int64_t* off_dev, const int2* table_dev,
+                             int nblocks, int k, int32_t* out);
+cudaError_t launch_records_multi(Launch L, const float4* X4, const double* aX64, const float4* Y4,
+                                 const double* aY64, const BatchPair* pairs, int npairs, int g_mode,
+                                 const DevStats* stats, float4* Xr, float2* XA, float4* Y0r);
+cudaError_t launch_stats_multi(Launch L, const float4* X4, const float4* Y4, const double* aX64,
+                               const BatchPair* pairs, int npairs, double sigma_user, DevStats* out);
+GridSpec make_grid_spec(const float* bbox6, int64_t n);
+int64_t grid_cells(const GridSpec& gs);
+cudaError_t launch_bbox(Launch L, const float4* P, int n, float* part, float* out6);
+cudaError_t launch_knn_grid(Launch L, const float4* P, int n, int k, const GridSpec& gs, int* cell_of, int* count,
+                            int* start, int* cursor, int* block_tot, float4* sorted, int* sorted_idx,
+                            int32_t* out);
 cudaError_t launch_check_curvature(Launch L, const double* a64, int n, float* a32, int* err);
 cudaError_t launch_records(Launch L, const float4* X4, const double* aX64, int n, int npad,
                            const float4* Y4, const double* aY64, int m, int mpad, int g_mode,
@@ -157,7 +191,14 @@ struct ForcePlan {
   int iblocks;    // grid.x
 };
 
-ForcePlan plan_force(int64_t m, int64_t npad, double p, int num_sms);
+// Overrides of the force plan (0: automatic), set by the autotuner.
+struct ForceTuning {
+  int P = 0;       // template points per thread: 1, 2 or 4
+  int tpb = 0;     // threads per block: 128 or 256
+  int splits = 0;  // reference splits
+};
+
+ForcePlan plan_force(int64_t m, int64_t npad, double p, int num_sms, const ForceTuning& tune = ForceTuning());
 int64_t force_mpad(int64_t m, const ForcePlan& fp);
 
 cudaError_t launch_force(Launch L, const ForcePlan& fp, const float4* Xr, const float2* XA,
@@ -173,6 +214,15 @@ cudaError_t launch_finalize(Launch L, const double* blockpart, int nblocks, DevP
 cudaError_t launch_apply(Launch L, const float4* Y4, int m, const DevPose* pose, float* out);
 cudaError_t launch_pose_refresh(Launch L, DevPose* pose, const DevStats* stats);
 
+cudaError_t launch_force_batch(Launch L, int pmode, int nitems, const int4* items, const BatchPair* pairs,
+                               const float4* Xr, const float2* XA, const float4* Y0r, const DevPose* poses,
+                               float qexp, float4* partial, int chunk_tiles);
+cudaError_t launch_combine_batch(Launch L, int nblocks, const int* cpair, const BatchPair* pairs,
+                                 const float4* partial, const float4* Y0r, const double* aY64, int g_mode,
+                                 const DevPose* poses, double* blockpart);
+cudaError_t launch_finalize_multi(Launch L, const double* blockpart, const BatchPair* pairs, int npairs,
+                                  DevPose* poses, const DevStats* stats, StepParams sp, int* err);
+cudaError_t launch_pose_init_multi(Launch L, DevPose* poses, const DevStats* stats, int npairs, int E);
 cudaError_t launch_pose_from7(Launch L, const double* pose7_dev, DevPose* ps, const DevStats* st);
 cudaError_t launch_adjoint_combine(Launch L, const float4* partial, int S, int mpad, int m, const float4* Y0r,
                                    const double* aY64, int g_mode, const DevPose* ps, float* grad_xyz,

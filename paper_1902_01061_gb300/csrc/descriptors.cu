@@ -46,23 +46,21 @@ cudaError_t launch_pack(Launch L, const float* xyz, int64_t n, float4* out, int*
 constexpr int KNN_TPB = 128;
 constexpr int KNN_TILE = 1024;
 
+// Scan candidates P[base .. base + n) in index order for one query q held by
+// this thread; tile staging is shared by the block (all threads of the block
+// must call this with the same base and n).  Indices written are global.
 template <int KC>
-__global__ void __launch_bounds__(KNN_TPB) knn_brute_kernel(const float4* __restrict__ P, int n,
-                                                            int k, int32_t* __restrict__ out) {
-  __shared__ float4 tile[KNN_TILE];
-  const int qi = blockIdx.x * KNN_TPB + threadIdx.x;
-  const float4 q = P[qi < n ? qi : n - 1];
-  float kd[KC];
-  int ki[KC];
+__device__ __forceinline__ void knn_scan(const float4* __restrict__ P, int64_t base, int n, float4 q, float* kd,
+                                         int* ki, float4* tile) {
 #pragma unroll
   for (int m = 0; m < KC; ++m) {
     kd[m] = INFINITY;
     ki[m] = INT_MAX;
   }
-  for (int base = 0; base < n; base += KNN_TILE) {
-    const int cnt = min(KNN_TILE, n - base);
+  for (int t0 = 0; t0 < n; t0 += KNN_TILE) {
+    const int cnt = min(KNN_TILE, n - t0);
     __syncthreads();
-    for (int t = threadIdx.x; t < cnt; t += KNN_TPB) tile[t] = P[base + t];
+    for (int t = threadIdx.x; t < cnt; t += KNN_TPB) tile[t] = P[base + t0 + t];
     __syncthreads();
 #pragma unroll 4
     for (int jj = 0; jj < cnt; ++jj) {
@@ -73,7 +71,7 @@ __global__ void __launch_bounds__(KNN_TPB) knn_brute_kernel(const float4* __rest
       const float key = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
       if (key < kd[KC - 1]) {
         kd[KC - 1] = key;
-        ki[KC - 1] = base + jj;
+        ki[KC - 1] = (int)(base + t0 + jj);
 #pragma unroll
         for (int m = KC - 1; m > 0; --m) {
           if (kd[m] < kd[m - 1]) {
@@ -88,11 +86,54 @@ __global__ void __launch_bounds__(KNN_TPB) knn_brute_kernel(const float4* __rest
       }
     }
   }
+}
+
+template <int KC>
+__global__ void __launch_bounds__(KNN_TPB) knn_brute_kernel(const float4* __restrict__ P, int n,
+                                                            int k, int32_t* __restrict__ out) {
+  __shared__ float4 tile[KNN_TILE];
+  const int qi = blockIdx.x * KNN_TPB + threadIdx.x;
+  const float4 q = P[qi < n ? qi : n - 1];
+  float kd[KC];
+  int ki[KC];
+  knn_scan<KC>(P, 0, n, q, kd, ki, tile);
   if (qi < n) {
 #pragma unroll
     for (int m = 0; m < KC; ++m)
       if (m < k) out[(int64_t)qi * k + m] = ki[m];
   }
+}
+
+// Many clouds in one launch: block b handles queries [q0, q0 + KNN_TPB) of
+// cloud c = table[b].x (q0 = table[b].y), each against its own cloud only.
+template <int KC>
+__global__ void __launch_bounds__(KNN_TPB) knn_brute_multi_kernel(const float4* __restrict__ P,
+                                                                  const int64_t* __restrict__ off,
+                                                                  const int2* __restrict__ table, int k,
+                                                                  int32_t* __restrict__ out) {
+  __shared__ float4 tile[KNN_TILE];
+  const int2 e = table[blockIdx.x];
+  const int64_t base = off[e.x];
+  const int n = (int)(off[e.x + 1] - base);
+  const int ql = e.y + threadIdx.x;
+  const float4 q = P[base + (ql < n ? ql : n - 1)];
+  float kd[KC];
+  int ki[KC];
+  knn_scan<KC>(P, base, n, q, kd, ki, tile);
+  if (ql < n) {
+#pragma unroll
+    for (int m = 0; m < KC; ++m)
+      if (m < k) out[(base + ql) * k + m] = ki[m];
+  }
+}
+
+cudaError_t launch_knn_multi(Launch L, const float4* P, const int64_t* off_dev, const int2* table_dev,
+                             int nblocks, int k, int32_t* out) {
+  if (nblocks <= 0) return cudaSuccess;
+  if (k <= 8) knn_brute_multi_kernel<8><<<nblocks, KNN_TPB, 0, L.stream>>>(P, off_dev, table_dev, k, out);
+  else if (k <= 16) knn_brute_multi_kernel<16><<<nblocks, KNN_TPB, 0, L.stream>>>(P, off_dev, table_dev, k, out);
+  else knn_brute_multi_kernel<32><<<nblocks, KNN_TPB, 0, L.stream>>>(P, off_dev, table_dev, k, out);
+  return after_launch(L);
 }
 
 cudaError_t launch_knn(Launch L, const float4* P, int n, int k, int32_t* out) {
@@ -295,45 +336,152 @@ cudaError_t launch_check_curvature(Launch L, const double* a64, int n, float* a3
 // that |X'|^2 + |Y'|^2 - 2 X'.Y' loses little to cancellation.  The records
 // are written tile-major as structure-of-arrays (FORCE_TJ points per tile).
 // Padding records carry -L = +inf, so their weight is exactly 0.
+__device__ __forceinline__ void write_x_record(int i, int n, const float4* __restrict__ X4,
+                                               const double* __restrict__ aX64, int g_mode, const DevStats& st,
+                                               float* __restrict__ Xr, float* __restrict__ XA) {
+  const double kscale = sqrt(1.4426950408889634) / st.sigma;  // sqrt(log2 e) / sigma
+  const size_t t = (size_t)(i / FORCE_TJ), r = (size_t)(i % FORCE_TJ);
+  float* xr = Xr + t * 4 * FORCE_TJ + r;
+  float* xa = XA + t * 2 * FORCE_TJ + r;
+  if (i < n) {
+    const float4 c = X4[i];
+    const float x = (float)((double)c.x - st.xbar[0]);
+    const float y = (float)((double)c.y - st.xbar[1]);
+    const float z = (float)((double)c.z - st.xbar[2]);
+    const double nn = (double)x * x + (double)y * y + (double)z * z;
+    xr[0] = x;
+    xr[FORCE_TJ] = y;
+    xr[2 * FORCE_TJ] = z;
+    xr[3 * FORCE_TJ] = (float)nn;
+    const double a = aX64[i];
+    const float nL = g_mode == 1 ? (a > 0.0 ? (float)(-log2(a)) : INFINITY) : 0.f;
+    xa[0] = (float)(a * kscale);
+    xa[FORCE_TJ] = nL;
+  } else {
+    xr[0] = xr[FORCE_TJ] = xr[2 * FORCE_TJ] = xr[3 * FORCE_TJ] = 0.f;
+    xa[0] = 0.f;
+    xa[FORCE_TJ] = INFINITY;
+  }
+}
+
+__device__ __forceinline__ void write_y_record(int i, int m, const float4* __restrict__ Y4,
+                                               const double* __restrict__ aY64, const DevStats& st,
+                                               float4* __restrict__ Y0r) {
+  if (i < m) {
+    const double kscale = sqrt(1.4426950408889634) / st.sigma;
+    const float4 c = Y4[i];
+    Y0r[i] = make_float4(c.x, c.y, c.z, (float)(aY64[i] * kscale));
+  } else {
+    Y0r[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+}
+
 __global__ void records_kernel(const float4* __restrict__ X4, const double* __restrict__ aX64,
                                int n, int npad, const float4* __restrict__ Y4,
                                const double* __restrict__ aY64, int m, int mpad, int g_mode,
                                const DevStats* __restrict__ st, float* __restrict__ Xr,
                                float* __restrict__ XA, float4* __restrict__ Y0r) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const double kscale = sqrt(1.4426950408889634) / st->sigma;  // sqrt(log2 e) / sigma
-  if (i < npad) {
-    const size_t t = (size_t)(i / FORCE_TJ), r = (size_t)(i % FORCE_TJ);
-    float* xr = Xr + t * 4 * FORCE_TJ + r;
-    float* xa = XA + t * 2 * FORCE_TJ + r;
-    if (i < n) {
-      const float4 c = X4[i];
-      const float x = (float)((double)c.x - st->xbar[0]);
-      const float y = (float)((double)c.y - st->xbar[1]);
-      const float z = (float)((double)c.z - st->xbar[2]);
-      const double nn = (double)x * x + (double)y * y + (double)z * z;
-      xr[0] = x;
-      xr[FORCE_TJ] = y;
-      xr[2 * FORCE_TJ] = z;
-      xr[3 * FORCE_TJ] = (float)nn;
-      const double a = aX64[i];
-      const float nL = g_mode == 1 ? (a > 0.0 ? (float)(-log2(a)) : INFINITY) : 0.f;
-      xa[0] = (float)(a * kscale);
-      xa[FORCE_TJ] = nL;
-    } else {
-      xr[0] = xr[FORCE_TJ] = xr[2 * FORCE_TJ] = xr[3 * FORCE_TJ] = 0.f;
-      xa[0] = 0.f;
-      xa[FORCE_TJ] = INFINITY;
+  if (i < npad) write_x_record(i, n, X4, aX64, g_mode, *st, Xr, XA);
+  if (i < mpad) write_y_record(i, m, Y4, aY64, *st, Y0r);
+}
+
+// Batched records: block (p, part) writes pair p's padded reference tiles and
+// template slots (grid-strided over `part`).
+__global__ void records_multi_kernel(const float4* __restrict__ X4, const double* __restrict__ aX64,
+                                     const float4* __restrict__ Y4, const double* __restrict__ aY64,
+                                     const BatchPair* __restrict__ pairs, int g_mode,
+                                     const DevStats* __restrict__ st, float* __restrict__ Xr,
+                                     float* __restrict__ XA, float4* __restrict__ Y0r) {
+  const BatchPair bp = pairs[blockIdx.x];
+  const DevStats& S = st[blockIdx.x];
+  const int stride = blockDim.x * gridDim.y;
+  const int npad = bp.ntiles * FORCE_TJ;
+  for (int i = blockIdx.y * blockDim.x + threadIdx.x; i < npad; i += stride)
+    write_x_record(i, (int)bp.n, X4 + bp.x0, aX64 + bp.x0, g_mode, S, Xr + (size_t)bp.xtile0 * 4 * FORCE_TJ,
+                   XA + (size_t)bp.xtile0 * 2 * FORCE_TJ);
+  for (int i = blockIdx.y * blockDim.x + threadIdx.x; i < bp.mpad; i += stride)
+    write_y_record(i, (int)bp.m, Y4 + bp.y0, aY64 + bp.y0, S, Y0r + bp.ybase);
+}
+
+cudaError_t launch_records_multi(Launch L, const float4* X4, const double* aX64, const float4* Y4,
+                                 const double* aY64, const BatchPair* pairs, int npairs, int g_mode,
+                                 const DevStats* stats, float4* Xr, float2* XA, float4* Y0r) {
+  records_multi_kernel<<<dim3(npairs, 8), 256, 0, L.stream>>>(X4, aX64, Y4, aY64, pairs, g_mode, stats,
+                                                               reinterpret_cast<float*>(Xr),
+                                                               reinterpret_cast<float*>(XA), Y0r);
+  return after_launch(L);
+}
+
+// Batched statistics: block p computes, in a fixed order, the reference and
+// template means, scatters and largest eigenvalues of pair p, and sigma
+// (population std of its reference curvatures, or sigma_user if > 0).
+__global__ void __launch_bounds__(RED_THREADS)
+    stats_multi_kernel(const float4* __restrict__ X4, const float4* __restrict__ Y4,
+                       const double* __restrict__ aX64, const BatchPair* __restrict__ pairs,
+                       double sigma_user, DevStats* __restrict__ out) {
+  __shared__ double sh[6][RED_THREADS];
+  const BatchPair bp = pairs[blockIdx.x];
+  DevStats* st = out + blockIdx.x;
+  for (int side = 0; side < 2; ++side) {
+    const float4* P = side == 0 ? X4 + bp.x0 : Y4 + bp.y0;
+    const int64_t n = side == 0 ? bp.n : bp.m;
+    double v3[3] = {0, 0, 0};
+    for (int64_t i = threadIdx.x; i < n; i += RED_THREADS) {
+      const float4 c = P[i];
+      v3[0] += c.x; v3[1] += c.y; v3[2] += c.z;
+    }
+    block_sum<3>(v3, sh);
+    const double mean[3] = {v3[0] / n, v3[1] / n, v3[2] / n};
+    __syncthreads();
+    double v6[6] = {0, 0, 0, 0, 0, 0};
+    for (int64_t i = threadIdx.x; i < n; i += RED_THREADS) {
+      const float4 c = P[i];
+      const double dx = c.x - mean[0], dy = c.y - mean[1], dz = c.z - mean[2];
+      v6[0] += dx * dx; v6[1] += dx * dy; v6[2] += dx * dz;
+      v6[3] += dy * dy; v6[4] += dy * dz; v6[5] += dz * dz;
+    }
+    block_sum<6>(v6, sh);
+    if (threadIdx.x == 0) {
+      const double S[9] = {v6[0], v6[1], v6[2], v6[1], v6[3], v6[4], v6[2], v6[4], v6[5]};
+      double C[9], lam[3];
+      for (int q = 0; q < 9; ++q) C[q] = S[q] / (double)n;
+      sym3_eigenvalues(C, lam);
+      double* mo = side == 0 ? st->xbar : st->ybar0;
+      double* so = side == 0 ? st->CX : st->S0;
+      for (int q = 0; q < 3; ++q) mo[q] = mean[q];
+      for (int q = 0; q < 9; ++q) so[q] = S[q];
+      if (side == 0) st->eX = lam[2];
+      else st->eY0 = lam[2];
+    }
+    __syncthreads();
+  }
+  double v1[1] = {0};
+  for (int64_t i = threadIdx.x; i < bp.n; i += RED_THREADS) v1[0] += aX64[bp.x0 + i];
+  block_sum<1>(v1, sh);
+  const double amean = v1[0] / bp.n;
+  const double asum = v1[0];
+  __syncthreads();
+  double v2[1] = {0};
+  for (int64_t i = threadIdx.x; i < bp.n; i += RED_THREADS) {
+    const double d = aX64[bp.x0 + i] - amean;
+    v2[0] += d * d;
+  }
+  block_sum<1>(v2, sh);
+  if (threadIdx.x == 0) {
+    st->asum[0] = asum;
+    if (sigma_user > 0.0) st->sigma = sigma_user;
+    else {
+      const double sd = sqrt(v2[0] / bp.n);
+      st->sigma = sd >= 1e-12 ? sd : 1.0;
     }
   }
-  if (i < mpad) {
-    if (i < m) {
-      const float4 c = Y4[i];
-      Y0r[i] = make_float4(c.x, c.y, c.z, (float)(aY64[i] * kscale));
-    } else {
-      Y0r[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-    }
-  }
+}
+
+cudaError_t launch_stats_multi(Launch L, const float4* X4, const float4* Y4, const double* aX64,
+                               const BatchPair* pairs, int npairs, double sigma_user, DevStats* out) {
+  stats_multi_kernel<<<npairs, RED_THREADS, 0, L.stream>>>(X4, Y4, aX64, pairs, sigma_user, out);
+  return after_launch(L);
 }
 
 cudaError_t launch_records(Launch L, const float4* X4, const double* aX64, int n, int npad,

@@ -134,21 +134,44 @@ __device__ __forceinline__ void pair2(u64 xv, u64 yv, u64 zv, u64 nv, u64 av, u6
   Sz = fma2(w, zv, Sz);
 }
 
-template <int P, int PM, int TPB, int TJ, int MINB>
+// BATCH = false: one problem, grid (template blocks, reference splits).
+// BATCH = true: one block per work item {pair, template block, reference
+// chunk} of a batch of independent problems (items[], pairs[], one pose per
+// pair); tiles_per_split is then the chunk length in tiles.
+template <int P, int PM, int TPB, int TJ, int MINB, bool BATCH>
 __global__ void __launch_bounds__(TPB, MINB)
     force_tile_kernel(const float* __restrict__ Xr, const float* __restrict__ XA, int ntiles,
                       int tiles_per_split, const float4* __restrict__ Y0r, int mpad,
-                      const DevPose* __restrict__ pose, float qexp, float4* __restrict__ partial) {
+                      const DevPose* __restrict__ pose, float qexp, float4* __restrict__ partial,
+                      const int4* __restrict__ items, const BatchPair* __restrict__ pairs) {
   __shared__ __align__(16) float sT[6][TJ];
   const int tid = threadIdx.x;
-  const int ibase = blockIdx.x * (TPB * P);
-  const int split = blockIdx.y;
+  int ibase, t0, t1;
+  const DevPose* ps;
+  float4* outbase;
+  if (BATCH) {
+    const int4 it = items[blockIdx.x];
+    const BatchPair& bp = pairs[it.x];
+    const int lt0 = it.z * tiles_per_split;
+    const int local = it.y * (TPB * P);
+    t0 = (int)bp.xtile0 + lt0;
+    t1 = (int)bp.xtile0 + min(bp.ntiles, lt0 + tiles_per_split);
+    ibase = (int)bp.ybase + local;
+    ps = pose + it.x;
+    outbase = partial + bp.pbase + (size_t)it.z * bp.mpad + local;
+  } else {
+    ibase = blockIdx.x * (TPB * P);
+    t0 = blockIdx.y * tiles_per_split;
+    t1 = min(ntiles, t0 + tiles_per_split);
+    ps = pose;
+    outbase = partial + (size_t)blockIdx.y * mpad + ibase;
+  }
 
   float A[9], b[3];
 #pragma unroll
-  for (int q = 0; q < 9; ++q) A[q] = pose->A[q];
+  for (int q = 0; q < 9; ++q) A[q] = ps->A[q];
 #pragma unroll
-  for (int q = 0; q < 3; ++q) b[q] = pose->b[q];
+  for (int q = 0; q < 3; ++q) b[q] = ps->b[q];
 
   u64 mx[P], my[P], mz[P], ny[P], ah[P];
 #pragma unroll
@@ -173,8 +196,6 @@ __global__ void __launch_bounds__(TPB, MINB)
     cW[q] = cx[q] = cy[q] = cz[q] = 0.f;
   }
 
-  const int t0 = split * tiles_per_split;
-  const int t1 = min(ntiles, t0 + tiles_per_split);
   for (int t = t0; t < t1; ++t) {
     __syncthreads();
     {
@@ -221,7 +242,7 @@ __global__ void __launch_bounds__(TPB, MINB)
     }
   }
 
-  float4* out = partial + (size_t)split * mpad + ibase + tid;
+  float4* out = outbase + tid;
 #pragma unroll
   for (int q = 0; q < P; ++q)
     out[q * TPB] = make_float4(hW[q] - cW[q], hx[q] - cx[q], hy[q] - cy[q], hz[q] - cz[q]);
@@ -236,7 +257,7 @@ static int force_blocks_per_sm(const ForcePlan& fp);
 // do (almost) the same work, so the last wave's fill decides the tail: pick
 // the smallest S in [S_lo, S_hi] whose grid fills its last wave to >= 99%
 // (else the best fill seen).
-ForcePlan plan_force(int64_t m, int64_t npad, double p, int num_sms) {
+ForcePlan plan_force(int64_t m, int64_t npad, double p, int num_sms, const ForceTuning& tune) {
   ForcePlan fp;
   fp.pmode = (p == 1.0) ? 1 : (p == 2.0) ? 2 : (p == 3.0) ? 3 : 0;
   fp.tile_j = FORCE_TJ;
@@ -245,6 +266,8 @@ ForcePlan plan_force(int64_t m, int64_t npad, double p, int num_sms) {
   else if (m >= (int64_t)num_sms * 256 * 2) fp.P = 2;
   else fp.P = 1;
   if (m < 4096) fp.tpb = 128;
+  if (tune.P == 1 || tune.P == 2 || tune.P == 4) fp.P = tune.P;
+  if (tune.tpb == 128 || tune.tpb == 256) fp.tpb = tune.tpb;
   const int64_t per_block = (int64_t)fp.tpb * fp.P;
   fp.iblocks = (int)((m + per_block - 1) / per_block);
   const int ntiles = (int)(npad / FORCE_TJ);
@@ -256,6 +279,7 @@ ForcePlan plan_force(int64_t m, int64_t npad, double p, int num_sms) {
   if (S_hi > 64) S_hi = 64;
   if (S_lo > S_hi) S_lo = S_hi;
   if (S_lo < 1) S_lo = 1;
+  if (tune.splits > 0) S_lo = S_hi = tune.splits < ntiles ? tune.splits : ntiles;
   int64_t best_S = S_lo;
   double best_fill = -1.0;
   for (int64_t S = S_lo; S <= S_hi; ++S) {
@@ -287,9 +311,9 @@ static void launch_force_t(cudaStream_t st, const ForcePlan& fp, const float4* X
                            const float2* XA, int ntiles, const float4* Y0r, int mpad,
                            const DevPose* pose, float qexp, float4* partial) {
   dim3 grid(fp.iblocks, fp.splits);
-  force_tile_kernel<P, PM, TPB, FORCE_TJ, 2><<<grid, TPB, 0, st>>>(
+  force_tile_kernel<P, PM, TPB, FORCE_TJ, 2, false><<<grid, TPB, 0, st>>>(
       reinterpret_cast<const float*>(Xr), reinterpret_cast<const float*>(XA), ntiles,
-      fp.tiles_per_split, Y0r, mpad, pose, qexp, partial);
+      fp.tiles_per_split, Y0r, mpad, pose, qexp, partial, nullptr, nullptr);
 }
 
 template <int PM>
@@ -301,7 +325,9 @@ static void launch_force_pm(cudaStream_t st, const ForcePlan& fp, const float4* 
     else if (fp.P == 2) launch_force_t<2, PM, 256>(st, fp, Xr, XA, ntiles, Y0r, mpad, pose, qexp, partial);
     else launch_force_t<1, PM, 256>(st, fp, Xr, XA, ntiles, Y0r, mpad, pose, qexp, partial);
   } else {
-    launch_force_t<1, PM, 128>(st, fp, Xr, XA, ntiles, Y0r, mpad, pose, qexp, partial);
+    if (fp.P == 4) launch_force_t<4, PM, 128>(st, fp, Xr, XA, ntiles, Y0r, mpad, pose, qexp, partial);
+    else if (fp.P == 2) launch_force_t<2, PM, 128>(st, fp, Xr, XA, ntiles, Y0r, mpad, pose, qexp, partial);
+    else launch_force_t<1, PM, 128>(st, fp, Xr, XA, ntiles, Y0r, mpad, pose, qexp, partial);
   }
 }
 
@@ -310,11 +336,13 @@ static int blocks_per_sm_pm(const ForcePlan& fp) {
   int nb = 0;
   cudaError_t e;
   if (fp.tpb == 256) {
-    if (fp.P == 4) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, force_tile_kernel<4, PM, 256, FORCE_TJ, 2>, 256, 0);
-    else if (fp.P == 2) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, force_tile_kernel<2, PM, 256, FORCE_TJ, 2>, 256, 0);
-    else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, force_tile_kernel<1, PM, 256, FORCE_TJ, 2>, 256, 0);
+    if (fp.P == 4) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, force_tile_kernel<4, PM, 256, FORCE_TJ, 2, false>, 256, 0);
+    else if (fp.P == 2) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, force_tile_kernel<2, PM, 256, FORCE_TJ, 2, false>, 256, 0);
+    else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, force_tile_kernel<1, PM, 256, FORCE_TJ, 2, false>, 256, 0);
   } else {
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, force_tile_kernel<1, PM, 128, FORCE_TJ, 2>, 128, 0);
+    if (fp.P == 4) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, force_tile_kernel<4, PM, 128, FORCE_TJ, 2, false>, 128, 0);
+    else if (fp.P == 2) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, force_tile_kernel<2, PM, 128, FORCE_TJ, 2, false>, 128, 0);
+    else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, force_tile_kernel<1, PM, 128, FORCE_TJ, 2, false>, 128, 0);
   }
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -345,23 +373,77 @@ cudaError_t launch_force(Launch L, const ForcePlan& fp, const float4* Xr, const 
   return cudaGetLastError();
 }
 
+// Batched force pass: one block of 128 template points per item.
+template <int PM>
+static void launch_force_batch_pm(cudaStream_t st, int nitems, const int4* items, const BatchPair* pairs,
+                                  const float4* Xr, const float2* XA, const float4* Y0r, const DevPose* poses,
+                                  float qexp, float4* partial, int chunk_tiles) {
+  force_tile_kernel<1, PM, 128, FORCE_TJ, 2, true><<<nitems, 128, 0, st>>>(
+      reinterpret_cast<const float*>(Xr), reinterpret_cast<const float*>(XA), 0, chunk_tiles, Y0r, 0, poses, qexp,
+      partial, items, pairs);
+}
+
+cudaError_t launch_force_batch(Launch L, int pmode, int nitems, const int4* items, const BatchPair* pairs,
+                               const float4* Xr, const float2* XA, const float4* Y0r, const DevPose* poses,
+                               float qexp, float4* partial, int chunk_tiles) {
+  if (nitems <= 0) return cudaSuccess;
+  switch (pmode) {
+    case 1: launch_force_batch_pm<1>(L.stream, nitems, items, pairs, Xr, XA, Y0r, poses, qexp, partial, chunk_tiles); break;
+    case 2: launch_force_batch_pm<2>(L.stream, nitems, items, pairs, Xr, XA, Y0r, poses, qexp, partial, chunk_tiles); break;
+    case 3: launch_force_batch_pm<3>(L.stream, nitems, items, pairs, Xr, XA, Y0r, poses, qexp, partial, chunk_tiles); break;
+    default: launch_force_batch_pm<0>(L.stream, nitems, items, pairs, Xr, XA, Y0r, poses, qexp, partial, chunk_tiles); break;
+  }
+  if (L.counter) ++*L.counter;
+  return cudaGetLastError();
+}
+
 // ---- combine: splits -> per-point force -> per-block (F, W, T) -------------
 constexpr int CMB_TPB = RED_THREADS;
 
+// BATCH = true: block b belongs to pair cpair[b]; its 256 template slots are
+// that pair's slots (b - cblk0) * 256 + threadIdx.x.
+template <bool BATCH>
 __global__ void __launch_bounds__(CMB_TPB)
     combine_kernel(const float4* __restrict__ partial, int S, int mpad, int m,
                    const float4* __restrict__ Y0r, const double* __restrict__ aY64, int g_mode,
                    const DevPose* __restrict__ pose, float4* __restrict__ f4out,
-                   double* __restrict__ blockpart) {
+                   double* __restrict__ blockpart, const int* __restrict__ cpair,
+                   const BatchPair* __restrict__ pairs) {
   __shared__ double sh[13][RED_THREADS];
-  const int i = blockIdx.x * CMB_TPB + threadIdx.x;
+  int i, mm, SS;
+  size_t pstride;
+  const float4* pbase;
+  const float4* ybase;
+  const double* abase;
+  const DevPose* ps;
+  if (BATCH) {
+    const int p = cpair[blockIdx.x];
+    const BatchPair& bp = pairs[p];
+    i = (blockIdx.x - bp.cblk0) * CMB_TPB + threadIdx.x;
+    mm = (int)bp.m;
+    SS = bp.chunks;
+    pstride = (size_t)bp.mpad;
+    pbase = partial + bp.pbase;
+    ybase = Y0r + bp.ybase;
+    abase = aY64 + bp.y0;
+    ps = pose + p;
+  } else {
+    i = blockIdx.x * CMB_TPB + threadIdx.x;
+    mm = m;
+    SS = S;
+    pstride = (size_t)mpad;
+    pbase = partial;
+    ybase = Y0r;
+    abase = aY64;
+    ps = pose;
+  }
   double v[13];
 #pragma unroll
   for (int q = 0; q < 13; ++q) v[q] = 0.0;
-  if (i < m) {
+  if (i < mm) {
     double W = 0, Sx = 0, Sy = 0, Sz = 0;
-    for (int s = 0; s < S; ++s) {
-      const float4 pp = partial[(size_t)s * mpad + i];
+    for (int s = 0; s < SS; ++s) {
+      const float4 pp = pbase[(size_t)s * pstride + i];
       W += pp.x;
       Sx += pp.y;
       Sy += pp.z;
@@ -369,17 +451,17 @@ __global__ void __launch_bounds__(CMB_TPB)
     }
     float A[9], b[3];
 #pragma unroll
-    for (int q = 0; q < 9; ++q) A[q] = pose->A[q];
+    for (int q = 0; q < 9; ++q) A[q] = ps->A[q];
 #pragma unroll
-    for (int q = 0; q < 3; ++q) b[q] = pose->b[q];
+    for (int q = 0; q < 3; ++q) b[q] = ps->b[q];
     float yx, yy, yz;
-    template_point(Y0r[i], A, b, yx, yy, yz);
-    const double ay = g_mode == 1 ? aY64[i] : 1.0;
+    template_point(ybase[i], A, b, yx, yy, yz);
+    const double ay = g_mode == 1 ? abase[i] : 1.0;
     const double f[3] = {ay * (Sx - (double)yx * W), ay * (Sy - (double)yy * W),
                          ay * (Sz - (double)yz * W)};
     const double Wi = ay * W;
-    const double c[3] = {(double)yx - pose->ybs[0], (double)yy - pose->ybs[1],
-                         (double)yz - pose->ybs[2]};
+    const double c[3] = {(double)yx - ps->ybs[0], (double)yy - ps->ybs[1],
+                         (double)yz - ps->ybs[2]};
     v[0] = f[0];
     v[1] = f[1];
     v[2] = f[2];
@@ -402,8 +484,19 @@ int combine_blocks(int64_t mpad) { return (int)((mpad + CMB_TPB - 1) / CMB_TPB);
 cudaError_t launch_combine(Launch L, const float4* partial, int S, int mpad, int m,
                            const float4* Y0r, const double* aY64, int g_mode, const DevPose* pose,
                            float4* f4out, double* blockpart) {
-  combine_kernel<<<combine_blocks(mpad), CMB_TPB, 0, L.stream>>>(partial, S, mpad, m, Y0r, aY64,
-                                                                 g_mode, pose, f4out, blockpart);
+  combine_kernel<false><<<combine_blocks(mpad), CMB_TPB, 0, L.stream>>>(partial, S, mpad, m, Y0r, aY64,
+                                                                        g_mode, pose, f4out, blockpart,
+                                                                        nullptr, nullptr);
+  if (L.counter) ++*L.counter;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_combine_batch(Launch L, int nblocks, const int* cpair, const BatchPair* pairs,
+                                 const float4* partial, const float4* Y0r, const double* aY64, int g_mode,
+                                 const DevPose* poses, double* blockpart) {
+  if (nblocks <= 0) return cudaSuccess;
+  combine_kernel<true><<<nblocks, CMB_TPB, 0, L.stream>>>(partial, 0, 0, 0, Y0r, aY64, g_mode, poses, nullptr,
+                                                          blockpart, cpair, pairs);
   if (L.counter) ++*L.counter;
   return cudaGetLastError();
 }

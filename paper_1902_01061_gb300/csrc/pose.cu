@@ -151,10 +151,9 @@ cudaError_t launch_pose_refresh(Launch L, DevPose* pose, const DevStats* stats) 
   return cudaGetLastError();
 }
 
-__global__ void __launch_bounds__(RED_THREADS)
-    finalize_kernel(const double* __restrict__ blockpart, int nblocks, DevPose* ps,
-                    const DevStats* __restrict__ st, StepParams sp, int* err) {
-  __shared__ double sh[13][RED_THREADS];
+__device__ void finalize_body(const double* __restrict__ blockpart, int nblocks, DevPose* ps,
+                              const DevStats* __restrict__ st, StepParams sp, int* err,
+                              double (*sh)[RED_THREADS]) {
   double v[13];
 #pragma unroll
   for (int q = 0; q < 13; ++q) v[q] = 0.0;
@@ -248,6 +247,50 @@ __global__ void __launch_bounds__(RED_THREADS)
   ps->s = cs * s;
   ps->it = it + 1;
   refresh_pose(ps, st);
+}
+
+__global__ void __launch_bounds__(RED_THREADS)
+    finalize_kernel(const double* __restrict__ blockpart, int nblocks, DevPose* ps,
+                    const DevStats* __restrict__ st, StepParams sp, int* err) {
+  __shared__ double sh[13][RED_THREADS];
+  finalize_body(blockpart, nblocks, ps, st, sp, err, sh);
+}
+
+// One block per pair of a batch.
+__global__ void __launch_bounds__(RED_THREADS)
+    finalize_multi_kernel(const double* __restrict__ blockpart, const BatchPair* __restrict__ pairs,
+                          DevPose* poses, const DevStats* __restrict__ stats, StepParams sp, int* err) {
+  __shared__ double sh[13][RED_THREADS];
+  const BatchPair& bp = pairs[blockIdx.x];
+  StepParams spp = sp;
+  spp.M = (int)bp.m;
+  finalize_body(blockpart + (size_t)bp.cblk0 * 13, bp.ncblk, poses + blockIdx.x, stats + blockIdx.x, spp, err, sh);
+}
+
+cudaError_t launch_finalize_multi(Launch L, const double* blockpart, const BatchPair* pairs, int npairs,
+                                  DevPose* poses, const DevStats* stats, StepParams sp, int* err) {
+  finalize_multi_kernel<<<npairs, RED_THREADS, 0, L.stream>>>(blockpart, pairs, poses, stats, sp, err);
+  if (L.counter) ++*L.counter;
+  return cudaGetLastError();
+}
+
+__global__ void pose_init_multi_kernel(DevPose* poses, const DevStats* stats, int npairs, int E) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= npairs) return;
+  DevPose* ps = poses + p;
+  for (int q = 0; q < 9; ++q) ps->R[q] = (q % 4 == 0) ? 1.0 : 0.0;
+  ps->t[0] = ps->t[1] = ps->t[2] = 0.0;
+  ps->s = 1.0;
+  ps->it = 0;
+  ps->E = E;
+  ps->degenerate = 0;
+  refresh_pose(ps, stats + p);
+}
+
+cudaError_t launch_pose_init_multi(Launch L, DevPose* poses, const DevStats* stats, int npairs, int E) {
+  pose_init_multi_kernel<<<(npairs + 127) / 128, 128, 0, L.stream>>>(poses, stats, npairs, E);
+  if (L.counter) ++*L.counter;
+  return cudaGetLastError();
 }
 
 cudaError_t launch_finalize(Launch L, const double* blockpart, int nblocks, DevPose* pose,

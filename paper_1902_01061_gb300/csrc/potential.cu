@@ -1,0 +1,217 @@
+// Shape-weighted potential and its adjoint (the differentiation form).
+//
+// U = sum_i sum_j g(s_ij) d_ij^(p+1) / (p+1) is the potential whose negative
+// gradient with respect to Y_i is the force of Eq. 5 (descriptors fixed).
+// With Y = s Y0 R(omega) + t (row vectors, R = exp([omega]_x)^T) the pose
+// gradient follows from G_i = dU/dY_i = -f_i:
+//   dU/dt = sum_i G_i,   dU/ds = sum_i G_i . (Y0_i R),
+//   dU/dR = s sum_i Y0_i^T G_i,   dU/dY0_i = s G_i R^T,
+// and for the axis-angle the SO(3) right Jacobian J_r: perturbing
+// R_col(omega + delta) = R_col(omega) exp([J_r(omega) delta]_x) gives
+// dU/domega = J_r(omega)^T w, where w is the axial vector of the skew part of
+// B = (dU/dR) R_col (w_c = sum_ab eps_abc B_ab).
+//
+// The forward pass is the force kernel with the distance exponent raised by
+// two (it accumulates sum_j g d^(p+1)); the adjoint pass re-runs the force
+// kernel at the same pose (tile recomputation: no N x M storage) and reduces
+// the chain-rule terms in float64 in a fixed order.
+#include <cmath>
+
+#include "common.cuh"
+
+namespace scgr {
+
+// Template point in the frame centred on the reference mean (identical
+// arithmetic to the force kernel's).
+__device__ __forceinline__ void tpoint(const float4 y0, const float* A, const float* b, float& yx,
+                                       float& yy, float& yz) {
+  yx = fmaf(y0.z, A[6], fmaf(y0.y, A[3], fmaf(y0.x, A[0], b[0])));
+  yy = fmaf(y0.z, A[7], fmaf(y0.y, A[4], fmaf(y0.x, A[1], b[1])));
+  yz = fmaf(y0.z, A[8], fmaf(y0.y, A[5], fmaf(y0.x, A[2], b[2])));
+}
+
+// Row-vector rotation R = exp([w]_x)^T by the Rodrigues formula.
+__device__ void rotation_from_axis_angle(const double* w, double* R) {
+  const double th2 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
+  double a, bq;  // exp([w]x) = I + a K + bq K^2
+  if (th2 < 1e-16) {
+    a = 1.0 - th2 / 6.0;
+    bq = 0.5 - th2 / 24.0;
+  } else {
+    const double th = sqrt(th2);
+    a = sin(th) / th;
+    bq = (1.0 - cos(th)) / th2;
+  }
+  const double K[9] = {0.0, -w[2], w[1], w[2], 0.0, -w[0], -w[1], w[0], 0.0};
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 3; ++c) {
+      double k2 = 0.0;
+      for (int q = 0; q < 3; ++q) k2 += K[r * 3 + q] * K[q * 3 + c];
+      const double rc = (r == c ? 1.0 : 0.0) + a * K[r * 3 + c] + bq * k2;
+      R[c * 3 + r] = rc;  // transpose: row-vector convention
+    }
+}
+
+__global__ void pose_from7_kernel(const double* __restrict__ pose7, DevPose* ps, const DevStats* st) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  rotation_from_axis_angle(pose7, ps->R);
+  for (int c = 0; c < 3; ++c) ps->t[c] = pose7[3 + c];
+  ps->s = pose7[6];
+  for (int q = 0; q < 9; ++q) ps->A[q] = (float)(ps->s * ps->R[q]);
+  for (int c = 0; c < 3; ++c) {
+    ps->b[c] = (float)(ps->t[c] - st->xbar[c]);
+    const double yb = ps->s * (st->ybar0[0] * ps->R[c] + st->ybar0[1] * ps->R[3 + c] +
+                               st->ybar0[2] * ps->R[6 + c]) + ps->t[c];
+    ps->ybs[c] = yb - st->xbar[c];
+  }
+  ps->it = 0;
+  ps->E = 1;
+  ps->degenerate = 0;
+}
+
+// Per point: G_i = -f_i from the split partials; the template-coordinate
+// gradient s G_i R^T; per-block chain-rule sums (sum G, sum G.(Y0 R),
+// sum Y0^T G).
+__global__ void __launch_bounds__(RED_THREADS)
+    adjoint_combine_kernel(const float4* __restrict__ partial, int S, int mpad, int m,
+                           const float4* __restrict__ Y0r, const double* __restrict__ aY64,
+                           int g_mode, const DevPose* __restrict__ ps, float* __restrict__ grad_xyz,
+                           double* __restrict__ blockpart) {
+  __shared__ double sh[13][RED_THREADS];
+  const int i = blockIdx.x * RED_THREADS + threadIdx.x;
+  double v[13];
+#pragma unroll
+  for (int q = 0; q < 13; ++q) v[q] = 0.0;
+  if (i < m) {
+    double W = 0, Sx = 0, Sy = 0, Sz = 0;
+    for (int s = 0; s < S; ++s) {
+      const float4 pp = partial[(size_t)s * mpad + i];
+      W += pp.x;
+      Sx += pp.y;
+      Sy += pp.z;
+      Sz += pp.w;
+    }
+    float A[9], b[3];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) A[q] = ps->A[q];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) b[q] = ps->b[q];
+    const float4 y0 = Y0r[i];
+    float yx, yy, yz;
+    tpoint(y0, A, b, yx, yy, yz);
+    const double ay = g_mode == 1 ? aY64[i] : 1.0;
+    // G = dU/dY = -f = aY (Y' sum w - sum w X')
+    const double G[3] = {ay * ((double)yx * W - Sx), ay * ((double)yy * W - Sy), ay * ((double)yz * W - Sz)};
+    const double Y0d[3] = {(double)y0.x, (double)y0.y, (double)y0.z};
+    double y0R[3];
+    for (int c = 0; c < 3; ++c)
+      y0R[c] = Y0d[0] * ps->R[c] + Y0d[1] * ps->R[3 + c] + Y0d[2] * ps->R[6 + c];
+    v[0] = G[0];
+    v[1] = G[1];
+    v[2] = G[2];
+    v[3] = G[0] * y0R[0] + G[1] * y0R[1] + G[2] * y0R[2];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int bb = 0; bb < 3; ++bb) v[4 + 3 * a + bb] = Y0d[a] * G[bb];
+    if (grad_xyz) {
+      for (int a = 0; a < 3; ++a) {
+        const double gr = ps->s * (G[0] * ps->R[a * 3] + G[1] * ps->R[a * 3 + 1] + G[2] * ps->R[a * 3 + 2]);
+        grad_xyz[(size_t)i * 3 + a] = (float)gr;
+      }
+    }
+  }
+  block_sum<13>(v, sh);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int q = 0; q < 13; ++q) blockpart[(size_t)blockIdx.x * 13 + q] = v[q];
+  }
+}
+
+// One block: fixed-order column sums of [nb][13] partials.
+__global__ void __launch_bounds__(RED_THREADS) column_sum13_kernel(const double* __restrict__ part, int nb,
+                                                                   double* __restrict__ out) {
+  __shared__ double sh[13][RED_THREADS];
+  double v[13];
+#pragma unroll
+  for (int q = 0; q < 13; ++q) v[q] = 0.0;
+  for (int b = threadIdx.x; b < nb; b += RED_THREADS) {
+#pragma unroll
+    for (int q = 0; q < 13; ++q) v[q] += part[(size_t)b * 13 + q];
+  }
+  block_sum<13>(v, sh);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int q = 0; q < 13; ++q) out[q] = v[q];
+  }
+}
+
+// grad7 = (dU/domega, dU/dt, dU/ds) from the chain-rule sums.
+__global__ void adjoint_finish_kernel(const double* __restrict__ tot, const double* __restrict__ pose7,
+                                      const DevPose* __restrict__ ps, double* __restrict__ grad7) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const double s = ps->s;
+  double M[9];  // dU/dR
+  for (int q = 0; q < 9; ++q) M[q] = s * tot[4 + q];
+  // B = M R_col, R_col = R^T
+  double B[9];
+  for (int a = 0; a < 3; ++a)
+    for (int c = 0; c < 3; ++c) {
+      double acc = 0.0;
+      for (int q = 0; q < 3; ++q) acc += M[a * 3 + q] * ps->R[c * 3 + q];
+      B[a * 3 + c] = acc;
+    }
+  const double w[3] = {B[5] - B[7], B[6] - B[2], B[1] - B[3]};
+  const double* om = pose7;
+  const double th2 = om[0] * om[0] + om[1] * om[1] + om[2] * om[2];
+  double c1, c2;  // J_r = I - c1 K + c2 K^2
+  if (th2 < 1e-12) {
+    c1 = 0.5 - th2 / 24.0;
+    c2 = 1.0 / 6.0 - th2 / 120.0;
+  } else {
+    const double th = sqrt(th2);
+    c1 = (1.0 - cos(th)) / th2;
+    c2 = (th - sin(th)) / (th2 * th);
+  }
+  const double K[9] = {0.0, -om[2], om[1], om[2], 0.0, -om[0], -om[1], om[0], 0.0};
+  double J[9];
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 3; ++c) {
+      double k2 = 0.0;
+      for (int q = 0; q < 3; ++q) k2 += K[r * 3 + q] * K[q * 3 + c];
+      J[r * 3 + c] = (r == c ? 1.0 : 0.0) - c1 * K[r * 3 + c] + c2 * k2;
+    }
+  for (int k = 0; k < 3; ++k) grad7[k] = J[0 * 3 + k] * w[0] + J[1 * 3 + k] * w[1] + J[2 * 3 + k] * w[2];
+  for (int c = 0; c < 3; ++c) grad7[3 + c] = tot[c];
+  grad7[6] = tot[3];
+}
+
+cudaError_t launch_pose_from7(Launch L, const double* pose7_dev, DevPose* ps, const DevStats* st) {
+  pose_from7_kernel<<<1, 32, 0, L.stream>>>(pose7_dev, ps, st);
+  if (L.counter) ++*L.counter;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_combine(Launch L, const float4* partial, int S, int mpad, int m, const float4* Y0r,
+                                   const double* aY64, int g_mode, const DevPose* ps, float* grad_xyz,
+                                   double* blockpart) {
+  adjoint_combine_kernel<<<(mpad + RED_THREADS - 1) / RED_THREADS, RED_THREADS, 0, L.stream>>>(
+      partial, S, mpad, m, Y0r, aY64, g_mode, ps, grad_xyz, blockpart);
+  if (L.counter) ++*L.counter;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_column_sum13(Launch L, const double* part, int nb, double* out) {
+  column_sum13_kernel<<<1, RED_THREADS, 0, L.stream>>>(part, nb, out);
+  if (L.counter) ++*L.counter;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_finish(Launch L, const double* tot, const double* pose7_dev, const DevPose* ps,
+                                  double* grad7) {
+  adjoint_finish_kernel<<<1, 32, 0, L.stream>>>(tot, pose7_dev, ps, grad7);
+  if (L.counter) ++*L.counter;
+  return cudaGetLastError();
+}
+
+}  // namespace scgr

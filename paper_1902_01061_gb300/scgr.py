@@ -29,7 +29,15 @@ EXPORTED = (
     "scgr_get_moved_host", "scgr_get_descriptors", "scgr_get_sigma", "scgr_get_curvature64",
     "scgr_forces", "scgr_get_state", "scgr_set_state", "scgr_sync", "scgr_launch_count",
     "scgr_set_curvature", "scgr_set_force_timing", "scgr_get_force_timing", "scgr_forces_static",
+    "scgr_potential", "scgr_batch_run", "scgr_set_tuning", "scgr_set_row_range", "scgr_step_partials",
+    "scgr_step_apply", "scgr_get_plan", "scgr_microbench",
 )
+SCGR_TUNE_BATCH_CHUNK_TILES = 1
+SCGR_TUNE_KNN_GRID_MIN = 2
+SCGR_TUNE_FORCE_P = 3
+SCGR_TUNE_FORCE_TPB = 4
+SCGR_TUNE_FORCE_SPLITS = 5
+SCGR_TUNE_REUSE_POSE_FREE = 6
 
 
 class scgr_params(Structure):
@@ -96,6 +104,14 @@ def load():
         "scgr_set_curvature": (S, [ctx, c_int, c_void_p]),
         "scgr_set_force_timing": (S, [ctx, c_int]),
         "scgr_get_force_timing": (S, [ctx, POINTER(c_int64), POINTER(c_double)]),
+        "scgr_batch_run": (S, [ctx, c_int, c_void_p, c_void_p, c_void_p, c_void_p, c_int, c_void_p]),
+        "scgr_set_tuning": (S, [ctx, c_int, c_int]),
+        "scgr_get_plan": (S, [ctx, POINTER(c_int)]),
+        "scgr_microbench": (S, [c_int, c_int, c_void_p, c_void_p, POINTER(c_int64), POINTER(c_double)]),
+        "scgr_set_row_range": (S, [ctx, c_int64, c_int64]),
+        "scgr_step_partials": (S, [ctx, POINTER(c_double)]),
+        "scgr_step_apply": (S, [ctx, POINTER(c_double)]),
+        "scgr_potential": (S, [ctx, POINTER(c_double), POINTER(c_double), POINTER(c_double), c_void_p]),
         "scgr_forces_static": (S, [c_void_p, c_int64, c_void_p, c_int64, c_void_p, c_void_p, c_double,
                                    c_double, c_int, c_void_p, c_void_p]),
     }
@@ -262,6 +278,74 @@ def scgr_forces_static(x, y, ax, ay, f4_out, sigma: float = 0.0, p: float = 1.0,
         raise ScgrError(st, "scgr_forces_static failed")
 
 
+def scgr_potential(ctx, pose7, want_grad: bool = True, grad_xyz_out=None):
+    """U at pose7 = (omega, t, s); with want_grad also dU/dpose7 (numpy
+    float64[7]); grad_xyz_out (CUDA float32 [m,3]) receives dU/dY0."""
+    p7 = (c_double * 7)(*[float(v) for v in np.asarray(pose7, dtype=np.float64).reshape(7)])
+    U = c_double()
+    g7 = (c_double * 7)() if want_grad else None
+    gx = _dev_ptr(grad_xyz_out, "float32", (3,)) if grad_xyz_out is not None else None
+    _check(load().scgr_potential(ctx, p7, ctypes.byref(U), g7, gx), ctx)
+    return float(U.value), (np.array(g7[:]) if want_grad else None)
+
+
+def scgr_batch_run(ctx, ref_off, ref_xyz, tmp_off, tmp_xyz, iterations: int):
+    """npairs registrations in one call.  ref_off/tmp_off: host int64 arrays of
+    npairs + 1 offsets; ref_xyz/tmp_xyz: CUDA float32 [total, 3] tensors.
+    Returns a list of scgr_result."""
+    ro = np.ascontiguousarray(ref_off, dtype=np.int64)
+    to = np.ascontiguousarray(tmp_off, dtype=np.int64)
+    npairs = len(ro) - 1
+    if len(to) != npairs + 1:
+        raise ValueError("offset arrays differ in length")
+    res = (scgr_result * npairs)()
+    _check(load().scgr_batch_run(ctx, npairs, ro.ctypes.data, _dev_ptr(ref_xyz, "float32", (3,)), to.ctypes.data,
+                                 _dev_ptr(tmp_xyz, "float32", (3,)), int(iterations), ctypes.addressof(res)), ctx)
+    return list(res)
+
+
+def scgr_set_row_range(ctx, row0: int, rows: int) -> None:
+    _check(load().scgr_set_row_range(ctx, int(row0), int(rows)), ctx)
+
+
+def scgr_step_partials(ctx) -> np.ndarray:
+    out = (c_double * 13)()
+    _check(load().scgr_step_partials(ctx, out), ctx)
+    return np.array(out[:])
+
+
+def scgr_step_apply(ctx, totals) -> None:
+    t = (c_double * 13)(*[float(v) for v in np.asarray(totals, dtype=np.float64).reshape(13)])
+    _check(load().scgr_step_apply(ctx, t), ctx)
+
+
+def scgr_microbench(kind: int, stream=None):
+    """(lane_ops, ms) of one throughput-microbenchmark launch filling the GPU:
+    kind 0 FFMA, 1 fma.f32x2, 2 ex2, 3 sqrt, 4 lg2."""
+    import torch
+    blocks = 8 * torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    out = torch.empty(blocks * 256, dtype=torch.float32, device="cuda")
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream
+    ops = c_int64()
+    ms = c_double()
+    st = load().scgr_microbench(int(kind), blocks, _dev_ptr(out, "float32"), c_void_p(stream), ctypes.byref(ops),
+                                ctypes.byref(ms))
+    if st != SCGR_OK:
+        raise ScgrError(st, "scgr_microbench failed")
+    return int(ops.value), float(ms.value)
+
+
+def scgr_get_plan(ctx) -> dict:
+    out = (c_int * 4)()
+    _check(load().scgr_get_plan(ctx, out), ctx)
+    return {"P": out[0], "tpb": out[1], "splits": out[2], "iblocks": out[3]}
+
+
+def scgr_set_tuning(ctx, key: int, value: int) -> None:
+    _check(load().scgr_set_tuning(ctx, int(key), int(value)), ctx)
+
+
 def scgr_forces(ctx, f4_out) -> None:
     _check(load().scgr_forces(ctx, _dev_ptr(f4_out, "float32", (4,))), ctx)
 
@@ -282,6 +366,52 @@ def scgr_sync(ctx) -> None:
 
 def scgr_launch_count(ctx) -> int:
     return int(load().scgr_launch_count(ctx))
+
+
+# ---- autograd ----------------------------------------------------------------
+
+def _potential_function():
+    import torch
+
+    class Potential(torch.autograd.Function):
+        """U(pose7, Y0) on a context whose template is Y0 (descriptors fixed).
+
+        forward: the potential only; backward: the hand-written adjoint
+        (scgr_potential with gradients), which recomputes the pair tiles
+        instead of storing the N x M pair terms."""
+
+        @staticmethod
+        def forward(fctx, pose7, Y0, handle):
+            fctx.handle = handle
+            fctx.save_for_backward(pose7)
+            fctx.m = Y0.shape[0]
+            fctx.device = Y0.device
+            U, _ = scgr_potential(handle, pose7.detach().double().cpu().numpy(), want_grad=False)
+            return torch.tensor(U, dtype=torch.float64)
+
+        @staticmethod
+        def backward(fctx, gU):
+            (pose7,) = fctx.saved_tensors
+            gx = torch.empty((fctx.m, 3), dtype=torch.float32, device=fctx.device)
+            _, g7 = scgr_potential(fctx.handle, pose7.detach().double().cpu().numpy(), want_grad=True,
+                                   grad_xyz_out=gx)
+            g = float(gU)
+            gp = torch.from_numpy(g7).to(pose7.dtype) * g
+            return gp.to(pose7.device), (gx * g).to(fctx.device), None
+
+    return Potential
+
+
+_POTENTIAL = None
+
+
+def potential(pose7, Y0, handle):
+    """Differentiable U(pose7, Y0): torch.autograd.Function around the
+    hand-written adjoint.  `handle` is a context whose template is Y0."""
+    global _POTENTIAL
+    if _POTENTIAL is None:
+        _POTENTIAL = _potential_function()
+    return _POTENTIAL.apply(pose7, Y0, handle)
 
 
 # ---- convenience wrapper ----------------------------------------------------

@@ -21,9 +21,11 @@ def rel_l2(a, b):
 class Gpu:
     """One context over device copies of X and Y0."""
 
-    def __init__(self, X, Y0, **prm):
+    def __init__(self, X, Y0, tune=None, **prm):
         self.params = scgr.scgr_default_params(**prm)
         self.ctx = scgr.scgr_create(self.params)
+        for key, value in (tune or {}).items():
+            scgr.scgr_set_tuning(self.ctx, key, value)
         self.X = torch.from_numpy(np.ascontiguousarray(X, np.float32)).cuda()
         self.Y0 = torch.from_numpy(np.ascontiguousarray(Y0, np.float32)).cuda()
         self.n, self.m = len(X), len(Y0)

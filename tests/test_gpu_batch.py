@@ -1,0 +1,117 @@
+"""Batching form on the GPU: many registrations of uneven sizes in one call
+(scgr_batch_run) give each pair the pose that a one-pair-per-call run gives,
+within the pose tolerance (0.5 degrees, 1e-3 of the diagonal, 1e-5 relative
+scale), and match the FP64 oracle on small pairs.  Graph replay of the batch
+loop is bit-identical to eager launches."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_1902_01061_gb300 import scgr, synth
+from tests.gpu_helpers import Gpu, rot_err_deg
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib(scgr_lib):
+    return scgr_lib
+
+
+def make_pairs(sizes, seed=5):
+    rng = np.random.default_rng(seed)
+    out = []
+    for i, n in enumerate(sizes):
+        surf = synth.EllipsoidUnion.random(rng, 3)
+        X = surf.sample_surface(rng, n).astype(np.float32)
+        R = synth.rotation_matrix(synth.random_unit(rng), float(rng.uniform(5, 40)))
+        s = float(rng.uniform(0.8, 1.25))
+        nout = int(0.1 * n) if i % 2 else 0
+        Y = s * X.astype(np.float64) @ R + rng.uniform(-0.2, 0.2, 3)
+        if nout:
+            Y = np.concatenate([Y, rng.uniform(Y.min(0), Y.max(0), size=(nout, 3))])
+        out.append((X, Y.astype(np.float32)))
+    return out
+
+
+def run_batch(pairs, iters, **prm):
+    ctx = scgr.scgr_create(scgr.scgr_default_params(**prm))
+    try:
+        ro = np.cumsum([0] + [len(x) for x, _ in pairs])
+        to = np.cumsum([0] + [len(y) for _, y in pairs])
+        Xc = torch.from_numpy(np.concatenate([x for x, _ in pairs])).cuda()
+        Yc = torch.from_numpy(np.concatenate([y for _, y in pairs])).cuda()
+        res = scgr.scgr_batch_run(ctx, ro, Xc, to, Yc, iters)
+        launches = scgr.scgr_launch_count(ctx)
+    finally:
+        scgr.scgr_destroy(ctx)
+    return res, launches
+
+
+def close(a, b, diag, rot=0.5, t=1e-3, s=1e-5):
+    Ra, ta, sa = a.as_numpy()
+    Rb, tb, sb = b.as_numpy() if hasattr(b, "as_numpy") else b
+    return rot_err_deg(Ra, Rb) <= rot and np.linalg.norm(ta - tb) <= t * diag and abs(sa - sb) <= s * abs(sb)
+
+
+@pytest.mark.parametrize("p", [2.0, 1.0])
+def test_batch_matches_single_pair_runs(p):
+    pairs = make_pairs([600, 257, 1500, 16, 2100, 513, 90])
+    iters = 25
+    res, launches = run_batch(pairs, iters, p=p)
+    assert len(res) == len(pairs)
+    for (X, Y), r in zip(pairs, res):
+        with Gpu(X, Y, p=p) as g:
+            single = g.run(iters)
+        assert r.iterations == iters
+        assert close(r, single, synth.bbox_diag(X)), (r.as_numpy(), single.as_numpy())
+
+
+def test_batch_matches_oracle_on_small_pairs():
+    pairs = make_pairs([300, 140, 420], seed=9)
+    iters = 20
+    res, _ = run_batch(pairs, iters)
+    for (X, Y), r in zip(pairs, res):
+        o = O.register(X, Y, O.Params(), iterations=iters)
+        assert close(r, (o["R"], o["t"], o["s"]), synth.bbox_diag(X))
+
+
+def test_batch_graph_replay_equals_eager():
+    pairs = make_pairs([400, 1200, 33, 800], seed=13)
+    a, la = run_batch(pairs, 15)
+    b, lb = run_batch(pairs, 15, use_graph=1)
+    assert la == lb
+    for ra, rb in zip(a, b):
+        assert list(ra.R) == list(rb.R) and list(ra.t) == list(rb.t) and ra.s == rb.s
+
+
+def test_batch_chunk_tuning_keeps_results_close():
+    pairs = make_pairs([3000, 700], seed=17)
+    a, _ = run_batch(pairs, 10)
+    ctx = scgr.scgr_create(scgr.scgr_default_params())
+    try:
+        scgr.scgr_set_tuning(ctx, scgr.SCGR_TUNE_BATCH_CHUNK_TILES, 3)
+        ro = np.cumsum([0] + [len(x) for x, _ in pairs])
+        to = np.cumsum([0] + [len(y) for _, y in pairs])
+        b = scgr.scgr_batch_run(ctx, ro, torch.from_numpy(np.concatenate([x for x, _ in pairs])).cuda(), to,
+                                torch.from_numpy(np.concatenate([y for _, y in pairs])).cuda(), 10)
+        with pytest.raises(scgr.ScgrError):
+            scgr.scgr_set_tuning(ctx, scgr.SCGR_TUNE_BATCH_CHUNK_TILES, 0)
+    finally:
+        scgr.scgr_destroy(ctx)
+    for (X, _), ra, rb in zip(pairs, a, b):
+        assert close(ra, rb, synth.bbox_diag(X))
+
+
+def test_batch_rejects_bad_offsets():
+    ctx = scgr.scgr_create(scgr.scgr_default_params())
+    try:
+        X = torch.zeros((40, 3), dtype=torch.float32, device="cuda")
+        with pytest.raises(scgr.ScgrError) as e:
+            scgr.scgr_batch_run(ctx, [0, 20, 40], X, [0, 30, 40], X, 3)    # second template has 10 < 16
+        assert e.value.status == 1
+        with pytest.raises(scgr.ScgrError):
+            scgr.scgr_batch_run(ctx, [1, 40], X, [0, 40], X, 3)            # offsets must start at 0
+    finally:
+        scgr.scgr_destroy(ctx)

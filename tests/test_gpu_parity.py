@@ -56,6 +56,38 @@ def test_knn_bit_exact_and_curvature(name):
         assert g.sigma() == pytest.approx(O.sigma_auto(aX), rel=1e-9)
 
 
+def degenerate_clouds():
+    rng = np.random.default_rng(77)
+    plane = np.c_[rng.uniform(-1, 1, (700, 2)), np.zeros(700)].astype(np.float32)
+    line = np.c_[np.linspace(0, 1, 300), np.linspace(0, 2, 300), np.zeros(300)].astype(np.float32)
+    same = np.tile(np.array([[0.5, -0.25, 2.0]], np.float32), (40, 1))
+    return {"plane": plane, "line": line, "coincident": same}
+
+
+@pytest.mark.parametrize("name", list(knn_cases().keys()) + list(degenerate_clouds().keys()))
+def test_grid_knn_bit_exact(name):
+    """The exact grid search, forced on small clouds, equals the oracle."""
+    if name in degenerate_clouds():
+        X = degenerate_clouds()[name]
+        Y0, k = X[::-1].copy(), 16
+    else:
+        X, Y0, k = knn_cases()[name]
+    with Gpu(X, Y0, k=k, tune={scgr.SCGR_TUNE_KNN_GRID_MIN: 0}) as g:
+        np.testing.assert_array_equal(g.knn(0), O.knn(X, k))
+        np.testing.assert_array_equal(g.knn(1), O.knn(Y0, k))
+
+
+def test_grid_knn_equals_brute_force_on_gpu():
+    sc = synth.scale_case()
+    X, Y0 = sc.X, sc.Y0
+    with Gpu(X, Y0, tune={scgr.SCGR_TUNE_KNN_GRID_MIN: 0}) as g:
+        a0, a1 = g.knn(0), g.knn(1)
+    with Gpu(X, Y0, tune={scgr.SCGR_TUNE_KNN_GRID_MIN: 1 << 30}) as g:
+        b0, b1 = g.knn(0), g.knn(1)
+    np.testing.assert_array_equal(a0, b0)
+    np.testing.assert_array_equal(a1, b1)
+
+
 def force_check(g, X, Y0, aX, aY, sigma, p, g_mode, rows=None):
     f4 = g.forces()
     fr, Wr = O.forces_rows(Y0, X, aY, aX, sigma, p, g_mode, rows)
@@ -226,7 +258,7 @@ def test_graph_replay_equals_eager():
 
 def test_force_timing_counts_launches():
     case = synth.mild(n=500)
-    with Gpu(case.X, case.Y0) as g:
+    with Gpu(case.X, case.Y0, p=2.0) as g:
         scgr.scgr_set_force_timing(g.ctx, True)
         before = scgr.scgr_launch_count(g.ctx)
         g.run(7)

@@ -1,0 +1,69 @@
+"""Every force-kernel tile shape the autotuner can pick gives oracle-parity
+forces, tuning in place keeps descriptors and pose, and the autotuner's
+cache round-trips."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1902_01061_gb300 import autotune, scgr, synth
+from tests.gpu_helpers import Gpu, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib(scgr_lib):
+    return scgr_lib
+
+
+@pytest.mark.parametrize("P,tpb,splits", [(1, 128, 0), (2, 128, 0), (4, 128, 0), (1, 256, 0), (2, 256, 0),
+                                          (4, 256, 0), (4, 256, 1), (2, 128, 7)])
+def test_every_tile_shape_matches_oracle(P, tpb, splits):
+    sc = synth.scale_case()
+    X = sc.X[synth.subsample(sc.X, 2600, 61)]
+    Y0 = sc.Y0[synth.subsample(sc.Y0, 1777, 62)]
+    d = O.descriptors(X, Y0, O.Params(p=2.0))
+    f_ref, W_ref = O.forces(Y0, X, d["aY"], d["aX"], d["sigma"], 2.0, 1)
+    with Gpu(X, Y0, p=2.0) as g:
+        scgr.scgr_set_tuning(g.ctx, scgr.SCGR_TUNE_FORCE_P, P)
+        scgr.scgr_set_tuning(g.ctx, scgr.SCGR_TUNE_FORCE_TPB, tpb)
+        scgr.scgr_set_tuning(g.ctx, scgr.SCGR_TUNE_FORCE_SPLITS, splits)
+        plan = scgr.scgr_get_plan(g.ctx)
+        assert (plan["P"], plan["tpb"]) == (P, tpb)
+        if splits:
+            assert plan["splits"] == splits
+        f4 = g.forces()
+    assert rel_l2(f4[:, :3], f_ref) <= 1e-5
+    assert rel_l2(f4[:, 3], W_ref) <= 1e-5
+
+
+def test_autotuner_picks_and_caches(tmp_path, monkeypatch):
+    monkeypatch.setenv("SCGR_TUNE_CACHE", str(tmp_path / "tune.json"))
+    case = synth.mild(n=3000)
+    with Gpu(case.X, case.Y0, p=2.0) as g:
+        best = autotune.tune_single(g.ctx, len(case.X), len(case.Y0), 2.0,
+                                    candidates=[(1, 128, 0), (2, 256, 0)], reps=2)
+        plan = scgr.scgr_get_plan(g.ctx)
+        assert (plan["P"], plan["tpb"]) == (best["P"], best["tpb"])
+        assert len(best["tried"]) == 2 and best["ms"] > 0
+    with Gpu(case.X, case.Y0, p=2.0) as g:
+        hit = autotune.apply_cached_single(g.ctx, len(case.X), len(case.Y0), 2.0)
+        assert hit is not None and hit["P"] == best["P"]
+        plan = scgr.scgr_get_plan(g.ctx)
+        assert (plan["P"], plan["tpb"]) == (best["P"], best["tpb"])
+
+
+@pytest.mark.parametrize("use_graph", [0, 1])
+def test_p1_force_sums_reused_bit_identically(use_graph):
+    """p = 1: the pose-free force sums computed once per run give the same
+    bits as recomputing them every iteration, with fewer launches."""
+    case = synth.mild(n=1200)
+    with Gpu(case.X, case.Y0, p=1.0, use_graph=use_graph) as g:
+        a = g.run(30)
+        na = scgr.scgr_launch_count(g.ctx)
+    with Gpu(case.X, case.Y0, p=1.0, use_graph=use_graph) as g:
+        scgr.scgr_set_tuning(g.ctx, scgr.SCGR_TUNE_REUSE_POSE_FREE, 0)
+        b = g.run(30)
+        nb = scgr.scgr_launch_count(g.ctx)
+    assert list(a.R) == list(b.R) and list(a.t) == list(b.t) and a.s == b.s
+    assert nb - na == 29

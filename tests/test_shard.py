@@ -1,0 +1,97 @@
+"""Template-row sharding (one registration over several ranks): the host
+logic of paper_1902_01061_gb300.shard with world_size-2 gloo ranks on CPU.
+Each rank's partial sums come from the FP64 oracle (test-side backend), the
+shard module reduces them in rank order and both ranks apply the totals."""
+import os
+import socket
+
+import numpy as np
+import pytest
+import torch.multiprocessing as mp
+
+import oracle as O
+from paper_1902_01061_gb300 import shard, synth
+
+
+class OracleRowShard:
+    """Rank compute from the oracle: partial sums of rows [row0, row0+rows)."""
+
+    def __init__(self, X, Y0, prm, row0, rows, E):
+        self.X = np.asarray(X, np.float64)
+        self.Y = np.asarray(Y0, np.float64).copy()
+        self.prm, self.E, self.it = prm, E, 0
+        self.rows = np.arange(row0, row0 + rows)
+        self.desc = O.descriptors(X, Y0, prm)
+        self.eX = O.cloud_stats(self.X)[2]
+
+    def step_partials(self):
+        return O.partial_sums(self.Y, self.X, self.desc, self.prm, self.rows)
+
+    def step_apply(self, totals):
+        self.Y, _ = O.update_from_totals(self.Y, totals, self.prm, self.it, self.E, self.eX)
+        self.it += 1
+
+
+def test_update_from_totals_equals_step_once():
+    case = synth.mild(n=250)
+    prm = O.Params()
+    desc = O.descriptors(case.X, case.Y0, prm)
+    X = case.X.astype(np.float64)
+    Y = case.Y0.astype(np.float64)
+    eX = O.cloud_stats(X)[2]
+    a, _ = O.step_once(Y, X, desc, prm, 3, 10, eX)
+    halves = [np.arange(0, 100), np.arange(100, 250)]
+    tot = sum(O.partial_sums(Y, X, desc, prm, r) for r in halves)
+    b, _ = O.update_from_totals(Y, tot, prm, 3, 10, eX)
+    np.testing.assert_allclose(b, a, atol=1e-12)
+
+
+def test_row_partition_covers_rows_once():
+    for m in (1, 7, 100, 1001):
+        for world in (1, 2, 3, 8):
+            if world > m:
+                continue
+            parts = [shard.row_partition(m, world, r) for r in range(world)]
+            assert parts[0][0] == 0 and sum(r for _, r in parts) == m
+            for (a0, ar), (b0, _) in zip(parts, parts[1:]):
+                assert a0 + ar == b0
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _worker(rank, world, port, iters, q):
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        case = synth.mild(n=300)
+        prm = O.Params(E=iters)
+        row0, rows = shard.row_partition(len(case.Y0), world, rank)
+        be = OracleRowShard(case.X, case.Y0, prm, row0, rows, iters)
+        shard.ShardedRegistration(be).run(iters)
+        q.put((rank, be.Y))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_match_single_rank():
+    iters = 5
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, iters, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    out = dict(q.get(timeout=300) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    np.testing.assert_array_equal(out[0], out[1])          # identical totals -> identical templates
+    case = synth.mild(n=300)
+    ref = O.register(case.X, case.Y0, O.Params(E=iters), iterations=iters)
+    np.testing.assert_allclose(out[0], ref["Y"], atol=1e-10)
