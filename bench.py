@@ -203,6 +203,10 @@ def bench_batch(args, scgr, torch, dev, steps, warmup):
     stream = torch.cuda.current_stream()
     ctx = scgr.scgr_create(params, stream)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    tuned = None
+    if not args.no_autotune:
+        from paper_1902_01061_gb300 import autotune
+        tuned = autotune.tune_batch(ctx, ro, Xc, to, Yc, 2.0, iterations=3)
 
     def one_batch():
         scgr.scgr_batch_run(ctx, ro, Xc, to, Yc, iters)
@@ -249,6 +253,7 @@ def bench_batch(args, scgr, torch, dev, steps, warmup):
             "launches_per_batch": int(batch_launches),
             "one_call_per_pair_registrations_per_s": len(pairs) / single_s,
             "speedup_vs_one_call_per_pair": single_s / batch_s,
+            "autotuned": tuned,
             "one_call_per_pair": "scgr_set_reference/template + compute_descriptors + run(100) + get_result "
                                  "per pair, eager launches",
             "timing": "host wall clock around each synchronising call, L2 flushed before each"}
@@ -306,6 +311,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-rows", type=int, default=48)
     ap.add_argument("--no-batch", action="store_true", help="skip the 512-pair batched leg")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default tile shapes")
+    ap.add_argument("--plan", default=None, help="pin the force tile shape 'P,TPB[,OCC]' (no autotuning), e.g. 2,256,1")
     args = ap.parse_args()
     ws, rank, local = dist_env()
     if args.impl == "reference":
@@ -335,6 +342,21 @@ def main():
     stream = torch.cuda.current_stream()
     ctx = scgr.scgr_create(params, stream)
     num_sms = torch.cuda.get_device_properties(dev).multi_processor_count
+
+    tuned = None
+    if args.plan:
+        vals = [int(v) for v in args.plan.split(",")]
+        P_, T_, O_ = vals[0], vals[1], (vals[2] if len(vals) > 2 else 0)
+        scgr.scgr_set_tuning(ctx, scgr.SCGR_TUNE_FORCE_P, P_)
+        scgr.scgr_set_tuning(ctx, scgr.SCGR_TUNE_FORCE_TPB, T_)
+        scgr.scgr_set_tuning(ctx, scgr.SCGR_TUNE_FORCE_OCC, O_)
+        tuned = {"P": P_, "tpb": T_, "occ": O_, "pinned": True}
+    elif not args.no_autotune:
+        from paper_1902_01061_gb300 import autotune
+        scgr.scgr_set_reference(ctx, Xd)
+        scgr.scgr_set_template(ctx, Yd)
+        scgr.scgr_compute_descriptors(ctx)
+        tuned = autotune.tune_single(ctx, n, m, 2.0, reps=2)
 
     def step_device():
         scgr.scgr_set_reference(ctx, Xd)
@@ -436,7 +458,7 @@ def main():
         "ms_per_iteration": ms_per_step / iters,
         "pct_fp32_peak": 100.0 * roofline["frac"],
         "config": {"workload": wl["desc"], "N": n, "M": m, "iterations": iters, "p": 2.0, "g_mode": 1,
-                   "k": 16, "pairs_per_step": pairs_per_step, "l2": "flushed between steps (256 MB write)",
+                   "k": 16, "pairs_per_step": pairs_per_step, "autotuned": tuned, "l2": "flushed between steps (256 MB write)",
                    "parallelism": f"replicas x{ws}"},
         "gpu_launches": launches,
         "wall_s_timed_region": wall,

@@ -73,6 +73,10 @@ typedef struct {
   double time;     /* literal-mode time step of Eq. 5.5 (default 1) */
   int scale_mode;  /* 0: c = sqrt(eX/eY) (default); 1: c = eX/eY as printed; 2: c = 1 (rigid) */
   int use_graph;   /* 1: scgr_run captures its iteration loop in a CUDA graph and replays it */
+  int neigh_mode;  /* curvature neighbourhood: 0 the k nearest neighbours (default); 1 all points within
+                      radius radius_scale * sqrt(e) of the point, e the largest covariance eigenvalue of its
+                      cloud (Sec. IV: radius sqrt(eX) for the reference, sqrt(eY) for the template) */
+  double radius_scale; /* radius multiplier of neigh_mode 1 (default 1) */
 } scgr_params;
 
 /* Result of a registration (Eq. 6, Eq. 8, Eq. 9): moved = s * Y0 @ R + t. */
@@ -169,6 +173,32 @@ SCGR_EXPORT scgr_status scgr_get_curvature64(scgr_ctx* ctx, int which, double* a
  * scgr_compute_descriptors. */
 SCGR_EXPORT scgr_status scgr_set_curvature(scgr_ctx* ctx, int which, const double* a64_dev);
 
+/* Pyramidal schedule (Sec. IV: for noisy data the neighbourhood size and
+ * sigma shrink as the iterations proceed).  Recompute both clouds'
+ * curvature with a new neighbourhood - k nearest (neigh_mode 0; 3 <= k <= 32)
+ * or radius_scale * sqrt(e) (neigh_mode 1) - and set
+ * sigma = sigma_scale * (params.sigma if > 0, else the population std of the
+ * new reference curvatures).  The pose and the position in the Eq. 12
+ * schedule are kept, so scgr_run continues the registration with the new
+ * descriptors.  STATE before scgr_compute_descriptors; INVALID_ARG for
+ * k outside [3, 32] or non-positive scales. */
+SCGR_EXPORT scgr_status scgr_set_neighbourhood(scgr_ctx* ctx, int k, double radius_scale, double sigma_scale);
+
+/* Nearest reference point of q_dev [nq][3] (float32): index int32 [nq] and
+ * float32 key (squared distance, the kNN key of R1) [nq]; either output may
+ * be NULL.  Ties go to the lower index.  Enqueued.  STATE without a
+ * reference. */
+SCGR_EXPORT scgr_status scgr_nearest(scgr_ctx* ctx, const float* q_dev, int64_t nq, int32_t* idx_dev,
+                                     float* key_dev);
+
+/* Change detection after registration (abstract; Sec. V, real scenes: parts
+ * of the template that moved between captures stay unaligned).  For every
+ * point of the moved template s Y0 R + t, mask_dev[i] = 1 (uint8) if its
+ * nearest reference point is farther than `threshold`, else 0; dist_dev
+ * (nullable, float32 [m]) receives that distance.  Enqueued.  STATE before
+ * descriptors. */
+SCGR_EXPORT scgr_status scgr_change_mask(scgr_ctx* ctx, double threshold, uint8_t* mask_dev, float* dist_dev);
+
 /* Forces at the current pose without updating it: per template point
  * (fx, fy, fz, W) as float32 [m][4], where f is Eq. 5 without the factor G
  * (f_i = -sum_j g(s_ij) h(d_ij) n_ij) and W_i = sum_j g(s_ij) d_ij^(p-1).
@@ -188,6 +218,14 @@ SCGR_EXPORT scgr_status scgr_forces(scgr_ctx* ctx, float* f4_dev);
  * descriptors; INVALID_ARG for a non-finite pose or s <= 0. */
 SCGR_EXPORT scgr_status scgr_potential(scgr_ctx* ctx, const double pose7[7], double* U_out,
                                        double* grad_pose7, float* grad_xyz_dev);
+
+/* Vector-Jacobian product of the force field at the current pose:
+ * grad_i = (d f_i / d Y_i)^T v_i with f_i of Eq. 5 (without G; descriptors
+ * fixed).  f_i depends only on Y_i, and
+ * d f_i / d Y_i = -aY_i sum_j w_ij [I + (p - 1) r_ij r_ij^T / d_ij^2].
+ * v_dev and grad_dev are float32 [m][3] device arrays.  The reference tiles
+ * are recomputed (no N x M storage).  Enqueued.  STATE before descriptors. */
+SCGR_EXPORT scgr_status scgr_force_vjp(scgr_ctx* ctx, const float* v_dev, float* grad_dev);
 
 /* Checkpoint / resume of the iteration state.  Both synchronise. */
 SCGR_EXPORT scgr_status scgr_get_state(scgr_ctx* ctx, scgr_state* host_out);
@@ -273,6 +311,8 @@ SCGR_EXPORT scgr_status scgr_step_apply(scgr_ctx* ctx, const double tot13[13]);
 #define SCGR_TUNE_FORCE_P 3           /* force kernel template points per thread: 0 auto, 1, 2, 4 */
 #define SCGR_TUNE_FORCE_TPB 4         /* force kernel threads per block: 0 auto, 128, 256 */
 #define SCGR_TUNE_FORCE_SPLITS 5      /* force kernel reference splits: 0 auto (wave-filling), >= 1 */
+#define SCGR_TUNE_FORCE_OCC 7         /* 1: force kernel variant with a tighter register budget and more
+                                         resident blocks per SM (3 at 256 threads, 4 at 128); 0 default */
 #define SCGR_TUNE_REUSE_POSE_FREE 6   /* 1 (default): for p = 1, whose pair weights do not depend on the
                                          pose, scgr_run computes the force sums once per call and reuses
                                          them in its later iterations (bit-identical); 0: every iteration */
@@ -282,8 +322,9 @@ SCGR_EXPORT scgr_status scgr_step_apply(scgr_ctx* ctx, const double tot13[13]);
  * value. */
 SCGR_EXPORT scgr_status scgr_set_tuning(scgr_ctx* ctx, int key, int value);
 /* The force plan in use: out = {points per thread, threads per block,
- * reference splits, template blocks}.  STATE before descriptors. */
-SCGR_EXPORT scgr_status scgr_get_plan(scgr_ctx* ctx, int out[4]);
+ * reference splits, template blocks, occupancy variant}.  STATE before
+ * descriptors. */
+SCGR_EXPORT scgr_status scgr_get_plan(scgr_ctx* ctx, int out[5]);
 
 /* Throughput microbenchmark of the units that bound the force kernel (no
  * paper counterpart; roofline evidence).  kind: 0 scalar FFMA, 1 packed

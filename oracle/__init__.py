@@ -20,12 +20,22 @@ Functions and their pins (the tests under ``tests/test_oracle_*.py``):
                        brute force and an exact-shift invariance.
 * ``curvature``      - Sec. III-A / IV; pinned to hand cases (plane, line,
                        axis star = 1/3, box corners = 1/14) and invariances.
+* ``curvature_radius`` - the radius neighbourhood of Sec. IV; pinned to the
+                       same hand cases (plane, axis star) and to the k-nearest
+                       curvature when the radius neighbourhood is the whole
+                       cloud.
+* ``register_pyramid`` - the pyramidal schedule of Sec. IV; pinned to
+                       ``register`` for a single level.
+* ``nearest`` / ``change_mask`` - the change-detection post-pass; pinned to
+                       the scalar brute force of the kNN pins (k = 1).
 * ``sigma_auto``     - R3; pinned to a closed form (two-valued population).
 * ``forces``         - Eq. 5 with Eq. 3, 10, 11; pinned to the two-point hand
                        case, the p=1 closed forms, Newton's third law,
                        rotation/translation equivariance and scaling.
 * ``potential`` / ``potential_grad`` - the potential whose negative gradient is
                        Eq. 5; pinned by central finite differences.
+* ``force_vjp``      - the force field's vector-Jacobian product; pinned by
+                       central differences of ``forces``.
 * ``g_schedule``     - Eq. 12; pinned to its closed-form values.
 * ``kabsch``         - Eq. 6; pinned to exact recovery of a known rotation,
                        including the reflection case.
@@ -58,4 +68,9 @@ from .scgr_oracle import (  # noqa: F401
     step_once,
     partial_sums,
     update_from_totals,
+    curvature_radius,
+    register_pyramid,
+    nearest,
+    change_mask,
+    force_vjp,
 )

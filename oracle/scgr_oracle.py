@@ -69,6 +69,8 @@ class Params:
     eta0: float = 0.5       # normalized step fraction (R6)
     time: float = 1.0       # literal-mode time step of Eq. 5.5
     scale_mode: int = 0     # 0: c = sqrt(eX/eY) (R8); 1: c = eX/eY as printed; 2: c = 1
+    neigh_mode: int = 0     # 0: k nearest neighbours (R2); 1: radius radius_scale*sqrt(e) (Sec. IV)
+    radius_scale: float = 1.0
 
 
 # ----------------------------------------------------------------- descriptors
@@ -126,6 +128,30 @@ def curvature(P, nbr: np.ndarray) -> np.ndarray:
     return a
 
 
+def curvature_radius(P, radius_scale: float = 1.0) -> np.ndarray:
+    """Curvature over the radius neighbourhood of Sec. IV: every point whose
+    distance from p is at most radius_scale * sqrt(e), e the largest
+    eigenvalue of the cloud's 1/n covariance.  Membership is decided on the
+    float32 key of R1 against float32(radius_scale^2 e) (same precision as the
+    GPU); the covariance of the members (1/|N|) is float64."""
+    P32 = np.ascontiguousarray(P, dtype=np.float32)
+    P64 = P32.astype(np.float64)
+    _, _, e = cloud_stats(P64)
+    r2 = np.float32(radius_scale * radius_scale * e)
+    a = np.zeros(len(P32))
+    for i in range(len(P32)):
+        dx = P32[i, 0] - P32[:, 0]
+        dy = P32[i, 1] - P32[:, 1]
+        dz = P32[i, 2] - P32[:, 2]
+        key = (dx * dx + dy * dy) + dz * dz
+        Q = P64[key <= r2]
+        D = Q - Q.mean(axis=0)
+        C = D.T @ D / len(Q)
+        tr = np.trace(C)
+        a[i] = max(np.linalg.eigvalsh(C)[0], 0.0) / tr if tr > 0 else 0.0
+    return a
+
+
 def sigma_auto(aX) -> float:
     """Reading R3: population std of the reference curvatures (1 if ~0)."""
     sd = float(np.std(np.asarray(aX, dtype=np.float64)))
@@ -141,13 +167,19 @@ def cloud_stats(P):
     return mu, C, float(np.linalg.eigvalsh(C)[-1])
 
 
-def descriptors(X, Y0, prm: Params):
-    """The one-time descriptor pass: kNN, curvature of both clouds, sigma."""
-    nX = knn(X, prm.k)
-    nY = knn(Y0, prm.k)
-    aX = curvature(X, nX)
-    aY = curvature(Y0, nY)
-    sigma = prm.sigma if prm.sigma > 0 else sigma_auto(aX)
+def descriptors(X, Y0, prm: Params, sigma_scale: float = 1.0):
+    """The one-time descriptor pass: neighbourhoods (k nearest, or the radius
+    of Sec. IV), curvature of both clouds, sigma (times sigma_scale)."""
+    if prm.neigh_mode == 1:
+        nX = nY = None
+        aX = curvature_radius(X, prm.radius_scale)
+        aY = curvature_radius(Y0, prm.radius_scale)
+    else:
+        nX = knn(X, prm.k)
+        nY = knn(Y0, prm.k)
+        aX = curvature(X, nX)
+        aY = curvature(Y0, nY)
+    sigma = (prm.sigma if prm.sigma > 0 else sigma_auto(aX)) * sigma_scale
     return dict(knnX=nX, knnY=nY, aX=aX, aY=aY, sigma=sigma)
 
 
@@ -217,6 +249,25 @@ def potential_grad(Y, X, aY, aX, sigma, p, g_mode):
     """dU/dY (M x 3) = -f (Eq. 5)."""
     f, _ = forces(Y, X, aY, aX, sigma, p, g_mode)
     return -f
+
+
+def force_vjp(Y, X, aY, aX, sigma, p, g_mode, v):
+    """(d f_i / d Y_i)^T v_i for the force of Eq. 5 (descriptors fixed): with
+    r = Y_i - X_j, d = |r| and w = g d^(p-1), f_i = -sum_j w r gives
+    d f_i / d Y_i = -sum_j [w I + r (dw/dY_i)^T], dw/dY_i = g (p-1) d^(p-3) r."""
+    Y = np.asarray(Y, dtype=np.float64)
+    X = np.asarray(X, dtype=np.float64)
+    out = np.zeros((len(Y), 3))
+    for i in range(len(Y)):
+        r, d, g = _pair_terms(Y[i:i + 1], X, np.asarray(aY, dtype=np.float64)[i:i + 1],
+                              np.asarray(aX, dtype=np.float64), sigma, p, g_mode)
+        r, d, g = r[0], d[0], g[0]
+        live = d > 0
+        w = np.where(live, g * np.where(live, d, 1.0) ** (p - 1.0), g if p == 1.0 else 0.0)
+        dw = np.where(live, g * (p - 1.0) * np.where(live, d, 1.0) ** (p - 3.0), 0.0)
+        J = -(w.sum() * np.eye(3) + (r * dw[:, None]).T @ r)
+        out[i] = J.T @ np.asarray(v, dtype=np.float64)[i]
+    return out
 
 
 def rodrigues(omega):
@@ -338,6 +389,57 @@ def step_once(Y, X, desc, prm: Params, it: int, E: int, eX: float):
                 degenerate=degenerate, Chat=Chat, f=f, Wi=Wi,
                 lam_min_sym=float(np.linalg.eigvalsh(sym)[0]))
     return Ynext, info
+
+
+def nearest(Q, X):
+    """Nearest point of X for every query of Q under the float32 key of R1,
+    ties to the lower index: (index, key)."""
+    Q = np.ascontiguousarray(Q, dtype=np.float32)
+    X = np.ascontiguousarray(X, dtype=np.float32)
+    idx = np.empty(len(Q), dtype=np.int32)
+    key = np.empty(len(Q), dtype=np.float32)
+    for i in range(len(Q)):
+        dx = Q[i, 0] - X[:, 0]
+        dy = Q[i, 1] - X[:, 1]
+        dz = Q[i, 2] - X[:, 2]
+        k = (dx * dx + dy * dy) + dz * dz
+        j = int(np.argmin(k))              # first minimum: the lowest index among ties
+        idx[i], key[i] = j, k[j]
+    return idx, key
+
+
+def change_mask(moved, X, threshold: float):
+    """Change detection after registration (abstract, Sec. V): a moved
+    template point is 'changed' if its nearest reference point is farther
+    than the threshold (decided on the float32 key against threshold^2)."""
+    _, key = nearest(moved, X)
+    return (key > np.float32(threshold * threshold)).astype(np.uint8), np.sqrt(key.astype(np.float32))
+
+
+def register_pyramid(X, Y0, prm: Params, levels):
+    """Pyramidal schedule (Sec. IV): `levels` = [(iterations, k, radius_scale,
+    sigma_scale), ...].  Each level recomputes the descriptors of both clouds
+    with its neighbourhood and sigma, then continues the iterations from the
+    current template (Eq. 9) and the current position in the Eq. 12 schedule
+    (E = all levels' iterations unless prm.E is set)."""
+    X64 = np.asarray(X, dtype=np.float64)
+    Y = np.asarray(Y0, dtype=np.float64).copy()
+    total = sum(lv[0] for lv in levels)
+    E = prm.E if prm.E > 0 else total
+    _, _, eX = cloud_stats(X64)
+    s, R, t = 1.0, np.eye(3), np.zeros(3)
+    it = 0
+    for iters, k, rscale, sscale in levels:
+        lp = replace(prm, k=k, radius_scale=rscale)
+        desc = descriptors(X, Y0, lp, sigma_scale=sscale)
+        for _ in range(iters):
+            Y, info = step_once(Y, X64, desc, lp, it, E, eX)
+            c, Rinc, mu, dvec = info["c"], info["Rinc"], info["mu"], info["d"]
+            t = c * (t - mu) @ Rinc + mu + dvec
+            R = polar(R @ Rinc)
+            s = c * s
+            it += 1
+    return dict(R=R, t=t, s=s, Y=Y, iterations=it, E=E)
 
 
 def partial_sums(Y, X, desc, prm: Params, rows):

@@ -16,7 +16,8 @@ import time
 
 from . import scgr
 
-SINGLE_CANDIDATES = [(P, tpb, 0) for P in (1, 2, 4) for tpb in (128, 256)]
+SINGLE_CANDIDATES = [(P, tpb, occ) for P in (1, 2, 4) for tpb in (128, 256) for occ in (0, 1)
+                     if not (P == 4 and tpb == 256 and occ == 1)]
 BATCH_CHUNKS = (4, 8, 16, 32)
 
 
@@ -80,22 +81,25 @@ def time_forces(ctx, m: int, reps: int = 3) -> float:
     return ms / max(n, 1)
 
 
-def tune_single(ctx, n: int, m: int, p: float, candidates=None, reps: int = 3, store: bool = True) -> dict:
-    """Time each (P, threads, splits) candidate on a context whose descriptors
-    are computed; leave the best in place and return it."""
-    results = []
-    for P, tpb, splits in candidates or SINGLE_CANDIDATES:
-        scgr.scgr_set_tuning(ctx, scgr.SCGR_TUNE_FORCE_P, P)
-        scgr.scgr_set_tuning(ctx, scgr.SCGR_TUNE_FORCE_TPB, tpb)
-        scgr.scgr_set_tuning(ctx, scgr.SCGR_TUNE_FORCE_SPLITS, splits)
-        results.append((time_forces(ctx, m, reps), P, tpb, splits, scgr.scgr_get_plan(ctx)))
-    results.sort(key=lambda r: r[0])
-    best_ms, P, tpb, splits, plan = results[0]
+def _apply(ctx, P: int, tpb: int, occ: int) -> None:
     scgr.scgr_set_tuning(ctx, scgr.SCGR_TUNE_FORCE_P, P)
     scgr.scgr_set_tuning(ctx, scgr.SCGR_TUNE_FORCE_TPB, tpb)
-    scgr.scgr_set_tuning(ctx, scgr.SCGR_TUNE_FORCE_SPLITS, splits)
-    best = {"P": P, "tpb": tpb, "splits": splits, "ms": best_ms, "plan": plan,
-            "tried": [{"P": r[1], "tpb": r[2], "splits": r[3], "ms": r[0]} for r in results],
+    scgr.scgr_set_tuning(ctx, scgr.SCGR_TUNE_FORCE_OCC, occ)
+
+
+def tune_single(ctx, n: int, m: int, p: float, candidates=None, reps: int = 3, store: bool = True) -> dict:
+    """Time each (P, threads, occupancy variant) candidate on a context whose
+    descriptors are computed (splits stay automatic); leave the best in place
+    and return it."""
+    results = []
+    for P, tpb, occ in candidates or SINGLE_CANDIDATES:
+        _apply(ctx, P, tpb, occ)
+        results.append((time_forces(ctx, m, reps), P, tpb, occ, scgr.scgr_get_plan(ctx)))
+    results.sort(key=lambda r: r[0])
+    best_ms, P, tpb, occ, plan = results[0]
+    _apply(ctx, P, tpb, occ)
+    best = {"P": P, "tpb": tpb, "occ": occ, "ms": best_ms, "plan": plan,
+            "tried": [{"P": r[1], "tpb": r[2], "occ": r[3], "ms": r[0]} for r in results],
             "when": time.strftime("%Y-%m-%d %H:%M:%S")}
     if store:
         _store(single_key(gpu_name(), n, m, p), best)
@@ -130,9 +134,7 @@ def tune_batch(ctx, ref_off, ref_xyz, tmp_off, tmp_xyz, p: float, iterations: in
 def apply_cached_single(ctx, n: int, m: int, p: float) -> dict | None:
     hit = _load().get(single_key(gpu_name(), n, m, p))
     if hit:
-        scgr.scgr_set_tuning(ctx, scgr.SCGR_TUNE_FORCE_P, hit["P"])
-        scgr.scgr_set_tuning(ctx, scgr.SCGR_TUNE_FORCE_TPB, hit["tpb"])
-        scgr.scgr_set_tuning(ctx, scgr.SCGR_TUNE_FORCE_SPLITS, hit["splits"])
+        _apply(ctx, hit["P"], hit["tpb"], hit.get("occ", 0))
     return hit
 
 

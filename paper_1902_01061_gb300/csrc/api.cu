@@ -65,7 +65,7 @@ struct scgr_ctx {
   int64_t knn_grid_min = 65536; // clouds with at least this many points use the grid kNN (tunable)
   ForceTuning ftune;            // force-plan overrides (tunable)
   int reuse_pose_free = 1;      // p = 1: one force pass per scgr_run (tunable)
-  DevBuf gcell, gcount, gstart, gcursor, gblock, gsorted, gsidx, gbb;
+  DevBuf gcell, gcount, gstart, gcursor, gblock, gsorted, gsidx, gbb, cd_key, cd_moved;
   cudaGraph_t bgraph = nullptr;
   cudaGraphExec_t bgexec = nullptr;
 
@@ -127,6 +127,8 @@ scgr_status check_params(const scgr_params* p, std::string& why) {
   if (!(p->eta0 > 0.0) || !std::isfinite(p->eta0)) { why = "eta0 must be > 0"; return SCGR_ERR_INVALID_ARG; }
   if (!std::isfinite(p->time)) { why = "time must be finite"; return SCGR_ERR_INVALID_ARG; }
   if (p->scale_mode < 0 || p->scale_mode > 2) { why = "scale_mode must be 0, 1 or 2"; return SCGR_ERR_INVALID_ARG; }
+  if (p->neigh_mode != 0 && p->neigh_mode != 1) { why = "neigh_mode must be 0 or 1"; return SCGR_ERR_INVALID_ARG; }
+  if (p->neigh_mode == 1 && !(p->radius_scale > 0.0 && std::isfinite(p->radius_scale))) { why = "radius_scale must be > 0"; return SCGR_ERR_INVALID_ARG; }
   return SCGR_OK;
 }
 
@@ -241,6 +243,39 @@ scgr_status knn_cloud(scgr_ctx* c, const float4* P, int n, int32_t* out) {
 
 void drop_graph(scgr_ctx* c);
 
+// Curvature of both clouds for the current neighbourhood mode (k nearest or
+// radius), then sigma (scaled by sigma_scale).
+scgr_status curvatures(scgr_ctx* c, int k, double radius_scale, double sigma_scale) {
+  const int n = (int)c->n, m = (int)c->m;
+  Launch L = c->L();
+  const float4* X4 = (const float4*)c->X4.p;
+  const float4* Y4 = (const float4*)c->Y4.p;
+  DevStats* st = c->stats;
+  if (c->prm.neigh_mode == 0) {
+    SCGR_CK(c, ensure(c->knnX, (size_t)n * k * sizeof(int32_t)));
+    SCGR_CK(c, ensure(c->knnY, (size_t)m * k * sizeof(int32_t)));
+    const int k_prev = c->prm.k;
+    c->prm.k = k;
+    scgr_status ks = knn_cloud(c, X4, n, (int32_t*)c->knnX.p);
+    if (ks == SCGR_OK) ks = knn_cloud(c, Y4, m, (int32_t*)c->knnY.p);
+    if (ks != SCGR_OK) {
+      c->prm.k = k_prev;
+      return ks;
+    }
+    SCGR_CK(c, launch_curvature(L, X4, (const int32_t*)c->knnX.p, n, k, (double*)c->aX64.p, (float*)c->aX32.p));
+    SCGR_CK(c, launch_curvature(L, Y4, (const int32_t*)c->knnY.p, m, k, (double*)c->aY64.p, (float*)c->aY32.p));
+  } else {
+    c->prm.radius_scale = radius_scale;
+    const double s2 = radius_scale * radius_scale;
+    SCGR_CK(c, launch_radius_curvature(L, X4, n, &st->eX, s2, (double*)c->aX64.p, (float*)c->aX32.p, nullptr));
+    SCGR_CK(c, launch_radius_curvature(L, Y4, m, &st->eY0, s2, (double*)c->aY64.p, (float*)c->aY32.p, nullptr));
+  }
+  const double user = c->prm.sigma > 0.0 ? c->prm.sigma * sigma_scale : 0.0;
+  SCGR_CK(c, launch_sigma(L, (const double*)c->aX64.p, n, user, c->red, &st->sigma, &st->asum[0]));
+  if (user <= 0.0 && sigma_scale != 1.0) SCGR_CK(c, launch_scale_double(L, &st->sigma, sigma_scale));
+  return SCGR_OK;
+}
+
 // Recompute the force plan (after a tuning change) and the buffers and
 // template records that depend on it; descriptors and pose are kept.
 scgr_status replan(scgr_ctx* c) {
@@ -305,6 +340,8 @@ scgr_status scgr_default_params(scgr_params* out) {
   out->time = 1.0;
   out->scale_mode = 0;
   out->use_graph = 0;
+  out->neigh_mode = 0;
+  out->radius_scale = 1.0;
   return SCGR_OK;
 }
 
@@ -360,7 +397,8 @@ void scgr_destroy(scgr_ctx* c) {
                     &c->bX4, &c->bY4, &c->bknnX, &c->bknnY, &c->baX64, &c->baY64, &c->baX32, &c->baY32,
                     &c->bXr, &c->bXA, &c->bY0r, &c->bpartial, &c->bblockpart, &c->bpairs, &c->bitems,
                     &c->bcpair, &c->btabX, &c->btabY, &c->bxoff, &c->byoff, &c->bstats, &c->bposes,
-                    &c->gcell, &c->gcount, &c->gstart, &c->gcursor, &c->gblock, &c->gsorted, &c->gsidx, &c->gbb};
+                    &c->gcell, &c->gcount, &c->gstart, &c->gcursor, &c->gblock, &c->gsorted, &c->gsidx, &c->gbb,
+                    &c->cd_key, &c->cd_moved};
   for (DevBuf* b : bufs) release(*b);
   if (c->pose) cudaFree(c->pose);
   if (c->pose_eval) cudaFree(c->pose_eval);
@@ -405,16 +443,11 @@ scgr_status scgr_compute_descriptors(scgr_ctx* c) {
   Launch L = c->L();
   const float4* X4 = (const float4*)c->X4.p;
   const float4* Y4 = (const float4*)c->Y4.p;
-  scgr_status ks = knn_cloud(c, X4, n, (int32_t*)c->knnX.p);
-  if (ks != SCGR_OK) return ks;
-  ks = knn_cloud(c, Y4, m, (int32_t*)c->knnY.p);
-  if (ks != SCGR_OK) return ks;
-  SCGR_CK(c, launch_curvature(L, X4, (const int32_t*)c->knnX.p, n, k, (double*)c->aX64.p, (float*)c->aX32.p));
-  SCGR_CK(c, launch_curvature(L, Y4, (const int32_t*)c->knnY.p, m, k, (double*)c->aY64.p, (float*)c->aY32.p));
   DevStats* st = c->stats;
   SCGR_CK(c, launch_cloud_stats(L, X4, n, c->red, st->xbar, st->CX, &st->eX));
   SCGR_CK(c, launch_cloud_stats(L, Y4, m, c->red, st->ybar0, st->S0, &st->eY0));
-  SCGR_CK(c, launch_sigma(L, (const double*)c->aX64.p, n, c->prm.sigma, c->red, &st->sigma, &st->asum[0]));
+  scgr_status cs = curvatures(c, c->prm.k, c->prm.radius_scale, 1.0);
+  if (cs != SCGR_OK) return cs;
   c->npad = (c->n + 255) / 256 * 256;
   const int64_t mloc = c->rows >= 0 ? c->rows : c->m;
   c->fp = plan_force(mloc, c->npad, c->prm.p, c->num_sms, c->ftune);
@@ -535,6 +568,7 @@ scgr_status scgr_get_descriptors(scgr_ctx* c, int which, int32_t* knn_dev, float
   if (which != 0 && which != 1) return fail(c, SCGR_ERR_INVALID_ARG, "which must be 0 (reference) or 1 (template)");
   if (!c->have_desc) return fail(c, SCGR_ERR_STATE, "compute descriptors first");
   const int64_t n = which == 0 ? c->n : c->m;
+  if (knn_dev && c->prm.neigh_mode != 0) return fail(c, SCGR_ERR_STATE, "no neighbour lists in the radius mode");
   if (knn_dev)
     SCGR_CK(c, cudaMemcpyAsync(knn_dev, which == 0 ? c->knnX.p : c->knnY.p, (size_t)n * c->prm.k * sizeof(int32_t),
                                cudaMemcpyDeviceToDevice, c->stream));
@@ -574,6 +608,61 @@ scgr_status scgr_forces(scgr_ctx* c, float* f4_dev) {
   SCGR_CK(c, launch_combine(c->L(), (const float4*)c->partial.p, c->fp.splits, (int)c->mpad, mloc,
                             (const float4*)c->Y0r.p, (const double*)c->aY64.p + c->row0, c->prm.g_mode, c->pose,
                             (float4*)f4_dev, (double*)c->blockpart.p));
+  return SCGR_OK;
+}
+
+scgr_status scgr_force_vjp(scgr_ctx* c, const float* v_dev, float* grad_dev) {
+  if (!c || !v_dev || !grad_dev) return fail(c, SCGR_ERR_INVALID_ARG, "NULL argument");
+  c->err.clear();
+  if (!c->have_desc) return fail(c, SCGR_ERR_STATE, "compute descriptors first");
+  if (c->rows >= 0) return fail(c, SCGR_ERR_STATE, "the VJP needs the whole template (a row range is set)");
+  SCGR_CK(c, launch_force_vjp(c->L(), (const float4*)c->Xr.p, (const float2*)c->XA.p, (int)(c->npad / FORCE_TJ),
+                              (const float4*)c->Y0r.p, (const double*)c->aY64.p, c->prm.g_mode, (int)c->m, c->pose,
+                              c->prm.p, v_dev, grad_dev));
+  return SCGR_OK;
+}
+
+scgr_status scgr_nearest(scgr_ctx* c, const float* q_dev, int64_t nq, int32_t* idx_dev, float* key_dev) {
+  if (!c || !q_dev || (!idx_dev && !key_dev)) return fail(c, SCGR_ERR_INVALID_ARG, "NULL argument");
+  c->err.clear();
+  if (!c->have_X) return fail(c, SCGR_ERR_STATE, "set the reference first");
+  if (nq < 0 || nq > (int64_t(1) << 30)) return fail(c, SCGR_ERR_INVALID_ARG, "bad query count");
+  SCGR_CK(c, launch_nearest(c->L(), (const float4*)c->X4.p, (int)c->n, q_dev, (int)nq, idx_dev, key_dev));
+  return SCGR_OK;
+}
+
+scgr_status scgr_change_mask(scgr_ctx* c, double threshold, uint8_t* mask_dev, float* dist_dev) {
+  if (!c || !mask_dev) return fail(c, SCGR_ERR_INVALID_ARG, "NULL argument");
+  c->err.clear();
+  if (!c->have_desc) return fail(c, SCGR_ERR_STATE, "compute descriptors first");
+  if (!(threshold >= 0.0) || !std::isfinite(threshold)) return fail(c, SCGR_ERR_INVALID_ARG, "threshold must be >= 0");
+  const int m = (int)c->m;
+  SCGR_CK(c, ensure(c->cd_moved, (size_t)m * 3 * sizeof(float)));
+  SCGR_CK(c, ensure(c->cd_key, (size_t)m * sizeof(float)));
+  SCGR_CK(c, launch_apply(c->L(), (const float4*)c->Y4.p, m, c->pose, (float*)c->cd_moved.p));
+  SCGR_CK(c, launch_nearest(c->L(), (const float4*)c->X4.p, (int)c->n, (const float*)c->cd_moved.p, m, nullptr,
+                            (float*)c->cd_key.p));
+  SCGR_CK(c, launch_threshold(c->L(), (const float*)c->cd_key.p, m, (float)(threshold * threshold), mask_dev,
+                              dist_dev));
+  return SCGR_OK;
+}
+
+scgr_status scgr_set_neighbourhood(scgr_ctx* c, int k, double radius_scale, double sigma_scale) {
+  if (!c) return SCGR_ERR_INVALID_ARG;
+  c->err.clear();
+  if (!c->have_desc) return fail(c, SCGR_ERR_STATE, "compute descriptors first");
+  if (c->prm.neigh_mode == 0 && (k < 3 || k > 32 || k > c->n || k > c->m))
+    return fail(c, SCGR_ERR_INVALID_ARG, "k must be in [3, 32] and at most the cloud sizes");
+  if (!(radius_scale > 0.0) || !(sigma_scale > 0.0) || !std::isfinite(radius_scale) || !std::isfinite(sigma_scale))
+    return fail(c, SCGR_ERR_INVALID_ARG, "scales must be finite and > 0");
+  drop_graph(c);
+  scgr_status cs = curvatures(c, c->prm.neigh_mode == 0 ? k : c->prm.k, radius_scale, sigma_scale);
+  if (cs != SCGR_OK) return cs;
+  const int64_t mloc = c->rows >= 0 ? c->rows : c->m;
+  SCGR_CK(c, launch_records(c->L(), (const float4*)c->X4.p, (const double*)c->aX64.p, (int)c->n, (int)c->npad,
+                            (const float4*)c->Y4.p + c->row0, (const double*)c->aY64.p + c->row0, (int)mloc,
+                            (int)c->mpad, c->prm.g_mode, c->stats, (float4*)c->Xr.p, (float2*)c->XA.p,
+                            (float4*)c->Y0r.p));
   return SCGR_OK;
 }
 
@@ -755,7 +844,7 @@ scgr_status scgr_step_apply(scgr_ctx* c, const double tot13[13]) {
   return read_error_word(c);
 }
 
-scgr_status scgr_get_plan(scgr_ctx* c, int out[4]) {
+scgr_status scgr_get_plan(scgr_ctx* c, int out[5]) {
   if (!c || !out) return fail(c, SCGR_ERR_INVALID_ARG, "NULL argument");
   c->err.clear();
   if (!c->have_desc) return fail(c, SCGR_ERR_STATE, "compute descriptors first");
@@ -763,6 +852,7 @@ scgr_status scgr_get_plan(scgr_ctx* c, int out[4]) {
   out[1] = c->fp.tpb;
   out[2] = c->fp.splits;
   out[3] = c->fp.iblocks;
+  out[4] = c->fp.occ;
   return SCGR_OK;
 }
 
@@ -777,6 +867,11 @@ scgr_status scgr_set_tuning(scgr_ctx* c, int key, int value) {
   if (key == SCGR_TUNE_FORCE_TPB) {
     if (value != 0 && value != 128 && value != 256) return fail(c, SCGR_ERR_INVALID_ARG, "threads per block must be 0, 128 or 256");
     c->ftune.tpb = value;
+    return c->have_desc ? replan(c) : SCGR_OK;
+  }
+  if (key == SCGR_TUNE_FORCE_OCC) {
+    if (value != 0 && value != 1) return fail(c, SCGR_ERR_INVALID_ARG, "occupancy variant must be 0 or 1");
+    c->ftune.occ = value;
     return c->have_desc ? replan(c) : SCGR_OK;
   }
   if (key == SCGR_TUNE_FORCE_SPLITS) {

@@ -172,6 +172,12 @@ cudaError_t launch_bbox(Launch L, const float4* P, int n, float* part, float* ou
 cudaError_t launch_knn_grid(Launch L, const float4* P, int n, int k, const GridSpec& gs, int* cell_of, int* count,
                             int* start, int* cursor, int* block_tot, float4* sorted, int* sorted_idx,
                             int32_t* out);
+cudaError_t launch_nearest(Launch L, const float4* P, int n, const float* q3, int nq, int32_t* idx_out,
+                           float* key_out);
+cudaError_t launch_threshold(Launch L, const float* key, int nq, float thr2, uint8_t* mask, float* dist);
+cudaError_t launch_scale_double(Launch L, double* v, double f);
+cudaError_t launch_radius_curvature(Launch L, const float4* P, int n, const double* e_dev, double scale2,
+                                    double* a64, float* a32, int* count_out);
 cudaError_t launch_check_curvature(Launch L, const double* a64, int n, float* a32, int* err);
 cudaError_t launch_records(Launch L, const float4* X4, const double* aX64, int n, int npad,
                            const float4* Y4, const double* aY64, int m, int mpad, int g_mode,
@@ -189,6 +195,7 @@ struct ForcePlan {
   int splits;     // reference-range splits (grid.y)
   int tiles_per_split;
   int iblocks;    // grid.x
+  int occ;        // 0: >= 2 resident blocks per SM; 1: more (3 for 256 threads and P <= 2, 4 for 128 threads)
 };
 
 // Overrides of the force plan (0: automatic), set by the autotuner.
@@ -196,6 +203,7 @@ struct ForceTuning {
   int P = 0;       // template points per thread: 1, 2 or 4
   int tpb = 0;     // threads per block: 128 or 256
   int splits = 0;  // reference splits
+  int occ = 0;     // 1: the higher-occupancy variant (tighter register budget)
 };
 
 ForcePlan plan_force(int64_t m, int64_t npad, double p, int num_sms, const ForceTuning& tune = ForceTuning());
@@ -223,6 +231,9 @@ cudaError_t launch_combine_batch(Launch L, int nblocks, const int* cpair, const 
 cudaError_t launch_finalize_multi(Launch L, const double* blockpart, const BatchPair* pairs, int npairs,
                                   DevPose* poses, const DevStats* stats, StepParams sp, int* err);
 cudaError_t launch_pose_init_multi(Launch L, DevPose* poses, const DevStats* stats, int npairs, int E);
+cudaError_t launch_force_vjp(Launch L, const float4* Xr, const float2* XA, int ntiles, const float4* Y0r,
+                             const double* aY64, int g_mode, int m, const DevPose* ps, double p, const float* v,
+                             float* grad);
 cudaError_t launch_pose_from7(Launch L, const double* pose7_dev, DevPose* ps, const DevStats* st);
 cudaError_t launch_adjoint_combine(Launch L, const float4* partial, int S, int mpad, int m, const float4* Y0r,
                                    const double* aY64, int g_mode, const DevPose* ps, float* grad_xyz,

@@ -127,6 +127,46 @@ __global__ void __launch_bounds__(KNN_TPB) knn_brute_multi_kernel(const float4* 
   }
 }
 
+// Nearest reference point of arbitrary query points (change detection):
+// the same exact key and (key, index) order as the kNN, k = 1.
+__global__ void __launch_bounds__(KNN_TPB) nearest_kernel(const float4* __restrict__ P, int n,
+                                                          const float* __restrict__ q3, int nq,
+                                                          int32_t* __restrict__ idx_out, float* __restrict__ key_out) {
+  __shared__ float4 tile[KNN_TILE];
+  const int qi = blockIdx.x * KNN_TPB + threadIdx.x;
+  const int qc = qi < nq ? qi : nq - 1;
+  const float4 q = make_float4(q3[3 * (size_t)qc], q3[3 * (size_t)qc + 1], q3[3 * (size_t)qc + 2], 0.f);
+  float kd[1];
+  int ki[1];
+  knn_scan<1>(P, 0, n, q, kd, ki, tile);
+  if (qi < nq) {
+    if (idx_out) idx_out[qi] = ki[0];
+    if (key_out) key_out[qi] = kd[0];
+  }
+}
+
+cudaError_t launch_nearest(Launch L, const float4* P, int n, const float* q3, int nq, int32_t* idx_out,
+                           float* key_out) {
+  if (nq <= 0) return cudaSuccess;
+  nearest_kernel<<<(nq + KNN_TPB - 1) / KNN_TPB, KNN_TPB, 0, L.stream>>>(P, n, q3, nq, idx_out, key_out);
+  return after_launch(L);
+}
+
+__global__ void threshold_kernel(const float* __restrict__ key, int nq, float thr2, uint8_t* __restrict__ mask,
+                                 float* __restrict__ dist) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nq) return;
+  const float k = key[i];
+  mask[i] = k > thr2 ? 1 : 0;
+  if (dist) dist[i] = sqrtf(k);
+}
+
+cudaError_t launch_threshold(Launch L, const float* key, int nq, float thr2, uint8_t* mask, float* dist) {
+  if (nq <= 0) return cudaSuccess;
+  threshold_kernel<<<(nq + 255) / 256, 256, 0, L.stream>>>(key, nq, thr2, mask, dist);
+  return after_launch(L);
+}
+
 cudaError_t launch_knn_multi(Launch L, const float4* P, const int64_t* off_dev, const int2* table_dev,
                              int nblocks, int k, int32_t* out) {
   if (nblocks <= 0) return cudaSuccess;
@@ -183,6 +223,93 @@ cudaError_t launch_curvature(Launch L, const float4* P, const int32_t* nbr, int 
                              double* a64, float* a32) {
   const int tpb = 128;
   curvature_kernel<<<(n + tpb - 1) / tpb, tpb, 0, L.stream>>>(P, nbr, n, k, a64, a32);
+  return after_launch(L);
+}
+
+// ---- radius neighbourhood curvature (Sec. IV) ----------------------------
+// The neighbourhood of p is every point q of the cloud (p included) whose
+// float32 key (dx*dx + dy*dy) + dz*dz, each operation rounded on its own,
+// is <= float32(scale^2 * e), e the largest eigenvalue of the cloud's 1/n
+// covariance (radius sqrt(e), Sec. IV).  Its 1/|N| covariance gives
+// a = lambda_min / trace.  Two passes over the cloud: the first finds the
+// neighbourhood's mean c (offsets summed in float32 per tile, float64
+// across tiles); the second accumulates the centred moments
+// sum (q - p - c) and sum (q - p - c)(q - p - c)^T in float64, so that a
+// near-planar neighbourhood keeps its small eigenvalue.
+constexpr int RAD_TPB = 128;
+constexpr int RAD_TILE = 512;
+
+__device__ __forceinline__ bool radius_member(float4 q, float4 c, float r2, float& dx, float& dy, float& dz) {
+  dx = __fsub_rn(c.x, q.x);
+  dy = __fsub_rn(c.y, q.y);
+  dz = __fsub_rn(c.z, q.z);
+  const float key = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+  return key <= r2;
+}
+
+__global__ void __launch_bounds__(RAD_TPB)
+    radius_curvature_kernel(const float4* __restrict__ P, int n, const double* __restrict__ e_dev, double scale2,
+                            double* __restrict__ a64, float* __restrict__ a32, int* __restrict__ count_out) {
+  __shared__ float4 tile[RAD_TILE];
+  const int i = blockIdx.x * RAD_TPB + threadIdx.x;
+  const float4 q = P[i < n ? i : n - 1];
+  const float r2 = (float)(scale2 * e_dev[0]);
+  // pass 1: count and mean offset
+  double M[3] = {0, 0, 0};
+  int cnt = 0;
+  for (int base = 0; base < n; base += RAD_TILE) {
+    const int m = min(RAD_TILE, n - base);
+    __syncthreads();
+    for (int t = threadIdx.x; t < m; t += RAD_TPB) tile[t] = P[base + t];
+    __syncthreads();
+    float s[3] = {0, 0, 0};
+    for (int jj = 0; jj < m; ++jj) {
+      float dx, dy, dz;
+      if (radius_member(q, tile[jj], r2, dx, dy, dz)) {
+        ++cnt;
+        s[0] += dx; s[1] += dy; s[2] += dz;
+      }
+    }
+    M[0] += s[0]; M[1] += s[1]; M[2] += s[2];
+  }
+  const double k = (double)cnt;
+  const double c[3] = {M[0] / k, M[1] / k, M[2] / k};
+  // pass 2: centred first and second moments in float64
+  double S[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+  for (int base = 0; base < n; base += RAD_TILE) {
+    const int m = min(RAD_TILE, n - base);
+    __syncthreads();
+    for (int t = threadIdx.x; t < m; t += RAD_TPB) tile[t] = P[base + t];
+    __syncthreads();
+    for (int jj = 0; jj < m; ++jj) {
+      float dx, dy, dz;
+      if (radius_member(q, tile[jj], r2, dx, dy, dz)) {
+        const double ex = (double)dx - c[0], ey = (double)dy - c[1], ez = (double)dz - c[2];
+        S[0] += ex; S[1] += ey; S[2] += ez;
+        S[3] += ex * ex; S[4] += ex * ey; S[5] += ex * ez;
+        S[6] += ey * ey; S[7] += ey * ez; S[8] += ez * ez;
+      }
+    }
+  }
+  if (i >= n) return;
+  const double mx = S[0] / k, my = S[1] / k, mz = S[2] / k;
+  double C[9];
+  C[0] = S[3] / k - mx * mx; C[1] = S[4] / k - mx * my; C[2] = S[5] / k - mx * mz;
+  C[4] = S[6] / k - my * my; C[5] = S[7] / k - my * mz; C[8] = S[8] / k - mz * mz;
+  C[3] = C[1]; C[6] = C[2]; C[7] = C[5];
+  double lam[3];
+  sym3_eigenvalues(C, lam);
+  const double tr = C[0] + C[4] + C[8];
+  const double a = tr > 0.0 ? fmax(lam[0], 0.0) / tr : 0.0;
+  a64[i] = a;
+  a32[i] = (float)a;
+  if (count_out) count_out[i] = cnt;
+}
+
+cudaError_t launch_radius_curvature(Launch L, const float4* P, int n, const double* e_dev, double scale2,
+                                    double* a64, float* a32, int* count_out) {
+  radius_curvature_kernel<<<(n + RAD_TPB - 1) / RAD_TPB, RAD_TPB, 0, L.stream>>>(P, n, e_dev, scale2, a64, a32,
+                                                                                 count_out);
   return after_launch(L);
 }
 
@@ -310,6 +437,15 @@ cudaError_t launch_sigma(Launch L, const double* a64, int n, double sigma_user, 
   sigma_finish_kernel<<<1, 32, 0, L.stream>>>(sums, n, sigma_user, sigma_out, asum_out);
   if (L.counter) *L.counter += 5;
   return cudaGetLastError();
+}
+
+__global__ void scale_double_kernel(double* v, double f) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) *v *= f;
+}
+
+cudaError_t launch_scale_double(Launch L, double* v, double f) {
+  scale_double_kernel<<<1, 32, 0, L.stream>>>(v, f);
+  return after_launch(L);
 }
 
 // ---- caller-supplied curvature --------------------------------------------

@@ -268,6 +268,7 @@ ForcePlan plan_force(int64_t m, int64_t npad, double p, int num_sms, const Force
   if (m < 4096) fp.tpb = 128;
   if (tune.P == 1 || tune.P == 2 || tune.P == 4) fp.P = tune.P;
   if (tune.tpb == 128 || tune.tpb == 256) fp.tpb = tune.tpb;
+  fp.occ = (tune.occ == 1 && !(fp.tpb == 256 && fp.P == 4)) ? 1 : 0;
   const int64_t per_block = (int64_t)fp.tpb * fp.P;
   fp.iblocks = (int)((m + per_block - 1) / per_block);
   const int ntiles = (int)(npad / FORCE_TJ);
@@ -306,49 +307,74 @@ int64_t force_mpad(int64_t m, const ForcePlan& fp) {
   return (mp + 255) / 256 * 256;
 }
 
-template <int P, int PM, int TPB>
+template <int P, int PM, int TPB, int MINB>
 static void launch_force_t(cudaStream_t st, const ForcePlan& fp, const float4* Xr,
                            const float2* XA, int ntiles, const float4* Y0r, int mpad,
                            const DevPose* pose, float qexp, float4* partial) {
   dim3 grid(fp.iblocks, fp.splits);
-  force_tile_kernel<P, PM, TPB, FORCE_TJ, 2, false><<<grid, TPB, 0, st>>>(
+  force_tile_kernel<P, PM, TPB, FORCE_TJ, MINB, false><<<grid, TPB, 0, st>>>(
       reinterpret_cast<const float*>(Xr), reinterpret_cast<const float*>(XA), ntiles,
       fp.tiles_per_split, Y0r, mpad, pose, qexp, partial, nullptr, nullptr);
 }
+
+// Dispatch on (points per thread, threads, occupancy variant): calls
+// f.template operator()<P, TPB, MINB>() for the kernel instance of the plan.
+template <class F>
+static int with_shape(const ForcePlan& fp, const F& f) {
+  const bool hi = fp.occ == 1;
+  if (fp.tpb == 256) {
+    if (fp.P == 4) return f.template operator()<4, 256, 2>();
+    if (fp.P == 2) return hi ? f.template operator()<2, 256, 3>() : f.template operator()<2, 256, 2>();
+    return hi ? f.template operator()<1, 256, 4>() : f.template operator()<1, 256, 2>();
+  }
+  if (fp.P == 4) return hi ? f.template operator()<4, 128, 4>() : f.template operator()<4, 128, 2>();
+  if (fp.P == 2) return hi ? f.template operator()<2, 128, 4>() : f.template operator()<2, 128, 2>();
+  return hi ? f.template operator()<1, 128, 4>() : f.template operator()<1, 128, 2>();
+}
+
+template <int PM>
+struct LaunchShape {
+  cudaStream_t st;
+  const ForcePlan& fp;
+  const float4* Xr;
+  const float2* XA;
+  int ntiles;
+  const float4* Y0r;
+  int mpad;
+  const DevPose* pose;
+  float qexp;
+  float4* partial;
+  template <int P, int TPB, int MINB>
+  int operator()() const {
+    launch_force_t<P, PM, TPB, MINB>(st, fp, Xr, XA, ntiles, Y0r, mpad, pose, qexp, partial);
+    return 0;
+  }
+};
 
 template <int PM>
 static void launch_force_pm(cudaStream_t st, const ForcePlan& fp, const float4* Xr,
                             const float2* XA, int ntiles, const float4* Y0r, int mpad,
                             const DevPose* pose, float qexp, float4* partial) {
-  if (fp.tpb == 256) {
-    if (fp.P == 4) launch_force_t<4, PM, 256>(st, fp, Xr, XA, ntiles, Y0r, mpad, pose, qexp, partial);
-    else if (fp.P == 2) launch_force_t<2, PM, 256>(st, fp, Xr, XA, ntiles, Y0r, mpad, pose, qexp, partial);
-    else launch_force_t<1, PM, 256>(st, fp, Xr, XA, ntiles, Y0r, mpad, pose, qexp, partial);
-  } else {
-    if (fp.P == 4) launch_force_t<4, PM, 128>(st, fp, Xr, XA, ntiles, Y0r, mpad, pose, qexp, partial);
-    else if (fp.P == 2) launch_force_t<2, PM, 128>(st, fp, Xr, XA, ntiles, Y0r, mpad, pose, qexp, partial);
-    else launch_force_t<1, PM, 128>(st, fp, Xr, XA, ntiles, Y0r, mpad, pose, qexp, partial);
-  }
+  with_shape(fp, LaunchShape<PM>{st, fp, Xr, XA, ntiles, Y0r, mpad, pose, qexp, partial});
 }
 
 template <int PM>
+struct OccShape {
+  template <int P, int TPB, int MINB>
+  int operator()() const {
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, force_tile_kernel<P, PM, TPB, FORCE_TJ, MINB, false>, TPB,
+                                                      0) != cudaSuccess) {
+      cudaGetLastError();
+      return 2;
+    }
+    return nb > 0 ? nb : 1;
+  }
+};
+
+template <int PM>
 static int blocks_per_sm_pm(const ForcePlan& fp) {
-  int nb = 0;
-  cudaError_t e;
-  if (fp.tpb == 256) {
-    if (fp.P == 4) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, force_tile_kernel<4, PM, 256, FORCE_TJ, 2, false>, 256, 0);
-    else if (fp.P == 2) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, force_tile_kernel<2, PM, 256, FORCE_TJ, 2, false>, 256, 0);
-    else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, force_tile_kernel<1, PM, 256, FORCE_TJ, 2, false>, 256, 0);
-  } else {
-    if (fp.P == 4) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, force_tile_kernel<4, PM, 128, FORCE_TJ, 2, false>, 128, 0);
-    else if (fp.P == 2) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, force_tile_kernel<2, PM, 128, FORCE_TJ, 2, false>, 128, 0);
-    else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, force_tile_kernel<1, PM, 128, FORCE_TJ, 2, false>, 128, 0);
-  }
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    return 2;
-  }
-  return nb > 0 ? nb : 1;
+  return with_shape(fp, OccShape<PM>{});
 }
 
 static int force_blocks_per_sm(const ForcePlan& fp) {

@@ -186,6 +186,74 @@ __global__ void adjoint_finish_kernel(const double* __restrict__ tot, const doub
   grad7[6] = tot[3];
 }
 
+// ---- vector-Jacobian product of the force field ---------------------------
+// f_i depends on Y_i only (X fixed, descriptors fixed), so dF/dY is block
+// diagonal with J_ii = -aY sum_j w_ij [I + (p - 1) r r^T / d^2], r = Y_i - X_j,
+// w_ij = g d^(p-1).  grad_i = J_ii v_i (J_ii is symmetric).  One thread per
+// template point; reference tiles of the force records are recomputed.
+constexpr int VJP_TPB = 128;
+constexpr int VJP_TILE = FORCE_TJ;
+
+__global__ void __launch_bounds__(VJP_TPB)
+    force_vjp_kernel(const float* __restrict__ Xr, const float* __restrict__ XA, int ntiles,
+                     const float4* __restrict__ Y0r, const double* __restrict__ aY64, int g_mode, int m,
+                     const DevPose* __restrict__ ps, double pm1, const float* __restrict__ v,
+                     float* __restrict__ grad) {
+  __shared__ float sT[6][VJP_TILE];
+  const int i = blockIdx.x * VJP_TPB + threadIdx.x;
+  float A[9], b[3];
+#pragma unroll
+  for (int q = 0; q < 9; ++q) A[q] = ps->A[q];
+#pragma unroll
+  for (int q = 0; q < 3; ++q) b[q] = ps->b[q];
+  const float4 y0 = Y0r[i < m ? i : m - 1];
+  float yx, yy, yz;
+  tpoint(y0, A, b, yx, yy, yz);
+  const float ah = y0.w;
+  const float q = (float)(0.5 * pm1);           // d^(p-1) = (d^2)^q
+  double Ws = 0.0, B[6] = {0, 0, 0, 0, 0, 0};   // sum w, sum w (p-1) r r^T / d^2
+  for (int t = 0; t < ntiles; ++t) {
+    __syncthreads();
+    for (int u = threadIdx.x; u < 4 * VJP_TILE; u += VJP_TPB) (&sT[0][0])[u] = Xr[(size_t)t * 4 * VJP_TILE + u];
+    for (int u = threadIdx.x; u < 2 * VJP_TILE; u += VJP_TPB) (&sT[4][0])[u] = XA[(size_t)t * 2 * VJP_TILE + u];
+    __syncthreads();
+    float ws = 0.f, bb[6] = {0, 0, 0, 0, 0, 0};
+    for (int j = 0; j < VJP_TILE; ++j) {
+      const float rx = yx - sT[0][j], ry = yy - sT[1][j], rz = yz - sT[2][j];
+      const float d2 = fmaf(rz, rz, fmaf(ry, ry, rx * rx));
+      const float uu = sT[4][j] - ah;
+      const float ep = fmaf(uu, uu, sT[5][j]);  // the weight is 2^-ep d^(p-1)
+      const float w = d2 > 0.f ? exp2f(fmaf(q, log2f(d2), -ep)) : (q == 0.f ? exp2f(-ep) : 0.f);
+      const float c = d2 > 0.f ? (float)pm1 * w / d2 : 0.f;
+      ws += w;
+      bb[0] = fmaf(c * rx, rx, bb[0]); bb[1] = fmaf(c * rx, ry, bb[1]); bb[2] = fmaf(c * rx, rz, bb[2]);
+      bb[3] = fmaf(c * ry, ry, bb[3]); bb[4] = fmaf(c * ry, rz, bb[4]); bb[5] = fmaf(c * rz, rz, bb[5]);
+    }
+    Ws += ws;
+    for (int u = 0; u < 6; ++u) B[u] += bb[u];
+  }
+  if (i >= m) return;
+  const double ay = g_mode == 1 ? aY64[i] : 1.0;
+  const double vx = v[3 * (size_t)i], vy = v[3 * (size_t)i + 1], vz = v[3 * (size_t)i + 2];
+  const double gx = -ay * (Ws * vx + B[0] * vx + B[1] * vy + B[2] * vz);
+  const double gy = -ay * (Ws * vy + B[1] * vx + B[3] * vy + B[4] * vz);
+  const double gz = -ay * (Ws * vz + B[2] * vx + B[4] * vy + B[5] * vz);
+  grad[3 * (size_t)i] = (float)gx;
+  grad[3 * (size_t)i + 1] = (float)gy;
+  grad[3 * (size_t)i + 2] = (float)gz;
+}
+
+cudaError_t launch_force_vjp(Launch L, const float4* Xr, const float2* XA, int ntiles, const float4* Y0r,
+                             const double* aY64, int g_mode, int m, const DevPose* ps, double p, const float* v,
+                             float* grad) {
+  if (m <= 0) return cudaSuccess;
+  force_vjp_kernel<<<(m + VJP_TPB - 1) / VJP_TPB, VJP_TPB, 0, L.stream>>>(
+      reinterpret_cast<const float*>(Xr), reinterpret_cast<const float*>(XA), ntiles, Y0r, aY64, g_mode, m, ps,
+      p - 1.0, v, grad);
+  if (L.counter) ++*L.counter;
+  return cudaGetLastError();
+}
+
 cudaError_t launch_pose_from7(Launch L, const double* pose7_dev, DevPose* ps, const DevStats* st) {
   pose_from7_kernel<<<1, 32, 0, L.stream>>>(pose7_dev, ps, st);
   if (L.counter) ++*L.counter;

@@ -30,7 +30,8 @@ EXPORTED = (
     "scgr_forces", "scgr_get_state", "scgr_set_state", "scgr_sync", "scgr_launch_count",
     "scgr_set_curvature", "scgr_set_force_timing", "scgr_get_force_timing", "scgr_forces_static",
     "scgr_potential", "scgr_batch_run", "scgr_set_tuning", "scgr_set_row_range", "scgr_step_partials",
-    "scgr_step_apply", "scgr_get_plan", "scgr_microbench",
+    "scgr_step_apply", "scgr_get_plan", "scgr_microbench", "scgr_set_neighbourhood", "scgr_nearest",
+    "scgr_change_mask", "scgr_force_vjp",
 )
 SCGR_TUNE_BATCH_CHUNK_TILES = 1
 SCGR_TUNE_KNN_GRID_MIN = 2
@@ -38,12 +39,14 @@ SCGR_TUNE_FORCE_P = 3
 SCGR_TUNE_FORCE_TPB = 4
 SCGR_TUNE_FORCE_SPLITS = 5
 SCGR_TUNE_REUSE_POSE_FREE = 6
+SCGR_TUNE_FORCE_OCC = 7
 
 
 class scgr_params(Structure):
     _fields_ = [("k", c_int), ("p", c_double), ("sigma", c_double), ("g_mode", c_int),
                 ("G1", c_double), ("E", c_int), ("step_mode", c_int), ("eta0", c_double),
-                ("time", c_double), ("scale_mode", c_int), ("use_graph", c_int)]
+                ("time", c_double), ("scale_mode", c_int), ("use_graph", c_int), ("neigh_mode", c_int),
+                ("radius_scale", c_double)]
 
 
 class scgr_result(Structure):
@@ -107,6 +110,10 @@ def load():
         "scgr_batch_run": (S, [ctx, c_int, c_void_p, c_void_p, c_void_p, c_void_p, c_int, c_void_p]),
         "scgr_set_tuning": (S, [ctx, c_int, c_int]),
         "scgr_get_plan": (S, [ctx, POINTER(c_int)]),
+        "scgr_set_neighbourhood": (S, [ctx, c_int, c_double, c_double]),
+        "scgr_force_vjp": (S, [ctx, c_void_p, c_void_p]),
+        "scgr_nearest": (S, [ctx, c_void_p, c_int64, c_void_p, c_void_p]),
+        "scgr_change_mask": (S, [ctx, c_double, c_void_p, c_void_p]),
         "scgr_microbench": (S, [c_int, c_int, c_void_p, c_void_p, POINTER(c_int64), POINTER(c_double)]),
         "scgr_set_row_range": (S, [ctx, c_int64, c_int64]),
         "scgr_step_partials": (S, [ctx, POINTER(c_double)]),
@@ -337,13 +344,42 @@ def scgr_microbench(kind: int, stream=None):
 
 
 def scgr_get_plan(ctx) -> dict:
-    out = (c_int * 4)()
+    out = (c_int * 5)()
     _check(load().scgr_get_plan(ctx, out), ctx)
-    return {"P": out[0], "tpb": out[1], "splits": out[2], "iblocks": out[3]}
+    return {"P": out[0], "tpb": out[1], "splits": out[2], "iblocks": out[3], "occ": out[4]}
 
 
 def scgr_set_tuning(ctx, key: int, value: int) -> None:
     _check(load().scgr_set_tuning(ctx, int(key), int(value)), ctx)
+
+
+def scgr_force_vjp(ctx, v, grad_out) -> None:
+    _check(load().scgr_force_vjp(ctx, _dev_ptr(v, "float32", (3,)), _dev_ptr(grad_out, "float32", (3,))), ctx)
+
+
+def scgr_nearest(ctx, q, idx_out=None, key_out=None) -> None:
+    _check(load().scgr_nearest(ctx, _dev_ptr(q, "float32", (3,)), q.shape[0],
+                               _dev_ptr(idx_out, "int32") if idx_out is not None else None,
+                               _dev_ptr(key_out, "float32") if key_out is not None else None), ctx)
+
+
+def scgr_change_mask(ctx, threshold: float, mask_out, dist_out=None) -> None:
+    _check(load().scgr_change_mask(ctx, float(threshold), _dev_ptr(mask_out, "uint8"),
+                                   _dev_ptr(dist_out, "float32") if dist_out is not None else None), ctx)
+
+
+def scgr_set_neighbourhood(ctx, k: int = 16, radius_scale: float = 1.0, sigma_scale: float = 1.0) -> None:
+    _check(load().scgr_set_neighbourhood(ctx, int(k), float(radius_scale), float(sigma_scale)), ctx)
+
+
+def run_pyramid(ctx, levels):
+    """Pyramidal schedule: `levels` is a sequence of (iterations, k,
+    radius_scale, sigma_scale); descriptors are recomputed at the start of
+    each level and the registration continues from the current pose."""
+    for iters, k, rscale, sscale in levels:
+        scgr_set_neighbourhood(ctx, k, rscale, sscale)
+        scgr_run(ctx, iters)
+    return scgr_get_result(ctx)
 
 
 def scgr_forces(ctx, f4_out) -> None:

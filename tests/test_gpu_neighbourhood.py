@@ -1,0 +1,97 @@
+"""Neighbourhood variants on the GPU against the oracle: the radius
+neighbourhood of Sec. IV (radius sqrt(e) times a scale) and the pyramidal
+schedule (neighbourhood and sigma shrinking between levels, pose kept)."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1902_01061_gb300 import scgr, synth
+from tests.gpu_helpers import Gpu, rot_err_deg
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib(scgr_lib):
+    return scgr_lib
+
+
+def pose_close(res, o, diag):
+    R, t, s = res.as_numpy()
+    return (rot_err_deg(R, o["R"]) <= 0.5 and np.linalg.norm(t - o["t"]) <= 1e-3 * diag
+            and abs(s - o["s"]) <= 1e-5 * o["s"])
+
+
+@pytest.mark.parametrize("scale", [1.0, 0.35])
+def test_radius_curvature_matches_oracle(scale):
+    case = synth.mild(n=1500)
+    with Gpu(case.X, case.Y0, neigh_mode=1, radius_scale=scale) as g:
+        for which, P in ((0, case.X), (1, case.Y0)):
+            np.testing.assert_allclose(g.curv64(which), O.curvature_radius(P, scale), rtol=1e-5, atol=1e-10)
+        assert g.sigma() == pytest.approx(O.sigma_auto(O.curvature_radius(case.X, scale)), rel=1e-5)
+
+
+def test_radius_mode_registration_matches_oracle():
+    case = synth.mild(n=800)
+    prm = O.Params(neigh_mode=1, radius_scale=0.4)
+    o = O.register(case.X, case.Y0, prm, iterations=20)
+    with Gpu(case.X, case.Y0, neigh_mode=1, radius_scale=0.4) as g:
+        assert pose_close(g.run(20), o, synth.bbox_diag(case.X))
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_pyramid_matches_oracle(mode):
+    case = synth.mild(n=900)
+    if mode == 0:
+        levels = [(10, 24, 1.0, 1.5), (10, 16, 1.0, 1.0), (10, 8, 1.0, 0.7)]
+    else:
+        levels = [(10, 16, 0.6, 1.5), (10, 16, 0.4, 1.0), (10, 16, 0.25, 0.7)]
+    prm = O.Params(neigh_mode=mode)
+    o = O.register_pyramid(case.X, case.Y0, prm, levels)
+    with Gpu(case.X, case.Y0, neigh_mode=mode, E=30) as g:
+        res = scgr.run_pyramid(g.ctx, levels)
+    assert res.iterations == 30
+    assert pose_close(res, o, synth.bbox_diag(case.X))
+
+
+def test_set_neighbourhood_rejects_bad_values():
+    case = synth.mild(n=300)
+    with Gpu(case.X, case.Y0) as g:
+        for args in ((2, 1.0, 1.0), (33, 1.0, 1.0), (16, 0.0, 1.0), (16, 1.0, -1.0)):
+            with pytest.raises(scgr.ScgrError):
+                scgr.scgr_set_neighbourhood(g.ctx, *args)
+
+
+def test_nearest_bit_exact():
+    import torch
+    sc = synth.scale_case()
+    X = sc.X[synth.subsample(sc.X, 3000, 71)]
+    Q = sc.Y0[synth.subsample(sc.Y0, 1200, 72)]
+    idx_ref, key_ref = O.nearest(Q, X)
+    with Gpu(X, X) as g:
+        idx = torch.empty(len(Q), dtype=torch.int32, device="cuda")
+        key = torch.empty(len(Q), dtype=torch.float32, device="cuda")
+        scgr.scgr_nearest(g.ctx, torch.from_numpy(Q).cuda(), idx, key)
+        np.testing.assert_array_equal(idx.cpu().numpy(), idx_ref)
+        np.testing.assert_array_equal(key.cpu().numpy(), key_ref)
+
+
+def test_change_mask_at_identity_pose():
+    """A template whose part moved between captures: the moved part is
+    flagged.  At the identity pose the moved template is Y0 itself, so the
+    oracle gets exactly the GPU's query points."""
+    import torch
+    rng = np.random.default_rng(81)
+    surf = synth.EllipsoidUnion.random(rng, 3)
+    X = surf.sample_surface(rng, 2000).astype(np.float32)
+    Y0 = X[synth.subsample(X, 1500, 82)].copy()
+    Y0[:200] += np.float32(0.2)                      # a part that moved
+    thr = 0.05
+    mask_ref, dist_ref = O.change_mask(Y0, X, thr)
+    with Gpu(X, Y0) as g:
+        mask = torch.empty(len(Y0), dtype=torch.uint8, device="cuda")
+        dist = torch.empty(len(Y0), dtype=torch.float32, device="cuda")
+        scgr.scgr_change_mask(g.ctx, thr, mask, dist)
+        np.testing.assert_array_equal(mask.cpu().numpy(), mask_ref)
+        np.testing.assert_allclose(dist.cpu().numpy(), dist_ref, rtol=1e-6)
+    assert mask_ref[:200].mean() > 0.5 and mask_ref[200:].mean() < 0.05

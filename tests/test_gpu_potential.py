@@ -109,3 +109,16 @@ def test_full_size_50k_sampled_rows_and_identities():
     F = f4[:, :3].astype(np.float64).sum(axis=0)
     assert rel_l2(g7[3:6], -F) <= 1e-5
     assert U > 0 and np.isfinite(g7).all()
+
+
+@pytest.mark.parametrize("p", [1.0, 2.0, 1.5])
+def test_force_vjp_matches_oracle(p):
+    case = synth.mild(n=700)
+    d = O.descriptors(case.X, case.Y0, O.Params(p=p))
+    v = np.random.default_rng(4).normal(size=(len(case.Y0), 3)).astype(np.float32)
+    ref = O.force_vjp(case.Y0, case.X, d["aY"], d["aX"], d["sigma"], p, 1, v)
+    with Gpu(case.X, case.Y0, p=p) as g:
+        out = torch.empty((g.m, 3), dtype=torch.float32, device="cuda")
+        scgr.scgr_force_vjp(g.ctx, torch.from_numpy(v).cuda(), out)
+        got = out.cpu().numpy()
+    assert rel_l2(got, ref) <= 1e-5

@@ -1,6 +1,7 @@
 """Pins of the curvature descriptor (Sec. III-A, Sec. IV; reading R2:
 a = lambda_min / trace of the 1/k neighbourhood covariance) and sigma (R3)."""
 import numpy as np
+import pytest
 
 import oracle as O
 
@@ -57,3 +58,24 @@ def test_sigma_population_std():
     a = np.array([0.0, 0.2] * 50)
     assert abs(O.sigma_auto(a) - 0.1) < 1e-15
     assert O.sigma_auto(np.full(10, 0.05)) == 1.0      # degenerate spread -> 1
+
+
+def test_radius_curvature_hand_cases():
+    # axis star, e = 2/7; a radius of 1.2 (between 1 and sqrt 2): the centre sees all 7 points -> 1/3, each
+    # outer point sees itself and the centre (two points, collinear) -> 0
+    P = np.array([[0, 0, 0], [1, 0, 0], [-1, 0, 0], [0, 1, 0], [0, -1, 0], [0, 0, 1], [0, 0, -1]], float)
+    a = O.curvature_radius(P, radius_scale=1.2 / np.sqrt(2.0 / 7.0))
+    assert a[0] == pytest.approx(1.0 / 3.0, rel=1e-12)
+    np.testing.assert_allclose(a[1:], 0.0, atol=1e-15)
+    # a radius large enough for the whole cloud reproduces the whole-cloud kNN curvature
+    rng = np.random.default_rng(3)
+    Q = (rng.normal(size=(30, 3)) * np.array([3.0, 1.0, 0.2])).astype(np.float32)   # inputs are float32
+    big = O.curvature_radius(Q, radius_scale=100.0)
+    ref = O.curvature(Q, np.tile(np.arange(30), (30, 1)))
+    np.testing.assert_allclose(big, ref, rtol=1e-10)
+
+
+def test_radius_curvature_planar_cloud_is_zero():
+    rng = np.random.default_rng(4)
+    P = np.c_[rng.uniform(-1, 1, (60, 2)), np.zeros(60)]
+    np.testing.assert_allclose(O.curvature_radius(P), 0.0, atol=1e-15)

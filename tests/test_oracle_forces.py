@@ -157,3 +157,20 @@ def test_pose_gradient_at_zero_rotation():
         fd = (O.pose_potential_and_grad(pp, Y0, X, aY, aX, 0.1, 2.0, 1)[0]
               - O.pose_potential_and_grad(pm, Y0, X, aY, aX, 0.1, 2.0, 1)[0]) / (2 * h)
         assert abs(fd - g[q]) <= 1e-6 * max(1.0, abs(g[q]))
+
+
+@pytest.mark.parametrize("p", [1.0, 2.0, 1.5])
+def test_force_vjp_matches_central_differences(p):
+    X, Y, aX, aY = rand_case(10, n=25, m=5)
+    v = np.random.default_rng(11).normal(size=(5, 3))
+    got = O.force_vjp(Y, X, aY, aX, 0.1, p, 1, v)
+    h = 1e-6
+    for i in range(len(Y)):
+        J = np.zeros((3, 3))
+        for c in range(3):
+            Yp = Y.copy(); Yp[i, c] += h
+            Ym = Y.copy(); Ym[i, c] -= h
+            fp, _ = O.forces_rows(Yp, X, aY, aX, 0.1, p, 1, [i])
+            fm, _ = O.forces_rows(Ym, X, aY, aX, 0.1, p, 1, [i])
+            J[:, c] = (fp[0] - fm[0]) / (2 * h)
+        np.testing.assert_allclose(got[i], J.T @ v[i], rtol=1e-6, atol=1e-9)

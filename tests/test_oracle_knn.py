@@ -62,3 +62,22 @@ def test_knn_invariant_under_exact_shift():
 def test_knn_rejects_k_above_n():
     with pytest.raises(ValueError):
         O.knn(np.zeros((3, 3), np.float32), 4)
+
+
+def test_nearest_matches_scalar_bruteforce():
+    rng = np.random.default_rng(8)
+    X = rng.integers(-3, 3, size=(40, 3)).astype(np.float32)    # integer grid: exact ties
+    Q = rng.integers(-3, 3, size=(25, 3)).astype(np.float32) + np.float32(0.5)
+    idx, key = O.nearest(Q, X)
+    for i in range(len(Q)):
+        cands = []
+        for j in range(len(X)):
+            dx = np.float32(Q[i, 0]) - np.float32(X[j, 0])
+            dy = np.float32(Q[i, 1]) - np.float32(X[j, 1])
+            dz = np.float32(Q[i, 2]) - np.float32(X[j, 2])
+            k = np.float32(np.float32(np.float32(dx * dx) + np.float32(dy * dy)) + np.float32(dz * dz))
+            cands.append((float(k), j))
+        cands.sort()
+        assert (int(idx[i]), float(key[i])) == (cands[0][1], cands[0][0])
+    mask, dist = O.change_mask(Q, X, 0.9)
+    np.testing.assert_array_equal(mask, (key > np.float32(0.81)).astype(np.uint8))

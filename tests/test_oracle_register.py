@@ -57,3 +57,12 @@ def test_paper_rotation_reduced():
     R, t, s = case.inverse_pose()
     assert rot_err_deg(res["R"], R) < 25.0
     assert res["s"] == pytest.approx(s, rel=5e-3)
+
+
+def test_pyramid_single_level_equals_register():
+    case = synth.mild(n=300)
+    prm = O.Params()
+    a = O.register_pyramid(case.X, case.Y0, prm, [(8, 16, 1.0, 1.0)])
+    b = O.register(case.X, case.Y0, prm, iterations=8)
+    np.testing.assert_allclose(a["Y"], b["Y"], atol=1e-12)
+    assert a["s"] == pytest.approx(b["s"], rel=1e-14)
