@@ -259,6 +259,68 @@ def bench_batch(args, scgr, torch, dev, steps, warmup):
             "timing": "host wall clock around each synchronising call, L2 flushed before each"}
 
 
+def _timed(fn, steps, warmup, torch):
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    out = []
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        fn()
+        torch.cuda.synchronize()
+        out.append(time.perf_counter() - t0)
+    return sum(out) / len(out)
+
+
+def bench_diff(args, scgr, torch, dev, steps, warmup):
+    """Differentiation form at 50,000 x 50,000 (rotation 30 deg, noise 0.01 of
+    the diagonal): the potential alone, potential + adjoint with tile
+    recomputation, and potential + adjoint from stored pair terms."""
+    from paper_1902_01061_gb300 import synth
+    case = synth.diff_case()
+    n, m = len(case.X), len(case.Y0)
+    ctx = scgr.scgr_create(scgr.scgr_default_params(p=2.0), torch.cuda.current_stream())
+    try:
+        scgr.scgr_set_reference(ctx, torch.from_numpy(case.X).to(dev))
+        scgr.scgr_set_template(ctx, torch.from_numpy(case.Y0).to(dev))
+        scgr.scgr_compute_descriptors(ctx)
+        pose = [0.1, -0.2, 0.3, 0.05, 0.0, -0.05, 1.02]
+        gx = torch.empty((m, 3), dtype=torch.float32, device=dev)
+        fwd = _timed(lambda: scgr.scgr_potential(ctx, pose, want_grad=False), steps, warmup, torch)
+        both = _timed(lambda: scgr.scgr_potential(ctx, pose, grad_xyz_out=gx), steps, warmup, torch)
+        stored = _timed(lambda: scgr.scgr_potential_stored(ctx, pose, grad_xyz_out=gx), steps, warmup, torch)
+    finally:
+        scgr.scgr_destroy(ctx)
+    return {"workload": "50,000 x 50,000 points, rotation 30 deg, noise 0.01 of the diagonal, p=2",
+            "potential_ms": fwd * 1e3, "potential_and_adjoint_recompute_ms": both * 1e3,
+            "potential_and_adjoint_stored_ms": stored * 1e3,
+            "stored_pair_terms_bytes": n * m * 4,
+            "adjoint_pair_interactions_per_s": 2 * n * m / both,
+            "timing": "host wall clock around each synchronising call"}
+
+
+def bench_scale(args, scgr, torch, dev, steps, warmup):
+    """One registration of the 35,000-point case (200 iterations) per step."""
+    from paper_1902_01061_gb300 import synth
+    case = synth.scale_case()
+    n, m = len(case.X), len(case.Y0)
+    X = torch.from_numpy(case.X).to(dev)
+    Y = torch.from_numpy(case.Y0).to(dev)
+    ctx = scgr.scgr_create(scgr.scgr_default_params(p=2.0, use_graph=1), torch.cuda.current_stream())
+    try:
+        def one():
+            scgr.scgr_set_reference(ctx, X)
+            scgr.scgr_set_template(ctx, Y)
+            scgr.scgr_compute_descriptors(ctx)
+            scgr.scgr_run(ctx, 200)
+            scgr.scgr_get_result(ctx)
+        sec = _timed(one, steps, warmup, torch)
+    finally:
+        scgr.scgr_destroy(ctx)
+    return {"workload": "35,000 reference x 30,800 template points, 200 iterations, p=2, CUDA graph",
+            "ms_per_registration": sec * 1e3, "pair_interactions_per_s": n * m * 200 / sec}
+
+
 def run_reference(args, ws, rank):
     """The oracle arm: bounded samples of the same workload on the host cores."""
     if rank != 0:
@@ -310,7 +372,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-rows", type=int, default=48)
-    ap.add_argument("--no-batch", action="store_true", help="skip the 512-pair batched leg")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched, differentiation and 35k legs")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default tile shapes")
     ap.add_argument("--plan", default=None, help="pin the force tile shape 'P,TPB[,OCC]' (no autotuning), e.g. 2,256,1")
     args = ap.parse_args()
@@ -429,9 +491,11 @@ def main():
         e2e = {"value": ws * pairs_per_step / e2e_s, "unit": "pair-interactions/s",
                "h2d_bytes_per_step": (n + m) * 12, "d2h_bytes_per_step": m * 12 + 8 * 13 + 8}
     scgr.scgr_destroy(ctx)
-    batch = None
+    batch = diff = scale = None
     if ws == 1 and not args.no_batch:
         batch = bench_batch(args, scgr, torch, dev, args.steps, args.warmup)
+        diff = bench_diff(args, scgr, torch, dev, args.steps, args.warmup)
+        scale = bench_scale(args, scgr, torch, dev, args.steps, args.warmup)
 
     if rank != 0:
         if ws > 1:
@@ -467,6 +531,8 @@ def main():
         "roofline": roofline,
         "e2e": e2e,
         "batch": batch,
+        "differentiation": diff,
+        "scale_case": scale,
     }
     line["peaks_measured"] = measured_peaks(scgr, num_sms, sm_mhz or sm_max_mhz)
     if ws == 1 and not args.no_cpu_baseline:

@@ -219,6 +219,14 @@ SCGR_EXPORT scgr_status scgr_forces(scgr_ctx* ctx, float* f4_dev);
 SCGR_EXPORT scgr_status scgr_potential(scgr_ctx* ctx, const double pose7[7], double* U_out,
                                        double* grad_pose7, float* grad_xyz_dev);
 
+/* Same outputs as scgr_potential, computed the other way round for
+ * comparison: the forward pass stores every pair weight w_ij (float32,
+ * M x N bytes x 4 of device memory, allocated on first use; OOM if it does
+ * not fit) and the backward pass streams them back from HBM instead of
+ * recomputing the tiles.  Synchronises. */
+SCGR_EXPORT scgr_status scgr_potential_stored(scgr_ctx* ctx, const double pose7[7], double* U_out,
+                                              double* grad_pose7, float* grad_xyz_dev);
+
 /* Vector-Jacobian product of the force field at the current pose:
  * grad_i = (d f_i / d Y_i)^T v_i with f_i of Eq. 5 (without G; descriptors
  * fixed).  f_i depends only on Y_i, and

@@ -65,7 +65,7 @@ struct scgr_ctx {
   int64_t knn_grid_min = 65536; // clouds with at least this many points use the grid kNN (tunable)
   ForceTuning ftune;            // force-plan overrides (tunable)
   int reuse_pose_free = 1;      // p = 1: one force pass per scgr_run (tunable)
-  DevBuf gcell, gcount, gstart, gcursor, gblock, gsorted, gsidx, gbb, cd_key, cd_moved;
+  DevBuf gcell, gcount, gstart, gcursor, gblock, gsorted, gsidx, gbb, cd_key, cd_moved, wstore, wupart, wpartial;
   cudaGraph_t bgraph = nullptr;
   cudaGraphExec_t bgexec = nullptr;
 
@@ -398,7 +398,7 @@ void scgr_destroy(scgr_ctx* c) {
                     &c->bXr, &c->bXA, &c->bY0r, &c->bpartial, &c->bblockpart, &c->bpairs, &c->bitems,
                     &c->bcpair, &c->btabX, &c->btabY, &c->bxoff, &c->byoff, &c->bstats, &c->bposes,
                     &c->gcell, &c->gcount, &c->gstart, &c->gcursor, &c->gblock, &c->gsorted, &c->gsidx, &c->gbb,
-                    &c->cd_key, &c->cd_moved};
+                    &c->cd_key, &c->cd_moved, &c->wstore, &c->wupart, &c->wpartial};
   for (DevBuf* b : bufs) release(*b);
   if (c->pose) cudaFree(c->pose);
   if (c->pose_eval) cudaFree(c->pose_eval);
@@ -609,6 +609,47 @@ scgr_status scgr_forces(scgr_ctx* c, float* f4_dev) {
                             (const float4*)c->Y0r.p, (const double*)c->aY64.p + c->row0, c->prm.g_mode, c->pose,
                             (float4*)f4_dev, (double*)c->blockpart.p));
   return SCGR_OK;
+}
+
+scgr_status scgr_potential_stored(scgr_ctx* c, const double pose7[7], double* U_out, double* grad_pose7,
+                                  float* grad_xyz_dev) {
+  if (!c || !pose7 || !U_out) return fail(c, SCGR_ERR_INVALID_ARG, "NULL argument");
+  c->err.clear();
+  if (!c->have_desc) return fail(c, SCGR_ERR_STATE, "compute descriptors first");
+  if (c->rows >= 0) return fail(c, SCGR_ERR_STATE, "the potential needs the whole template (a row range is set)");
+  for (int q = 0; q < 7; ++q)
+    if (!std::isfinite(pose7[q])) return fail(c, SCGR_ERR_INVALID_ARG, "non-finite pose");
+  if (!(pose7[6] > 0.0)) return fail(c, SCGR_ERR_INVALID_ARG, "scale must be > 0");
+  const int n = (int)c->n, m = (int)c->m;
+  const int nb = (n + 255) / 256;
+  SCGR_CK(c, ensure(c->wstore, (size_t)n * m * sizeof(float)));
+  SCGR_CK(c, ensure(c->wupart, (size_t)nb * m * sizeof(double)));
+  SCGR_CK(c, ensure(c->wpartial, (size_t)c->mpad * sizeof(float4)));
+  Launch L = c->L();
+  double* d7 = c->aux + 48;
+  SCGR_CK(c, cudaMemcpyAsync(d7, pose7, 7 * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  SCGR_CK(c, launch_pose_from7(L, d7, c->pose_eval, c->stats));
+  // forward: store w_ij and sum U
+  SCGR_CK(c, launch_store_pairs(L, (const float2*)c->XA.p, (const float4*)c->Xr.p, n, (const float4*)c->Y0r.p,
+                                (const double*)c->aY64.p, c->prm.g_mode, m, c->pose_eval, c->qexp,
+                                (float*)c->wstore.p, (double*)c->wupart.p, c->aux + 3));
+  if (grad_pose7 || grad_xyz_dev) {
+    // backward from the stored terms
+    SCGR_CK(c, launch_stored_rows(L, (const float*)c->wstore.p, n, m, (const float4*)c->Xr.p,
+                                  (float4*)c->wpartial.p));
+    SCGR_CK(c, launch_adjoint_combine(L, (const float4*)c->wpartial.p, 1, (int)c->mpad, m, (const float4*)c->Y0r.p,
+                                      (const double*)c->aY64.p, c->prm.g_mode, c->pose_eval, grad_xyz_dev,
+                                      (double*)c->blockpart.p));
+    SCGR_CK(c, launch_column_sum13(L, (const double*)c->blockpart.p, combine_blocks(c->mpad), c->aux + 16));
+    SCGR_CK(c, launch_adjoint_finish(L, c->aux + 16, d7, c->pose_eval, c->aux + 32));
+  }
+  double h[40];
+  SCGR_CK(c, cudaMemcpyAsync(h, c->aux, 40 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  SCGR_CK(c, cudaStreamSynchronize(c->stream));
+  *U_out = h[3] / (c->prm.p + 1.0);
+  if (grad_pose7)
+    for (int q = 0; q < 7; ++q) grad_pose7[q] = h[32 + q];
+  return read_error_word(c);
 }
 
 scgr_status scgr_force_vjp(scgr_ctx* c, const float* v_dev, float* grad_dev) {

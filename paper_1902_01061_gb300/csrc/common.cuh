@@ -234,6 +234,10 @@ cudaError_t launch_pose_init_multi(Launch L, DevPose* poses, const DevStats* sta
 cudaError_t launch_force_vjp(Launch L, const float4* Xr, const float2* XA, int ntiles, const float4* Y0r,
                              const double* aY64, int g_mode, int m, const DevPose* ps, double p, const float* v,
                              float* grad);
+cudaError_t launch_store_pairs(Launch L, const float2* XA, const float4* Xr, int n, const float4* Y0r,
+                               const double* aY64, int g_mode, int m, const DevPose* ps, float qexp, float* Wst,
+                               double* Upart, double* Uout);
+cudaError_t launch_stored_rows(Launch L, const float* Wst, int n, int m, const float4* Xr, float4* partial);
 cudaError_t launch_pose_from7(Launch L, const double* pose7_dev, DevPose* ps, const DevStats* st);
 cudaError_t launch_adjoint_combine(Launch L, const float4* partial, int S, int mpad, int m, const float4* Y0r,
                                    const double* aY64, int g_mode, const DevPose* ps, float* grad_xyz,

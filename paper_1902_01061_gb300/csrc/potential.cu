@@ -254,6 +254,97 @@ cudaError_t launch_force_vjp(Launch L, const float4* Xr, const float2* XA, int n
   return cudaGetLastError();
 }
 
+// ---- stored pair terms (comparison variant of the adjoint) -----------------
+// Forward: every pair weight w_ij = g d^(p-1) is written to W[i][n] (float32,
+// M x N, coalesced along j) and the potential U = sum aY w d^2 / (p + 1) is
+// summed per block.  Backward: one block per template point streams its row
+// back from HBM and forms the same per-point sums (sum w, sum w X') that the
+// force kernel accumulates, so the adjoint reduction is shared.
+constexpr int ST_TPB = 256;
+
+__global__ void __launch_bounds__(ST_TPB)
+    store_pairs_kernel(const float* __restrict__ Xr, const float* __restrict__ XA, int n,
+                       const float4* __restrict__ Y0r, const double* __restrict__ aY64, int g_mode,
+                       const DevPose* __restrict__ ps, float qexp, float* __restrict__ Wst,
+                       double* __restrict__ Upart) {
+  __shared__ double sh[1][RED_THREADS];
+  const int i = blockIdx.x;  // template point (grid.x: no 65535 limit)
+  const int j = blockIdx.y * ST_TPB + threadIdx.x;
+  float A[9], b[3];
+#pragma unroll
+  for (int q = 0; q < 9; ++q) A[q] = ps->A[q];
+#pragma unroll
+  for (int q = 0; q < 3; ++q) b[q] = ps->b[q];
+  const float4 y0 = Y0r[i];
+  float yx, yy, yz;
+  tpoint(y0, A, b, yx, yy, yz);
+  double u[1] = {0.0};
+  if (j < n) {
+    const size_t t = (size_t)(j / FORCE_TJ), r = (size_t)(j % FORCE_TJ);
+    const float* xr = Xr + t * 4 * FORCE_TJ + r;
+    const float* xa = XA + t * 2 * FORCE_TJ + r;
+    const float rx = yx - xr[0], ry = yy - xr[FORCE_TJ], rz = yz - xr[2 * FORCE_TJ];
+    const float d2 = fmaf(rz, rz, fmaf(ry, ry, rx * rx));
+    const float uu = xa[0] - y0.w;
+    const float ep = fmaf(uu, uu, xa[FORCE_TJ]);
+    const float w = d2 > 0.f ? exp2f(fmaf(qexp, log2f(d2), -ep)) : (qexp == 0.f ? exp2f(-ep) : 0.f);
+    Wst[(size_t)i * n + j] = w;
+    u[0] = (double)w * (double)d2;
+  }
+  block_sum<1>(u, sh);
+  if (threadIdx.x == 0) {
+    const double ay = g_mode == 1 ? aY64[i] : 1.0;
+    Upart[(size_t)i * gridDim.y + blockIdx.y] = ay * u[0];
+  }
+}
+
+__global__ void __launch_bounds__(ST_TPB)
+    stored_rows_kernel(const float* __restrict__ Wst, int n, const float* __restrict__ Xr,
+                       float4* __restrict__ partial) {
+  __shared__ double sh[4][RED_THREADS];
+  const int i = blockIdx.x;
+  double v[4] = {0, 0, 0, 0};
+  const float* row = Wst + (size_t)i * n;
+  for (int j = threadIdx.x; j < n; j += ST_TPB) {
+    const double w = row[j];
+    const size_t t = (size_t)(j / FORCE_TJ), r = (size_t)(j % FORCE_TJ);
+    const float* xr = Xr + t * 4 * FORCE_TJ + r;
+    v[0] += w;
+    v[1] += w * xr[0];
+    v[2] += w * xr[FORCE_TJ];
+    v[3] += w * xr[2 * FORCE_TJ];
+  }
+  block_sum<4>(v, sh);
+  if (threadIdx.x == 0) partial[i] = make_float4((float)v[0], (float)v[1], (float)v[2], (float)v[3]);
+}
+
+__global__ void __launch_bounds__(RED_THREADS) sum_rows_kernel(const double* __restrict__ part, int64_t count,
+                                                               double* __restrict__ out) {
+  __shared__ double sh[1][RED_THREADS];
+  double v[1] = {0.0};
+  for (int64_t q = threadIdx.x; q < count; q += RED_THREADS) v[0] += part[q];
+  block_sum<1>(v, sh);
+  if (threadIdx.x == 0) out[0] = v[0];
+}
+
+cudaError_t launch_store_pairs(Launch L, const float2* XA, const float4* Xr, int n, const float4* Y0r,
+                               const double* aY64, int g_mode, int m, const DevPose* ps, float qexp, float* Wst,
+                               double* Upart, double* Uout) {
+  const int nb = (n + ST_TPB - 1) / ST_TPB;
+  store_pairs_kernel<<<dim3(m, nb), ST_TPB, 0, L.stream>>>(reinterpret_cast<const float*>(Xr),
+                                                          reinterpret_cast<const float*>(XA), n, Y0r, aY64, g_mode,
+                                                          ps, qexp, Wst, Upart);
+  sum_rows_kernel<<<1, RED_THREADS, 0, L.stream>>>(Upart, (int64_t)nb * m, Uout);
+  if (L.counter) *L.counter += 2;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_stored_rows(Launch L, const float* Wst, int n, int m, const float4* Xr, float4* partial) {
+  stored_rows_kernel<<<m, ST_TPB, 0, L.stream>>>(Wst, n, reinterpret_cast<const float*>(Xr), partial);
+  if (L.counter) ++*L.counter;
+  return cudaGetLastError();
+}
+
 cudaError_t launch_pose_from7(Launch L, const double* pose7_dev, DevPose* ps, const DevStats* st) {
   pose_from7_kernel<<<1, 32, 0, L.stream>>>(pose7_dev, ps, st);
   if (L.counter) ++*L.counter;

@@ -31,7 +31,7 @@ EXPORTED = (
     "scgr_set_curvature", "scgr_set_force_timing", "scgr_get_force_timing", "scgr_forces_static",
     "scgr_potential", "scgr_batch_run", "scgr_set_tuning", "scgr_set_row_range", "scgr_step_partials",
     "scgr_step_apply", "scgr_get_plan", "scgr_microbench", "scgr_set_neighbourhood", "scgr_nearest",
-    "scgr_change_mask", "scgr_force_vjp",
+    "scgr_change_mask", "scgr_force_vjp", "scgr_potential_stored",
 )
 SCGR_TUNE_BATCH_CHUNK_TILES = 1
 SCGR_TUNE_KNN_GRID_MIN = 2
@@ -112,6 +112,7 @@ def load():
         "scgr_get_plan": (S, [ctx, POINTER(c_int)]),
         "scgr_set_neighbourhood": (S, [ctx, c_int, c_double, c_double]),
         "scgr_force_vjp": (S, [ctx, c_void_p, c_void_p]),
+        "scgr_potential_stored": (S, [ctx, POINTER(c_double), POINTER(c_double), POINTER(c_double), c_void_p]),
         "scgr_nearest": (S, [ctx, c_void_p, c_int64, c_void_p, c_void_p]),
         "scgr_change_mask": (S, [ctx, c_double, c_void_p, c_void_p]),
         "scgr_microbench": (S, [c_int, c_int, c_void_p, c_void_p, POINTER(c_int64), POINTER(c_double)]),
@@ -380,6 +381,17 @@ def run_pyramid(ctx, levels):
         scgr_set_neighbourhood(ctx, k, rscale, sscale)
         scgr_run(ctx, iters)
     return scgr_get_result(ctx)
+
+
+def scgr_potential_stored(ctx, pose7, want_grad: bool = True, grad_xyz_out=None):
+    """As scgr_potential, with the forward pass storing the N x M pair
+    weights and the backward pass reading them (comparison variant)."""
+    p7 = (c_double * 7)(*[float(v) for v in np.asarray(pose7, dtype=np.float64).reshape(7)])
+    U = c_double()
+    g7 = (c_double * 7)() if want_grad else None
+    gx = _dev_ptr(grad_xyz_out, "float32", (3,)) if grad_xyz_out is not None else None
+    _check(load().scgr_potential_stored(ctx, p7, ctypes.byref(U), g7, gx), ctx)
+    return float(U.value), (np.array(g7[:]) if want_grad else None)
 
 
 def scgr_forces(ctx, f4_out) -> None:

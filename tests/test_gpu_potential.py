@@ -122,3 +122,19 @@ def test_force_vjp_matches_oracle(p):
         scgr.scgr_force_vjp(g.ctx, torch.from_numpy(v).cuda(), out)
         got = out.cpu().numpy()
     assert rel_l2(got, ref) <= 1e-5
+
+
+@pytest.mark.parametrize("p", [2.0, 1.0])
+def test_stored_pair_terms_match_recomputation(p):
+    case = synth.mild(n=800)
+    d = O.descriptors(case.X, case.Y0, O.Params(p=p))
+    pose = POSES[0]
+    with Gpu(case.X, case.Y0, p=p) as g:
+        gx_r = torch.empty((g.m, 3), dtype=torch.float32, device="cuda")
+        gx_s = torch.empty((g.m, 3), dtype=torch.float32, device="cuda")
+        U_r, g_r = scgr.scgr_potential(g.ctx, pose, grad_xyz_out=gx_r)
+        U_s, g_s = scgr.scgr_potential_stored(g.ctx, pose, grad_xyz_out=gx_s)
+    Uo, g7o, gY0o = O.pose_potential_and_grad(pose, case.Y0, case.X, d["aY"], d["aX"], d["sigma"], p, 1)
+    assert abs(U_s - Uo) <= 1e-6 * abs(Uo) and abs(U_r - Uo) <= 1e-6 * abs(Uo)
+    assert max(block_rel(g_s, g7o)) <= 1e-4 and max(block_rel(g_r, g7o)) <= 1e-4
+    assert rel_l2(gx_s.cpu().numpy(), gY0o) <= 1e-5

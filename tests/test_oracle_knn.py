@@ -81,3 +81,29 @@ def test_nearest_matches_scalar_bruteforce():
         assert (int(idx[i]), float(key[i])) == (cands[0][1], cands[0][0])
     mask, dist = O.change_mask(Q, X, 0.9)
     np.testing.assert_array_equal(mask, (key > np.float32(0.81)).astype(np.uint8))
+
+
+def _per_op_key(q, p):
+    dx = np.float32(q[0]) - np.float32(p[0])
+    dy = np.float32(q[1]) - np.float32(p[1])
+    dz = np.float32(q[2]) - np.float32(p[2])
+    return np.float32(np.float32(np.float32(dx * dx) + np.float32(dy * dy)) + np.float32(dz * dz))
+
+
+def test_knn_key_is_rounded_per_operation():
+    """(a, b, c) and (c, a, b) are equally far from the origin, but the float32
+    key (dx*dx + dy*dy) + dz*dz rounds differently for them; the order must
+    follow the rounded keys (R1), not the exact distances."""
+    rng = np.random.default_rng(123)
+    q = np.zeros(3, np.float32)
+    for _ in range(10000):
+        a, b, c = rng.uniform(0.5, 1.0, 3).astype(np.float32)
+        p_lo, p_hi = np.array([c, a, b], np.float32), np.array([a, b, c], np.float32)
+        if _per_op_key(q, p_hi) < _per_op_key(q, p_lo):     # the higher index must come first
+            break
+    else:
+        pytest.skip("no distinguishing case found")
+    far = rng.uniform(5.0, 6.0, size=(6, 3)).astype(np.float32)
+    P = np.concatenate([q[None], p_lo[None], p_hi[None], far])
+    nb = O.knn(P, 3)
+    assert list(nb[0]) == [0, 2, 1]
