@@ -319,11 +319,16 @@ SCGR_EXPORT scgr_status scgr_step_apply(scgr_ctx* ctx, const double tot13[13]);
 #define SCGR_TUNE_FORCE_P 3           /* force kernel template points per thread: 0 auto, 1, 2, 4 */
 #define SCGR_TUNE_FORCE_TPB 4         /* force kernel threads per block: 0 auto, 128, 256 */
 #define SCGR_TUNE_FORCE_SPLITS 5      /* force kernel reference splits: 0 auto (wave-filling), >= 1 */
+#define SCGR_TUNE_BATCH_P 8           /* template points per thread in the batched force kernel: 1 (default), 2 */
 #define SCGR_TUNE_FORCE_OCC 7         /* 1: force kernel variant with a tighter register budget and more
                                          resident blocks per SM (3 at 256 threads, 4 at 128); 0 default */
-#define SCGR_TUNE_REUSE_POSE_FREE 6   /* 1 (default): for p = 1, whose pair weights do not depend on the
-                                         pose, scgr_run computes the force sums once per call and reuses
-                                         them in its later iterations (bit-identical); 0: every iteration */
+#define SCGR_TUNE_REUSE_POSE_FREE 6   /* 1 (default): odd integer p skips the per-iteration all-pairs pass.
+                                         p = 1: the pair weights do not depend on the pose, so scgr_run
+                                         computes the force sums once per call and reuses them
+                                         (bit-identical).  p = 3: the sums are a quadratic form in the
+                                         template point over 14 moments of the similarity weights,
+                                         computed once per call (equal up to rounding).  0: the all-pairs
+                                         pass in every iteration */
 /* Set one knob.  A force-plan knob re-plans at once when descriptors exist
  * (records and workspace are rebuilt; descriptors and pose are kept),
  * otherwise at scgr_compute_descriptors.  INVALID_ARG for an unknown key or

@@ -18,7 +18,8 @@ from . import scgr
 
 SINGLE_CANDIDATES = [(P, tpb, occ) for P in (1, 2, 4) for tpb in (128, 256) for occ in (0, 1)
                      if not (P == 4 and tpb == 256 and occ == 1)]
-BATCH_CHUNKS = (4, 8, 16, 32)
+BATCH_CHUNKS = (8, 16, 32)
+BATCH_P = (1, 2)
 
 
 def cache_path() -> str:
@@ -114,18 +115,22 @@ def tune_batch(ctx, ref_off, ref_xyz, tmp_off, tmp_xyz, p: float, iterations: in
     to = np.asarray(tmp_off, dtype=np.int64)
     work = int(np.sum(np.diff(ro) * np.diff(to)))
     results = []
-    for ct in BATCH_CHUNKS:
-        scgr.scgr_set_tuning(ctx, scgr.SCGR_TUNE_BATCH_CHUNK_TILES, ct)
-        scgr.scgr_batch_run(ctx, ro, ref_xyz, to, tmp_xyz, 1)           # warm
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        scgr.scgr_batch_run(ctx, ro, ref_xyz, to, tmp_xyz, iterations)
-        results.append((time.perf_counter() - t0, ct))
+    for P in BATCH_P:
+        for ct in BATCH_CHUNKS:
+            scgr.scgr_set_tuning(ctx, scgr.SCGR_TUNE_BATCH_P, P)
+            scgr.scgr_set_tuning(ctx, scgr.SCGR_TUNE_BATCH_CHUNK_TILES, ct)
+            scgr.scgr_batch_run(ctx, ro, ref_xyz, to, tmp_xyz, 1)           # warm
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            scgr.scgr_batch_run(ctx, ro, ref_xyz, to, tmp_xyz, iterations)
+            results.append((time.perf_counter() - t0, ct, P))
     results.sort()
-    best_s, ct = results[0]
+    best_s, ct, P = results[0]
+    scgr.scgr_set_tuning(ctx, scgr.SCGR_TUNE_BATCH_P, P)
     scgr.scgr_set_tuning(ctx, scgr.SCGR_TUNE_BATCH_CHUNK_TILES, ct)
-    best = {"chunk_tiles": ct, "s": best_s, "iterations": iterations,
-            "tried": [{"chunk_tiles": c, "s": t} for t, c in results], "when": time.strftime("%Y-%m-%d %H:%M:%S")}
+    best = {"chunk_tiles": ct, "P": P, "s": best_s, "iterations": iterations,
+            "tried": [{"chunk_tiles": c, "P": q, "s": t} for t, c, q in results],
+            "when": time.strftime("%Y-%m-%d %H:%M:%S")}
     if store:
         _store(batch_key(gpu_name(), len(ro) - 1, work, p), best)
     return best
@@ -142,4 +147,5 @@ def apply_cached_batch(ctx, npairs: int, work: int, p: float) -> dict | None:
     hit = _load().get(batch_key(gpu_name(), npairs, work, p))
     if hit:
         scgr.scgr_set_tuning(ctx, scgr.SCGR_TUNE_BATCH_CHUNK_TILES, hit["chunk_tiles"])
+        scgr.scgr_set_tuning(ctx, scgr.SCGR_TUNE_BATCH_P, hit.get("P", 1))
     return hit

@@ -62,10 +62,12 @@ struct scgr_ctx {
   DevBuf bX4, bY4, bknnX, bknnY, baX64, baY64, baX32, baY32, bXr, bXA, bY0r, bpartial, bblockpart,
       bpairs, bitems, bcpair, btabX, btabY, bxoff, byoff, bstats, bposes;
   int batch_chunk_tiles = 16;   // reference tiles per batched work item (tunable)
+  int batch_P = 1;              // template points per thread in the batched force kernel (tunable)
   int64_t knn_grid_min = 65536; // clouds with at least this many points use the grid kNN (tunable)
   ForceTuning ftune;            // force-plan overrides (tunable)
   int reuse_pose_free = 1;      // p = 1: one force pass per scgr_run (tunable)
-  DevBuf gcell, gcount, gstart, gcursor, gblock, gsorted, gsidx, gbb, cd_key, cd_moved, wstore, wupart, wpartial;
+  DevBuf gcell, gcount, gstart, gcursor, gblock, gsorted, gsidx, gbb, cd_key, cd_moved, wstore, wupart, wpartial,
+      mpart, mom;
   cudaGraph_t bgraph = nullptr;
   cudaGraphExec_t bgexec = nullptr;
 
@@ -293,15 +295,35 @@ scgr_status replan(scgr_ctx* c) {
   return SCGR_OK;
 }
 
-// For p = 1 the pair weight aX s_ij d^0 does not depend on the pose, so the
-// force kernel's per-split sums (sum w, sum w X') are the same in every
-// iteration: the first iteration of a run computes them and the others reuse
-// them (bit-identical results, O(M) work per later iteration).
+// Odd integer p needs no all-pairs pass per iteration.  For p = 1 the pair
+// weight aX s_ij d^0 does not depend on the pose, so the force kernel's
+// per-split sums (sum w, sum w X') are the same in every iteration: the first
+// iteration of a run computes them and the others reuse them (bit-identical).
+// For p = 3 the sums are a quadratic form in the template point over 14
+// pose-free moments of g (computed once per run; an exact re-association, so
+// equal to the direct pass up to rounding).
 scgr_status enqueue_iterations(scgr_ctx* c, int iters) {
   const int nb = combine_blocks(c->mpad);
   const StepParams sp = step_params(c);
   const bool pose_free = c->fp.pmode == 1 && c->reuse_pose_free;
+  const bool moments = c->fp.pmode == 3 && c->reuse_pose_free;
+  const int mloc = (int)(c->rows >= 0 ? c->rows : c->m);
+  if (moments && iters > 0) {
+    const int ntiles = (int)(c->npad / c->fp.tile_j);
+    const int S = moments_splits(ntiles, c->num_sms, c->mpad);
+    SCGR_CK(c, ensure(c->mpart, (size_t)S * c->mpad * 14 * sizeof(double)));
+    SCGR_CK(c, ensure(c->mom, (size_t)c->mpad * 14 * sizeof(double)));
+    SCGR_CK(c, launch_moments(c->L(), (const float4*)c->Xr.p, (const float2*)c->XA.p, ntiles, (const float4*)c->Y0r.p,
+                              (int)c->mpad, mloc, S, (double*)c->mpart.p, (double*)c->mom.p));
+  }
   for (int t = 0; t < iters; ++t) {
+    if (moments) {
+      SCGR_CK(c, launch_combine_moments(c->L(), (const double*)c->mom.p, mloc, (int)c->mpad, (const float4*)c->Y0r.p,
+                                        (const double*)c->aY64.p, c->prm.g_mode, c->pose, nullptr,
+                                        (double*)c->blockpart.p));
+      SCGR_CK(c, launch_finalize(c->L(), (const double*)c->blockpart.p, nb, c->pose, c->stats, sp, c->errword));
+      continue;
+    }
     if (!(pose_free && t > 0)) {
       scgr_status fs = force_launch(c);
       if (fs != SCGR_OK) return fs;
@@ -398,7 +420,7 @@ void scgr_destroy(scgr_ctx* c) {
                     &c->bXr, &c->bXA, &c->bY0r, &c->bpartial, &c->bblockpart, &c->bpairs, &c->bitems,
                     &c->bcpair, &c->btabX, &c->btabY, &c->bxoff, &c->byoff, &c->bstats, &c->bposes,
                     &c->gcell, &c->gcount, &c->gstart, &c->gcursor, &c->gblock, &c->gsorted, &c->gsidx, &c->gbb,
-                    &c->cd_key, &c->cd_moved, &c->wstore, &c->wupart, &c->wpartial};
+                    &c->cd_key, &c->cd_moved, &c->wstore, &c->wupart, &c->wpartial, &c->mpart, &c->mom};
   for (DevBuf* b : bufs) release(*b);
   if (c->pose) cudaFree(c->pose);
   if (c->pose_eval) cudaFree(c->pose_eval);
@@ -512,7 +534,8 @@ scgr_status scgr_run(scgr_ctx* c, int iters) {
     SCGR_CK(c, cudaGraphLaunch(c->gexec, c->cap_stream));
     SCGR_CK(c, cudaEventRecord(c->join_out, c->cap_stream));
     SCGR_CK(c, cudaStreamWaitEvent(c->stream, c->join_out, 0));
-    c->launches += (c->fp.pmode == 1 && c->reuse_pose_free) ? 2 * (int64_t)iters + 1 : 3 * (int64_t)iters;
+    const bool pf = c->fp.pmode == 1 && c->reuse_pose_free, mo = c->fp.pmode == 3 && c->reuse_pose_free;
+    c->launches += pf ? 2 * (int64_t)iters + 1 : (mo ? 2 * (int64_t)iters + 2 : 3 * (int64_t)iters);
   } else {
     scgr_status st = enqueue_iterations(c, iters);
     if (st != SCGR_OK) return st;
@@ -623,7 +646,7 @@ scgr_status scgr_potential_stored(scgr_ctx* c, const double pose7[7], double* U_
   const int n = (int)c->n, m = (int)c->m;
   const int nb = (n + 255) / 256;
   SCGR_CK(c, ensure(c->wstore, (size_t)n * m * sizeof(float)));
-  SCGR_CK(c, ensure(c->wupart, (size_t)nb * m * sizeof(double)));
+  SCGR_CK(c, ensure(c->wupart, (size_t)nb * ((m + 63) / 64) * sizeof(double)));
   SCGR_CK(c, ensure(c->wpartial, (size_t)c->mpad * sizeof(float4)));
   Launch L = c->L();
   double* d7 = c->aux + 48;
@@ -931,6 +954,11 @@ scgr_status scgr_set_tuning(scgr_ctx* c, int key, int value) {
     c->knn_grid_min = value;
     return SCGR_OK;
   }
+  if (key == SCGR_TUNE_BATCH_P) {
+    if (value != 1 && value != 2) return fail(c, SCGR_ERR_INVALID_ARG, "batch points per thread must be 1 or 2");
+    c->batch_P = value;
+    return SCGR_OK;
+  }
   if (key == SCGR_TUNE_BATCH_CHUNK_TILES) {
     if (value < 1 || value > 4096) return fail(c, SCGR_ERR_INVALID_ARG, "chunk tiles must be in [1, 4096]");
     c->batch_chunk_tiles = value;
@@ -958,7 +986,7 @@ scgr_status scgr_batch_run(scgr_ctx* c, int npairs, const int64_t* ref_off, cons
 
   // ---- host plan: per-pair geometry, work items (longest first), tables
   const int CT = c->batch_chunk_tiles;
-  const int FB = 128;  // template points per batched force block
+  const int FB = 128 * c->batch_P;  // template points per batched force block
   std::vector<BatchPair> pairs(npairs);
   std::vector<int4> items;
   std::vector<int> cpair;
@@ -1056,7 +1084,7 @@ scgr_status scgr_batch_run(scgr_ctx* c, int npairs, const int64_t* ref_off, cons
   const int pmode = (c->prm.p == 1.0) ? 1 : (c->prm.p == 2.0) ? 2 : (c->prm.p == 3.0) ? 3 : 0;
   auto enqueue = [&](Launch LL) -> scgr_status {
     for (int t = 0; t < iterations; ++t) {
-      SCGR_CK(c, launch_force_batch(LL, pmode, (int)items.size(), (const int4*)c->bitems.p, dpairs,
+      SCGR_CK(c, launch_force_batch(LL, pmode, c->batch_P, (int)items.size(), (const int4*)c->bitems.p, dpairs,
                                     (const float4*)c->bXr.p, (const float2*)c->bXA.p, (const float4*)c->bY0r.p,
                                     (const DevPose*)c->bposes.p, c->qexp, (float4*)c->bpartial.p, CT));
       SCGR_CK(c, launch_combine_batch(LL, cb, (const int*)c->bcpair.p, dpairs, (const float4*)c->bpartial.p,

@@ -222,7 +222,13 @@ cudaError_t launch_finalize(Launch L, const double* blockpart, int nblocks, DevP
 cudaError_t launch_apply(Launch L, const float4* Y4, int m, const DevPose* pose, float* out);
 cudaError_t launch_pose_refresh(Launch L, DevPose* pose, const DevStats* stats);
 
-cudaError_t launch_force_batch(Launch L, int pmode, int nitems, const int4* items, const BatchPair* pairs,
+int moments_splits(int ntiles, int num_sms, int64_t mpad);
+cudaError_t launch_moments(Launch L, const float4* Xr, const float2* XA, int ntiles, const float4* Y0r, int mpad,
+                           int m, int S, double* mpart, double* mom);
+cudaError_t launch_combine_moments(Launch L, const double* mom, int m, int mpad, const float4* Y0r,
+                                   const double* aY64, int g_mode, const DevPose* pose, float4* f4out,
+                                   double* blockpart);
+cudaError_t launch_force_batch(Launch L, int pmode, int P, int nitems, const int4* items, const BatchPair* pairs,
                                const float4* Xr, const float2* XA, const float4* Y0r, const DevPose* poses,
                                float qexp, float4* partial, int chunk_tiles);
 cudaError_t launch_combine_batch(Launch L, int nblocks, const int* cpair, const BatchPair* pairs,

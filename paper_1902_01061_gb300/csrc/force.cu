@@ -399,26 +399,172 @@ cudaError_t launch_force(Launch L, const ForcePlan& fp, const float4* Xr, const 
   return cudaGetLastError();
 }
 
-// Batched force pass: one block of 128 template points per item.
+// Batched force pass: one block of 128 threads (P template points each) per item.
 template <int PM>
-static void launch_force_batch_pm(cudaStream_t st, int nitems, const int4* items, const BatchPair* pairs,
+static void launch_force_batch_pm(cudaStream_t st, int P, int nitems, const int4* items, const BatchPair* pairs,
                                   const float4* Xr, const float2* XA, const float4* Y0r, const DevPose* poses,
                                   float qexp, float4* partial, int chunk_tiles) {
-  force_tile_kernel<1, PM, 128, FORCE_TJ, 2, true><<<nitems, 128, 0, st>>>(
-      reinterpret_cast<const float*>(Xr), reinterpret_cast<const float*>(XA), 0, chunk_tiles, Y0r, 0, poses, qexp,
-      partial, items, pairs);
+  if (P == 2)
+    force_tile_kernel<2, PM, 128, FORCE_TJ, 2, true><<<nitems, 128, 0, st>>>(
+        reinterpret_cast<const float*>(Xr), reinterpret_cast<const float*>(XA), 0, chunk_tiles, Y0r, 0, poses, qexp,
+        partial, items, pairs);
+  else
+    force_tile_kernel<1, PM, 128, FORCE_TJ, 2, true><<<nitems, 128, 0, st>>>(
+        reinterpret_cast<const float*>(Xr), reinterpret_cast<const float*>(XA), 0, chunk_tiles, Y0r, 0, poses, qexp,
+        partial, items, pairs);
 }
 
-cudaError_t launch_force_batch(Launch L, int pmode, int nitems, const int4* items, const BatchPair* pairs,
+cudaError_t launch_force_batch(Launch L, int pmode, int P, int nitems, const int4* items, const BatchPair* pairs,
                                const float4* Xr, const float2* XA, const float4* Y0r, const DevPose* poses,
                                float qexp, float4* partial, int chunk_tiles) {
   if (nitems <= 0) return cudaSuccess;
   switch (pmode) {
-    case 1: launch_force_batch_pm<1>(L.stream, nitems, items, pairs, Xr, XA, Y0r, poses, qexp, partial, chunk_tiles); break;
-    case 2: launch_force_batch_pm<2>(L.stream, nitems, items, pairs, Xr, XA, Y0r, poses, qexp, partial, chunk_tiles); break;
-    case 3: launch_force_batch_pm<3>(L.stream, nitems, items, pairs, Xr, XA, Y0r, poses, qexp, partial, chunk_tiles); break;
-    default: launch_force_batch_pm<0>(L.stream, nitems, items, pairs, Xr, XA, Y0r, poses, qexp, partial, chunk_tiles); break;
+    case 1: launch_force_batch_pm<1>(L.stream, P, nitems, items, pairs, Xr, XA, Y0r, poses, qexp, partial, chunk_tiles); break;
+    case 2: launch_force_batch_pm<2>(L.stream, P, nitems, items, pairs, Xr, XA, Y0r, poses, qexp, partial, chunk_tiles); break;
+    case 3: launch_force_batch_pm<3>(L.stream, P, nitems, items, pairs, Xr, XA, Y0r, poses, qexp, partial, chunk_tiles); break;
+    default: launch_force_batch_pm<0>(L.stream, P, nitems, items, pairs, Xr, XA, Y0r, poses, qexp, partial, chunk_tiles); break;
   }
+  if (L.counter) ++*L.counter;
+  return cudaGetLastError();
+}
+
+// ---- p = 3: moments of the pair weights over the reference ------------------
+// For p = 3, w_ij = g_ij d_ij^2 with g_ij = aX_j s_ij (or s_ij) independent of
+// the pose, and d^2 = |Y|^2 - 2 Y.X + |X|^2, so the per-point sums expand into
+// moments over j of g alone (X' in the frame centred on the reference mean):
+//   sum w   = |Y|^2 M0 - 2 Y.M1 + m2,
+//   sum w X = |Y|^2 M1 - 2 M2 Y + m3,
+// with M0 = sum g, M1 = sum g X', M2 = sum g X' X'^T, m2 = sum g |X'|^2,
+// m3 = sum g |X'|^2 X'.  One pass computes them (float32 per tile, float64
+// across tiles), after which an iteration is O(M).
+constexpr int MOM_TPB = 256;
+constexpr int NMOM = 14;  // M0, M1[3], M2[6] (xx xy xz yy yz zz), m2, m3[3]
+
+__global__ void __launch_bounds__(MOM_TPB)
+    moments_kernel(const float* __restrict__ Xr, const float* __restrict__ XA, int ntiles, int tiles_per_split,
+                   const float4* __restrict__ Y0r, int mpad, double* __restrict__ mpart) {
+  __shared__ float sT[6][FORCE_TJ];
+  const int i = blockIdx.x * MOM_TPB + threadIdx.x;
+  const int split = blockIdx.y;
+  const float ah = Y0r[i].w;
+  double acc[NMOM];
+#pragma unroll
+  for (int q = 0; q < NMOM; ++q) acc[q] = 0.0;
+  const int t0 = split * tiles_per_split;
+  const int t1 = min(ntiles, t0 + tiles_per_split);
+  for (int t = t0; t < t1; ++t) {
+    __syncthreads();
+    for (int u = threadIdx.x; u < 4 * FORCE_TJ; u += MOM_TPB) (&sT[0][0])[u] = Xr[(size_t)t * 4 * FORCE_TJ + u];
+    for (int u = threadIdx.x; u < 2 * FORCE_TJ; u += MOM_TPB) (&sT[4][0])[u] = XA[(size_t)t * 2 * FORCE_TJ + u];
+    __syncthreads();
+    float m[NMOM];
+#pragma unroll
+    for (int q = 0; q < NMOM; ++q) m[q] = 0.f;
+    for (int j = 0; j < FORCE_TJ; ++j) {
+      const float x = sT[0][j], y = sT[1][j], z = sT[2][j], nx = sT[3][j];
+      const float uu = sT[4][j] - ah;
+      const float g = exp2f(-fmaf(uu, uu, sT[5][j]));
+      const float gx = g * x, gy = g * y, gz = g * z, gn = g * nx;
+      m[0] += g;
+      m[1] += gx; m[2] += gy; m[3] += gz;
+      m[4] = fmaf(gx, x, m[4]); m[5] = fmaf(gx, y, m[5]); m[6] = fmaf(gx, z, m[6]);
+      m[7] = fmaf(gy, y, m[7]); m[8] = fmaf(gy, z, m[8]); m[9] = fmaf(gz, z, m[9]);
+      m[10] += gn;
+      m[11] = fmaf(gn, x, m[11]); m[12] = fmaf(gn, y, m[12]); m[13] = fmaf(gn, z, m[13]);
+    }
+#pragma unroll
+    for (int q = 0; q < NMOM; ++q) acc[q] += m[q];
+  }
+  double* out = mpart + ((size_t)split * mpad + i) * NMOM;
+#pragma unroll
+  for (int q = 0; q < NMOM; ++q) out[q] = acc[q];
+}
+
+// Per-point moments: the splits added in order.
+__global__ void moments_reduce_kernel(const double* __restrict__ mpart, int S, int mpad, int m,
+                                      double* __restrict__ mom) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  double acc[NMOM];
+  for (int q = 0; q < NMOM; ++q) acc[q] = 0.0;
+  for (int s = 0; s < S; ++s)
+    for (int q = 0; q < NMOM; ++q) acc[q] += mpart[((size_t)s * mpad + i) * NMOM + q];
+  for (int q = 0; q < NMOM; ++q) mom[(size_t)i * NMOM + q] = acc[q];
+}
+
+// The combine of an iteration from the moments (same per-block output as
+// combine_kernel).
+__global__ void __launch_bounds__(RED_THREADS)
+    combine_moments_kernel(const double* __restrict__ mom, int m, const float4* __restrict__ Y0r,
+                           const double* __restrict__ aY64, int g_mode, const DevPose* __restrict__ ps,
+                           float4* __restrict__ f4out, double* __restrict__ blockpart) {
+  __shared__ double sh[13][RED_THREADS];
+  const int i = blockIdx.x * RED_THREADS + threadIdx.x;
+  double v[13];
+#pragma unroll
+  for (int q = 0; q < 13; ++q) v[q] = 0.0;
+  if (i < m) {
+    const double* M = mom + (size_t)i * NMOM;
+    float A[9], b[3];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) A[q] = ps->A[q];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) b[q] = ps->b[q];
+    float yx, yy, yz;
+    template_point(Y0r[i], A, b, yx, yy, yz);
+    const double Y[3] = {yx, yy, yz};
+    const double ny = Y[0] * Y[0] + Y[1] * Y[1] + Y[2] * Y[2];
+    const double W = ny * M[0] - 2.0 * (Y[0] * M[1] + Y[1] * M[2] + Y[2] * M[3]) + M[10];
+    const double M2Y[3] = {M[4] * Y[0] + M[5] * Y[1] + M[6] * Y[2], M[5] * Y[0] + M[7] * Y[1] + M[8] * Y[2],
+                           M[6] * Y[0] + M[8] * Y[1] + M[9] * Y[2]};
+    const double S[3] = {ny * M[1] - 2.0 * M2Y[0] + M[11], ny * M[2] - 2.0 * M2Y[1] + M[12],
+                         ny * M[3] - 2.0 * M2Y[2] + M[13]};
+    const double ay = g_mode == 1 ? aY64[i] : 1.0;
+    const double f[3] = {ay * (S[0] - Y[0] * W), ay * (S[1] - Y[1] * W), ay * (S[2] - Y[2] * W)};
+    const double Wi = ay * W;
+    const double c[3] = {Y[0] - ps->ybs[0], Y[1] - ps->ybs[1], Y[2] - ps->ybs[2]};
+    v[0] = f[0];
+    v[1] = f[1];
+    v[2] = f[2];
+    v[3] = Wi;
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int bb = 0; bb < 3; ++bb) v[4 + 3 * a + bb] = f[a] * c[bb];
+    if (f4out) f4out[i] = make_float4((float)f[0], (float)f[1], (float)f[2], (float)Wi);
+  }
+  block_sum<13>(v, sh);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int q = 0; q < 13; ++q) blockpart[(size_t)blockIdx.x * 13 + q] = v[q];
+  }
+}
+
+int moments_splits(int ntiles, int num_sms, int64_t mpad) {
+  const int64_t blocks = (mpad + MOM_TPB - 1) / MOM_TPB;
+  int64_t S = (num_sms * 4 * 4 + blocks - 1) / blocks;
+  if (S > ntiles) S = ntiles;
+  if (S < 1) S = 1;
+  if (S > 32) S = 32;
+  return (int)S;
+}
+
+cudaError_t launch_moments(Launch L, const float4* Xr, const float2* XA, int ntiles, const float4* Y0r, int mpad,
+                           int m, int S, double* mpart, double* mom) {
+  const int tps = (ntiles + S - 1) / S;
+  const int splits = (ntiles + tps - 1) / tps;
+  moments_kernel<<<dim3((mpad + MOM_TPB - 1) / MOM_TPB, splits), MOM_TPB, 0, L.stream>>>(
+      reinterpret_cast<const float*>(Xr), reinterpret_cast<const float*>(XA), ntiles, tps, Y0r, mpad, mpart);
+  moments_reduce_kernel<<<(m + 255) / 256, 256, 0, L.stream>>>(mpart, splits, mpad, m, mom);
+  if (L.counter) *L.counter += 2;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_combine_moments(Launch L, const double* mom, int m, int mpad, const float4* Y0r,
+                                   const double* aY64, int g_mode, const DevPose* pose, float4* f4out,
+                                   double* blockpart) {
+  combine_moments_kernel<<<combine_blocks(mpad), RED_THREADS, 0, L.stream>>>(mom, m, Y0r, aY64, g_mode, pose, f4out,
+                                                                              blockpart);
   if (L.counter) ++*L.counter;
   return cudaGetLastError();
 }

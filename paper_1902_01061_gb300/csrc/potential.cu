@@ -262,40 +262,53 @@ cudaError_t launch_force_vjp(Launch L, const float4* Xr, const float2* XA, int n
 // force kernel accumulates, so the adjoint reduction is shared.
 constexpr int ST_TPB = 256;
 
+// Block (i-block of ST_ROWS template points, j-tile of ST_TPB reference
+// points): the tile's records are read once, each thread owns one j and
+// walks the block's template points, so every row segment is written as
+// ST_TPB consecutive floats.
+constexpr int ST_ROWS = 64;
+
 __global__ void __launch_bounds__(ST_TPB)
-    store_pairs_kernel(const float* __restrict__ Xr, const float* __restrict__ XA, int n,
+    store_pairs_kernel(const float* __restrict__ Xr, const float* __restrict__ XA, int n, int m,
                        const float4* __restrict__ Y0r, const double* __restrict__ aY64, int g_mode,
                        const DevPose* __restrict__ ps, float qexp, float* __restrict__ Wst,
                        double* __restrict__ Upart) {
   __shared__ double sh[1][RED_THREADS];
-  const int i = blockIdx.x;  // template point (grid.x: no 65535 limit)
   const int j = blockIdx.y * ST_TPB + threadIdx.x;
+  const int i0 = blockIdx.x * ST_ROWS;
   float A[9], b[3];
 #pragma unroll
   for (int q = 0; q < 9; ++q) A[q] = ps->A[q];
 #pragma unroll
   for (int q = 0; q < 3; ++q) b[q] = ps->b[q];
-  const float4 y0 = Y0r[i];
-  float yx, yy, yz;
-  tpoint(y0, A, b, yx, yy, yz);
-  double u[1] = {0.0};
+  float x = 0.f, y = 0.f, z = 0.f, ah = 0.f, nl = INFINITY;
   if (j < n) {
     const size_t t = (size_t)(j / FORCE_TJ), r = (size_t)(j % FORCE_TJ);
     const float* xr = Xr + t * 4 * FORCE_TJ + r;
     const float* xa = XA + t * 2 * FORCE_TJ + r;
-    const float rx = yx - xr[0], ry = yy - xr[FORCE_TJ], rz = yz - xr[2 * FORCE_TJ];
+    x = xr[0];
+    y = xr[FORCE_TJ];
+    z = xr[2 * FORCE_TJ];
+    ah = xa[0];
+    nl = xa[FORCE_TJ];
+  }
+  double u[1] = {0.0};
+  const int iend = min(m, i0 + ST_ROWS);
+  for (int i = i0; i < iend; ++i) {
+    const float4 y0 = Y0r[i];
+    float yx, yy, yz;
+    tpoint(y0, A, b, yx, yy, yz);
+    const float rx = yx - x, ry = yy - y, rz = yz - z;
     const float d2 = fmaf(rz, rz, fmaf(ry, ry, rx * rx));
-    const float uu = xa[0] - y0.w;
-    const float ep = fmaf(uu, uu, xa[FORCE_TJ]);
+    const float uu = ah - y0.w;
+    const float ep = fmaf(uu, uu, nl);
     const float w = d2 > 0.f ? exp2f(fmaf(qexp, log2f(d2), -ep)) : (qexp == 0.f ? exp2f(-ep) : 0.f);
-    Wst[(size_t)i * n + j] = w;
-    u[0] = (double)w * (double)d2;
+    if (j < n) Wst[(size_t)i * n + j] = w;
+    const double ay = g_mode == 1 ? aY64[i] : 1.0;
+    u[0] += ay * (double)w * (double)d2;
   }
   block_sum<1>(u, sh);
-  if (threadIdx.x == 0) {
-    const double ay = g_mode == 1 ? aY64[i] : 1.0;
-    Upart[(size_t)i * gridDim.y + blockIdx.y] = ay * u[0];
-  }
+  if (threadIdx.x == 0) Upart[(size_t)blockIdx.x * gridDim.y + blockIdx.y] = u[0];
 }
 
 __global__ void __launch_bounds__(ST_TPB)
@@ -331,10 +344,11 @@ cudaError_t launch_store_pairs(Launch L, const float2* XA, const float4* Xr, int
                                const double* aY64, int g_mode, int m, const DevPose* ps, float qexp, float* Wst,
                                double* Upart, double* Uout) {
   const int nb = (n + ST_TPB - 1) / ST_TPB;
-  store_pairs_kernel<<<dim3(m, nb), ST_TPB, 0, L.stream>>>(reinterpret_cast<const float*>(Xr),
-                                                          reinterpret_cast<const float*>(XA), n, Y0r, aY64, g_mode,
-                                                          ps, qexp, Wst, Upart);
-  sum_rows_kernel<<<1, RED_THREADS, 0, L.stream>>>(Upart, (int64_t)nb * m, Uout);
+  const int ib = (m + ST_ROWS - 1) / ST_ROWS;
+  store_pairs_kernel<<<dim3(ib, nb), ST_TPB, 0, L.stream>>>(reinterpret_cast<const float*>(Xr),
+                                                           reinterpret_cast<const float*>(XA), n, m, Y0r, aY64,
+                                                           g_mode, ps, qexp, Wst, Upart);
+  sum_rows_kernel<<<1, RED_THREADS, 0, L.stream>>>(Upart, (int64_t)nb * ib, Uout);
   if (L.counter) *L.counter += 2;
   return cudaGetLastError();
 }

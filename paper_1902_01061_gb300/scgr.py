@@ -40,6 +40,7 @@ SCGR_TUNE_FORCE_TPB = 4
 SCGR_TUNE_FORCE_SPLITS = 5
 SCGR_TUNE_REUSE_POSE_FREE = 6
 SCGR_TUNE_FORCE_OCC = 7
+SCGR_TUNE_BATCH_P = 8
 
 
 class scgr_params(Structure):

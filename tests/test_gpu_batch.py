@@ -92,6 +92,7 @@ def test_batch_chunk_tuning_keeps_results_close():
     ctx = scgr.scgr_create(scgr.scgr_default_params())
     try:
         scgr.scgr_set_tuning(ctx, scgr.SCGR_TUNE_BATCH_CHUNK_TILES, 3)
+        scgr.scgr_set_tuning(ctx, scgr.SCGR_TUNE_BATCH_P, 2)
         ro = np.cumsum([0] + [len(x) for x, _ in pairs])
         to = np.cumsum([0] + [len(y) for _, y in pairs])
         b = scgr.scgr_batch_run(ctx, ro, torch.from_numpy(np.concatenate([x for x, _ in pairs])).cuda(), to,

@@ -71,3 +71,28 @@ def test_p1_force_sums_reused_bit_identically(use_graph):
         nb = scgr.scgr_launch_count(g.ctx)
     assert list(a.R) == list(b.R) and list(a.t) == list(b.t) and a.s == b.s
     assert nb - na == 29
+
+
+def test_p3_moment_path_matches_all_pairs_and_oracle():
+    """p = 3: 14 pose-free moments once per run instead of an all-pairs pass
+    per iteration; equal to the all-pairs path (and the oracle) within the
+    pose tolerance."""
+    import oracle as O
+    from tests.gpu_helpers import rot_err_deg
+    case = synth.mild(n=1500)
+    iters = 25
+    with Gpu(case.X, case.Y0, p=3.0) as g:
+        a = g.run(iters)
+        na = scgr.scgr_launch_count(g.ctx)
+    with Gpu(case.X, case.Y0, p=3.0) as g:
+        scgr.scgr_set_tuning(g.ctx, scgr.SCGR_TUNE_REUSE_POSE_FREE, 0)
+        b = g.run(iters)
+        nb = scgr.scgr_launch_count(g.ctx)
+    o = O.register(case.X, case.Y0, O.Params(p=3.0), iterations=iters)
+    diag = synth.bbox_diag(case.X)
+    for r in (a, b):
+        R, t, s = r.as_numpy()
+        assert rot_err_deg(R, o["R"]) <= 0.5
+        assert np.linalg.norm(t - o["t"]) <= 1e-3 * diag
+        assert abs(s - o["s"]) <= 1e-5 * o["s"]
+    assert nb - na == iters - 2          # 2 moment launches replace 25 force launches
