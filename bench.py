@@ -50,6 +50,16 @@ WORKLOADS = {
 }
 
 
+def metric_name(workload):
+    return "pair-interactions/s at 1Mx1M" if workload == "large" else "pair-interactions/s"
+
+
+def base_config(workload, n, m):
+    wl = WORKLOADS[workload]
+    return {"workload": wl["desc"], "N": n, "M": m, "iterations": wl["iters"], "p": 2.0, "g_mode": 1, "k": 16,
+            "pairs_per_step": n * m * wl["iters"]}
+
+
 def make_pair(name):
     from paper_1902_01061_gb300 import synth
     if name == "large":
@@ -148,7 +158,7 @@ def profile_traffic():
 def measured_peaks(scgr, num_sms, sm_mhz):
     """Unit throughputs measured by the library's microbenchmark at the
     current clock: FP32 lane-FMAs and MUFU results per clock per SM."""
-    names = ["ffma", "ffma2_f32x2", "mufu_ex2", "mufu_sqrt", "mufu_lg2"]
+    names = ["ffma", "ffma2_f32x2", "mufu_ex2", "mufu_sqrt", "mufu_lg2", "mufu_rsqrt", "mufu_ex2_rsqrt_mixed"]
     out = {}
     for kind, name in enumerate(names):
         ops, ms = scgr.scgr_microbench(kind)
@@ -181,9 +191,73 @@ def cpu_baseline(pair, p, g_mode, seconds=15.0):
     t0 = time.perf_counter()
     O.forces_rows(Y, pair.X, aY, aX, sigma, p, g_mode, rows)
     dt = time.perf_counter() - t0
-    return {"value": nrows * n / dt, "unit": "pair-interactions/s", "cores": 1, "kind": "oracle",
-            "sample": f"iteration-0 force pass (Eq. 5) of {nrows} template rows x {n} reference points "
-                      f"in float64 numpy, single thread, {dt:.1f} s"}
+    value = nrows * n / dt
+    out = {"value": value, "unit": "pair-interactions/s", "cores": 1, "kind": "oracle",
+           "sample": f"iteration-0 force pass (Eq. 5) of {nrows} template rows x {n} reference points "
+                     f"in float64 numpy, single thread, {dt:.1f} s",
+           "cpu": _cpu_model(),
+           "extrapolated_s_per_iteration": n * m / value}
+    try:
+        allc = cpu_baseline_all_cores(pair, p, g_mode, dt / nrows)
+        allc["extrapolated_s_per_iteration"] = n * m / allc["value"]
+        out["all_cores"] = allc
+    except Exception as e:                       # the single-thread figure stands on its own
+        out["all_cores"] = {"unavailable": f"{type(e).__name__}: {e}"[:200]}
+    return out
+
+
+def _cpu_model():
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part", "hardware")):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+_POOL_DATA = {}
+
+
+def _pool_init(Y, X, aY, aX, sigma, p, g_mode):
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    _POOL_DATA.update(Y=Y, X=X, aY=aY, aX=aX, sigma=sigma, p=p, g_mode=g_mode)
+
+
+def _pool_rows(rows):
+    import oracle as O
+    d = _POOL_DATA
+    O.forces_rows(d["Y"], d["X"], d["aY"], d["aX"], d["sigma"], d["p"], d["g_mode"], rows)
+    return len(rows)
+
+
+def cpu_baseline_all_cores(pair, p, g_mode, per_row_s, seconds=10.0):
+    """The same oracle sample spread over every host core: a spawned process
+    pool (started fresh, so no CUDA state is inherited), one block of template
+    rows per process, each row summed as the oracle sums it."""
+    import multiprocessing as mp
+    import numpy as np
+    import oracle as O
+    cores = os.cpu_count() or 1
+    rng = np.random.default_rng(4321)
+    n, m = len(pair.X), len(pair.Y0)
+    aX = np.clip(rng.gamma(1.2, 0.015, size=n), 0, 0.33)
+    aY = np.clip(rng.gamma(1.2, 0.015, size=m), 0, 0.33)
+    sigma = O.sigma_auto(aX)
+    Y = pair.Y0.astype(np.float64)
+    per_core = int(max(2, seconds / max(per_row_s, 1e-9)))
+    rows = np.sort(rng.choice(m, size=min(m, per_core * cores), replace=False))
+    chunks = np.array_split(rows, cores)
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(cores, initializer=_pool_init, initargs=(Y, pair.X, aY, aX, sigma, p, g_mode)) as pool:
+        pool.map(_pool_rows, [c[:1] for c in chunks])          # workers up, oracle imported
+        t0 = time.perf_counter()
+        done = sum(pool.map(_pool_rows, chunks))
+        dt = time.perf_counter() - t0
+    return {"value": done * n / dt, "unit": "pair-interactions/s", "cores": cores, "kind": "oracle",
+            "sample": f"iteration-0 force pass of {done} template rows x {n} reference points, float64 numpy, "
+                      f"{cores} spawned processes over row blocks, {dt:.1f} s"}
 
 
 def bench_batch(args, scgr, torch, dev, steps, warmup):
@@ -223,6 +297,14 @@ def bench_batch(args, scgr, torch, dev, steps, warmup):
         times.append(time.perf_counter() - t0)
     batch_launches = (scgr.scgr_launch_count(ctx) - l0) // max(steps, 1)
     batch_s = sum(times) / len(times)
+    dtimes = []                          # descriptors alone: the same call with 0 iterations
+    for _ in range(max(steps, 1)):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        scgr.scgr_batch_run(ctx, ro, Xc, to, Yc, 0)
+        dtimes.append(time.perf_counter() - t0)
+    desc_s = sum(dtimes) / len(dtimes)
     scgr.scgr_destroy(ctx)
 
     # one call per pair, same method parameters, eager launches (capturing a
@@ -249,6 +331,8 @@ def bench_batch(args, scgr, torch, dev, steps, warmup):
                         "0-15% outliers, p=2, k=16, 100 iterations in one CUDA graph",
             "npairs": len(pairs), "points": int(ro[-1] + to[-1]), "pair_interactions_per_iteration": pair_work,
             "registrations_per_s": len(pairs) / batch_s, "ms_per_batch": batch_s * 1e3,
+            "descriptors_ms": desc_s * 1e3,
+            "registrations_per_s_without_descriptors": len(pairs) / max(batch_s - desc_s, 1e-9),
             "pair_interactions_per_s": pair_work * iters / batch_s,
             "launches_per_batch": int(batch_launches),
             "one_call_per_pair_registrations_per_s": len(pairs) / single_s,
@@ -277,7 +361,8 @@ def bench_diff(args, scgr, torch, dev, steps, warmup):
     the diagonal): the potential alone, potential + adjoint with tile
     recomputation, and potential + adjoint from stored pair terms."""
     from paper_1902_01061_gb300 import synth
-    case = synth.diff_case()
+    nd = getattr(args, "diff_n", 50_000)
+    case = synth.diff_case(n=nd)
     n, m = len(case.X), len(case.Y0)
     ctx = scgr.scgr_create(scgr.scgr_default_params(p=2.0), torch.cuda.current_stream())
     try:
@@ -291,10 +376,10 @@ def bench_diff(args, scgr, torch, dev, steps, warmup):
         stored = _timed(lambda: scgr.scgr_potential_stored(ctx, pose, grad_xyz_out=gx), steps, warmup, torch)
     finally:
         scgr.scgr_destroy(ctx)
-    return {"workload": "50,000 x 50,000 points, rotation 30 deg, noise 0.01 of the diagonal, p=2",
+    return {"workload": f"{n:,} x {m:,} points, rotation 30 deg, noise 0.01 of the diagonal, p=2",
             "potential_ms": fwd * 1e3, "potential_and_adjoint_recompute_ms": both * 1e3,
             "potential_and_adjoint_stored_ms": stored * 1e3,
-            "stored_pair_terms_bytes": n * m * 4,
+            "stored_pair_terms_bytes": m * ((n + 255) // 256 * 256) * 4,
             "adjoint_pair_interactions_per_s": 2 * n * m / both,
             "timing": "host wall clock around each synchronising call"}
 
@@ -349,10 +434,10 @@ def run_reference(args, ws, rank):
     mean = sum(times) / len(times)
     value = rows_per_step * n / mean
     line = {
-        "impl": "reference", "metric": "pair-interactions/s", "value": value, "unit": "pair-interactions/s",
+        "impl": "reference", "metric": metric_name(args.workload), "value": value, "unit": "pair-interactions/s",
         "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": mean * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": wl["desc"], "N": n, "M": m},
+        "data": "synthetic", "config": base_config(args.workload, n, m),
         "cpu_baseline": {"value": value, "unit": "pair-interactions/s", "cores": 1, "kind": "oracle",
                          "sample": f"each step: iteration-0 force pass of {rows_per_step} random template rows "
                                    f"x {n} reference points, float64 numpy, single thread"},
@@ -374,7 +459,10 @@ def main():
     ap.add_argument("--ref-rows", type=int, default=48)
     ap.add_argument("--no-batch", action="store_true", help="skip the batched, differentiation and 35k legs")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default tile shapes")
-    ap.add_argument("--plan", default=None, help="pin the force tile shape 'P,TPB[,OCC]' (no autotuning), e.g. 2,256,1")
+    ap.add_argument("--diff-only", action="store_true",
+                    help="run only the differentiation leg (potential, recomputing and stored adjoints) and print it")
+    ap.add_argument("--diff-n", type=int, default=50_000, help="points per cloud of the differentiation leg")
+    ap.add_argument("--plan", default=None, help="pin the force kernel 'P,TPB[,OCC[,RSQRT]]' (no autotuning), e.g. 2,256,0,1")
     args = ap.parse_args()
     ws, rank, local = dist_env()
     if args.impl == "reference":
@@ -391,6 +479,12 @@ def main():
     if ws > 1:
         dist.init_process_group("nccl")
     scgr.load()                      # fails loudly if the CUDA library is missing
+    if args.diff_only:
+        if rank == 0:
+            out = bench_diff(args, scgr, torch, torch.device("cuda", local), args.steps, args.warmup)
+            print(json.dumps({"leg": "differentiation", "steps": args.steps, "warmup": args.warmup, **out}),
+                  flush=True)
+        return 0
     wl = WORKLOADS[args.workload]
     pair = make_pair(args.workload)
     n, m, iters = len(pair.X), len(pair.Y0), wl["iters"]
@@ -409,10 +503,12 @@ def main():
     if args.plan:
         vals = [int(v) for v in args.plan.split(",")]
         P_, T_, O_ = vals[0], vals[1], (vals[2] if len(vals) > 2 else 0)
+        R_ = vals[3] if len(vals) > 3 else 0
         scgr.scgr_set_tuning(ctx, scgr.SCGR_TUNE_FORCE_P, P_)
         scgr.scgr_set_tuning(ctx, scgr.SCGR_TUNE_FORCE_TPB, T_)
         scgr.scgr_set_tuning(ctx, scgr.SCGR_TUNE_FORCE_OCC, O_)
-        tuned = {"P": P_, "tpb": T_, "occ": O_, "pinned": True}
+        scgr.scgr_set_tuning(ctx, scgr.SCGR_TUNE_FORCE_RSQRT, R_)
+        tuned = {"P": P_, "tpb": T_, "occ": O_, "rsqrt": R_, "pinned": True}
     elif not args.no_autotune:
         from paper_1902_01061_gb300 import autotune
         scgr.scgr_set_reference(ctx, Xd)
@@ -515,15 +611,14 @@ def main():
     if sm_mhz:
         roofline["frac_at_measured_clock"] = achieved_tflops / (peak_tflops * sm_mhz / sm_max_mhz)
     line = {
-        "metric": "pair-interactions/s at 1Mx1M" if args.workload == "large" else "pair-interactions/s",
+        "metric": metric_name(args.workload),
         "value": value, "unit": "pair-interactions/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "ms_per_iteration": ms_per_step / iters,
         "pct_fp32_peak": 100.0 * roofline["frac"],
-        "config": {"workload": wl["desc"], "N": n, "M": m, "iterations": iters, "p": 2.0, "g_mode": 1,
-                   "k": 16, "pairs_per_step": pairs_per_step, "autotuned": tuned, "l2": "flushed between steps (256 MB write)",
-                   "parallelism": f"replicas x{ws}"},
+        "config": dict(base_config(args.workload, n, m), autotuned=tuned, l2="flushed between steps (256 MB write)",
+                       parallelism=f"replicas x{ws}"),
         "gpu_launches": launches,
         "wall_s_timed_region": wall,
         "pose": {"s": res.s, "iterations": res.iterations},

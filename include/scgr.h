@@ -220,10 +220,12 @@ SCGR_EXPORT scgr_status scgr_potential(scgr_ctx* ctx, const double pose7[7], dou
                                        double* grad_pose7, float* grad_xyz_dev);
 
 /* Same outputs as scgr_potential, computed the other way round for
- * comparison: the forward pass stores every pair weight w_ij (float32,
- * M x N bytes x 4 of device memory, allocated on first use; OOM if it does
- * not fit) and the backward pass streams them back from HBM instead of
- * recomputing the tiles.  Synchronises. */
+ * comparison: the forward pass stores every pair weight w_ij (float32, M rows
+ * of N rounded up to a multiple of 256, so 4 x M x ceil(N/256) x 256 bytes of
+ * device memory, allocated on first use and kept by the context; OOM if it
+ * does not fit) and the backward pass streams them back from HBM instead of
+ * recomputing the tiles.  The weights use the special-function unit's ex2 and
+ * lg2 like the force kernel.  Synchronises. */
 SCGR_EXPORT scgr_status scgr_potential_stored(scgr_ctx* ctx, const double pose7[7], double* U_out,
                                               double* grad_pose7, float* grad_xyz_dev);
 
@@ -322,6 +324,11 @@ SCGR_EXPORT scgr_status scgr_step_apply(scgr_ctx* ctx, const double tot13[13]);
 #define SCGR_TUNE_BATCH_P 8           /* template points per thread in the batched force kernel: 1 (default), 2 */
 #define SCGR_TUNE_FORCE_OCC 7         /* 1: force kernel variant with a tighter register budget and more
                                          resident blocks per SM (3 at 256 threads, 4 at 128); 0 default */
+#define SCGR_TUNE_FORCE_RSQRT 9       /* p = 2 distance factor d = sqrt(d^2): 0 automatic (the square
+                                         root), 1 d^2 * rsqrt(d^2), 2 the square root; all-pairs and
+                                         batched force kernels; results agree to rounding.  On GB300
+                                         rsqrt costs the special-function unit as much as sqrt, so form 1
+                                         only adds a multiply; the autotuner times both */
 #define SCGR_TUNE_REUSE_POSE_FREE 6   /* 1 (default): odd integer p skips the per-iteration all-pairs pass.
                                          p = 1: the pair weights do not depend on the pose, so scgr_run
                                          computes the force sums once per call and reuses them
@@ -348,6 +355,11 @@ SCGR_EXPORT scgr_status scgr_get_plan(scgr_ctx* ctx, int out[5]);
  * time (ms) of three launches.  Synchronises the stream. */
 SCGR_EXPORT scgr_status scgr_microbench(int kind, int blocks, float* out_dev, void* cuda_stream,
                                         int64_t* lane_ops, double* ms);
+
+/* Test hook (host-side fault injection): the next `count` workspace
+ * allocations of any context fail as if the device were out of memory
+ * (SCGR_ERR_OOM), without asking the device.  0 switches it off. */
+SCGR_EXPORT scgr_status scgr_debug_fail_allocations(int count);
 
 /* Number of kernel launches this context has issued so far (diagnostic). */
 SCGR_EXPORT int64_t scgr_launch_count(const scgr_ctx* ctx);

@@ -82,25 +82,32 @@ def time_forces(ctx, m: int, reps: int = 3) -> float:
     return ms / max(n, 1)
 
 
-def _apply(ctx, P: int, tpb: int, occ: int) -> None:
+def _apply(ctx, P: int, tpb: int, occ: int, rsq: int = 0) -> None:
     scgr.scgr_set_tuning(ctx, scgr.SCGR_TUNE_FORCE_P, P)
     scgr.scgr_set_tuning(ctx, scgr.SCGR_TUNE_FORCE_TPB, tpb)
     scgr.scgr_set_tuning(ctx, scgr.SCGR_TUNE_FORCE_OCC, occ)
+    scgr.scgr_set_tuning(ctx, scgr.SCGR_TUNE_FORCE_RSQRT, rsq)
 
 
 def tune_single(ctx, n: int, m: int, p: float, candidates=None, reps: int = 3, store: bool = True) -> dict:
     """Time each (P, threads, occupancy variant) candidate on a context whose
-    descriptors are computed (splits stay automatic); leave the best in place
-    and return it."""
+    descriptors are computed (splits stay automatic); for p = 2 the two best
+    shapes are timed again with the rsqrt form of the distance factor.  Leave
+    the best in place and return it."""
     results = []
     for P, tpb, occ in candidates or SINGLE_CANDIDATES:
-        _apply(ctx, P, tpb, occ)
-        results.append((time_forces(ctx, m, reps), P, tpb, occ, scgr.scgr_get_plan(ctx)))
+        _apply(ctx, P, tpb, occ, 0)
+        results.append((time_forces(ctx, m, reps), P, tpb, occ, 0, scgr.scgr_get_plan(ctx)))
     results.sort(key=lambda r: r[0])
-    best_ms, P, tpb, occ, plan = results[0]
-    _apply(ctx, P, tpb, occ)
-    best = {"P": P, "tpb": tpb, "occ": occ, "ms": best_ms, "plan": plan,
-            "tried": [{"P": r[1], "tpb": r[2], "occ": r[3], "ms": r[0]} for r in results],
+    if float(p) == 2.0:
+        for r in results[:2]:
+            _apply(ctx, r[1], r[2], r[3], 1)
+            results.append((time_forces(ctx, m, reps), r[1], r[2], r[3], 1, scgr.scgr_get_plan(ctx)))
+        results.sort(key=lambda r: r[0])
+    best_ms, P, tpb, occ, rsq, plan = results[0]
+    _apply(ctx, P, tpb, occ, rsq)
+    best = {"P": P, "tpb": tpb, "occ": occ, "rsqrt": rsq, "ms": best_ms, "plan": plan,
+            "tried": [{"P": r[1], "tpb": r[2], "occ": r[3], "rsqrt": r[4], "ms": r[0]} for r in results],
             "when": time.strftime("%Y-%m-%d %H:%M:%S")}
     if store:
         _store(single_key(gpu_name(), n, m, p), best)
@@ -124,12 +131,25 @@ def tune_batch(ctx, ref_off, ref_xyz, tmp_off, tmp_xyz, p: float, iterations: in
             t0 = time.perf_counter()
             scgr.scgr_batch_run(ctx, ro, ref_xyz, to, tmp_xyz, iterations)
             results.append((time.perf_counter() - t0, ct, P))
+    results = [(t, c, q, 0) for t, c, q in results]
     results.sort()
-    best_s, ct, P = results[0]
+    if float(p) == 2.0:
+        _, ct, P, _ = results[0]
+        scgr.scgr_set_tuning(ctx, scgr.SCGR_TUNE_BATCH_P, P)
+        scgr.scgr_set_tuning(ctx, scgr.SCGR_TUNE_BATCH_CHUNK_TILES, ct)
+        scgr.scgr_set_tuning(ctx, scgr.SCGR_TUNE_FORCE_RSQRT, 1)
+        scgr.scgr_batch_run(ctx, ro, ref_xyz, to, tmp_xyz, 1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        scgr.scgr_batch_run(ctx, ro, ref_xyz, to, tmp_xyz, iterations)
+        results.append((time.perf_counter() - t0, ct, P, 1))
+        results.sort()
+    best_s, ct, P, rsq = results[0]
     scgr.scgr_set_tuning(ctx, scgr.SCGR_TUNE_BATCH_P, P)
     scgr.scgr_set_tuning(ctx, scgr.SCGR_TUNE_BATCH_CHUNK_TILES, ct)
-    best = {"chunk_tiles": ct, "P": P, "s": best_s, "iterations": iterations,
-            "tried": [{"chunk_tiles": c, "P": q, "s": t} for t, c, q in results],
+    scgr.scgr_set_tuning(ctx, scgr.SCGR_TUNE_FORCE_RSQRT, rsq)
+    best = {"chunk_tiles": ct, "P": P, "rsqrt": rsq, "s": best_s, "iterations": iterations,
+            "tried": [{"chunk_tiles": c, "P": q, "rsqrt": r, "s": t} for t, c, q, r in results],
             "when": time.strftime("%Y-%m-%d %H:%M:%S")}
     if store:
         _store(batch_key(gpu_name(), len(ro) - 1, work, p), best)
@@ -139,7 +159,7 @@ def tune_batch(ctx, ref_off, ref_xyz, tmp_off, tmp_xyz, p: float, iterations: in
 def apply_cached_single(ctx, n: int, m: int, p: float) -> dict | None:
     hit = _load().get(single_key(gpu_name(), n, m, p))
     if hit:
-        _apply(ctx, hit["P"], hit["tpb"], hit.get("occ", 0))
+        _apply(ctx, hit["P"], hit["tpb"], hit.get("occ", 0), hit.get("rsqrt", 0))
     return hit
 
 
@@ -148,4 +168,5 @@ def apply_cached_batch(ctx, npairs: int, work: int, p: float) -> dict | None:
     if hit:
         scgr.scgr_set_tuning(ctx, scgr.SCGR_TUNE_BATCH_CHUNK_TILES, hit["chunk_tiles"])
         scgr.scgr_set_tuning(ctx, scgr.SCGR_TUNE_BATCH_P, hit.get("P", 1))
+        scgr.scgr_set_tuning(ctx, scgr.SCGR_TUNE_FORCE_RSQRT, hit.get("rsqrt", 0))
     return hit

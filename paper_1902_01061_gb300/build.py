@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libscgr.so")
-SOURCES = ["api.cu", "descriptors.cu", "force.cu", "pose.cu", "forces_static.cu", "potential.cu", "knn_grid.cu", "microbench.cu"]
+SOURCES = ["api.cu", "api_diff.cu", "api_batch.cu", "api_extra.cu", "ctx.cu", "descriptors.cu", "force.cu", "pose.cu", "forces_static.cu", "potential.cu", "knn_grid.cu", "microbench.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "-I", INCLUDE, "-I", CSRC]

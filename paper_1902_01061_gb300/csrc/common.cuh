@@ -190,7 +190,7 @@ constexpr int FORCE_TJ = 256;
 struct ForcePlan {
   int P;          // template points per thread
   int tpb;        // threads per block
-  int pmode;      // 1: p == 1, 2: p == 2, 3: p == 3, 0: general p
+  int pmode;      // 1: p == 1, 2: p == 2, 3: p == 3, 0: general p, 4: p == 2 through rsqrt
   int tile_j;     // reference points per shared-memory tile
   int splits;     // reference-range splits (grid.y)
   int tiles_per_split;
@@ -204,6 +204,7 @@ struct ForceTuning {
   int tpb = 0;     // threads per block: 128 or 256
   int splits = 0;  // reference splits
   int occ = 0;     // 1: the higher-occupancy variant (tighter register budget)
+  int rsq = 0;     // p = 2 distance factor: 0 / 2 sqrt, 1 d^2 * rsqrt(d^2)
 };
 
 ForcePlan plan_force(int64_t m, int64_t npad, double p, int num_sms, const ForceTuning& tune = ForceTuning());
@@ -240,10 +241,14 @@ cudaError_t launch_pose_init_multi(Launch L, DevPose* poses, const DevStats* sta
 cudaError_t launch_force_vjp(Launch L, const float4* Xr, const float2* XA, int ntiles, const float4* Y0r,
                              const double* aY64, int g_mode, int m, const DevPose* ps, double p, const float* v,
                              float* grad);
-cudaError_t launch_store_pairs(Launch L, const float2* XA, const float4* Xr, int n, const float4* Y0r,
+// Stored pair terms: W is M rows of npad floats (npad = the padded reference
+// length of the records, a multiple of 256).
+cudaError_t launch_store_pairs(Launch L, const float2* XA, const float4* Xr, int npad, const float4* Y0r,
                                const double* aY64, int g_mode, int m, const DevPose* ps, float qexp, float* Wst,
                                double* Upart, double* Uout);
-cudaError_t launch_stored_rows(Launch L, const float* Wst, int n, int m, const float4* Xr, float4* partial);
+cudaError_t launch_stored_rows(Launch L, const float* Wst, int npad, int m, const float4* Xr, float4* partial);
+int store_pairs_columns(int npad);   // grid columns of the store pass
+int store_pairs_row_blocks(int m);   // grid rows of the store pass
 cudaError_t launch_pose_from7(Launch L, const double* pose7_dev, DevPose* ps, const DevStats* st);
 cudaError_t launch_adjoint_combine(Launch L, const float4* partial, int S, int mpad, int m, const float4* Y0r,
                                    const double* aY64, int g_mode, const DevPose* ps, float* grad_xyz,

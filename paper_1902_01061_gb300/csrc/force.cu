@@ -74,6 +74,11 @@ __device__ __forceinline__ float lg2_approx(float x) {
   asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
   return y;
 }
+__device__ __forceinline__ float rsqrt_approx(float x) {
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
 __device__ __forceinline__ float sqrt_approx(float x) {
   float y;
   asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
@@ -95,6 +100,8 @@ __device__ __forceinline__ void kahan_add(float& s, float& c, float x) {
   c = (t - s) - y;
   s = t;
 }
+
+constexpr float RSQRT_CAP = 1e18f;
 
 // One packed pair update: reference points (j, j+1) against one template point.
 template <int PM>
@@ -120,6 +127,17 @@ __device__ __forceinline__ void pair2(u64 xv, u64 yv, u64 zv, u64 nv, u64 av, u6
     float e0, e1;
     upk2(ep, e0, e1);
     w = mul2(pk2(ex2_neg(e0), ex2_neg(e1)), d2);
+  } else if (PM == 4) {
+    // p = 2 with d = d^2 / sqrt(|d^2|): a reciprocal square root and one more
+    // packed multiply (kept as a tunable alternative: on GB300 rsqrt and sqrt
+    // occupy the special-function unit equally, so this form is slower).
+    // The cap keeps d^2 = 0 at weight 0 (0 * inf would be NaN); a d^2 below
+    // the rounding of its own terms may come out with either sign.
+    float e0, e1, q0, q1;
+    upk2(ep, e0, e1);
+    upk2(d2, q0, q1);
+    const u64 r = pk2(fminf(rsqrt_approx(fabsf(q0)), RSQRT_CAP), fminf(rsqrt_approx(fabsf(q1)), RSQRT_CAP));
+    w = mul2(mul2(pk2(ex2_neg(e0), ex2_neg(e1)), d2), r);
   } else {
     float q0, q1;
     upk2(d2, q0, q1);
@@ -259,7 +277,7 @@ static int force_blocks_per_sm(const ForcePlan& fp);
 // (else the best fill seen).
 ForcePlan plan_force(int64_t m, int64_t npad, double p, int num_sms, const ForceTuning& tune) {
   ForcePlan fp;
-  fp.pmode = (p == 1.0) ? 1 : (p == 2.0) ? 2 : (p == 3.0) ? 3 : 0;
+  fp.pmode = (p == 1.0) ? 1 : (p == 2.0) ? (tune.rsq == 1 ? 4 : 2) : (p == 3.0) ? 3 : 0;
   fp.tile_j = FORCE_TJ;
   fp.tpb = 256;
   if (m >= (int64_t)num_sms * 2 * 256 * 4) fp.P = 4;
@@ -382,6 +400,7 @@ static int force_blocks_per_sm(const ForcePlan& fp) {
     case 1: return blocks_per_sm_pm<1>(fp);
     case 2: return blocks_per_sm_pm<2>(fp);
     case 3: return blocks_per_sm_pm<3>(fp);
+    case 4: return blocks_per_sm_pm<4>(fp);
     default: return blocks_per_sm_pm<0>(fp);
   }
 }
@@ -393,6 +412,7 @@ cudaError_t launch_force(Launch L, const ForcePlan& fp, const float4* Xr, const 
     case 1: launch_force_pm<1>(L.stream, fp, Xr, XA, ntiles, Y0r, mpad, pose, qexp, partial); break;
     case 2: launch_force_pm<2>(L.stream, fp, Xr, XA, ntiles, Y0r, mpad, pose, qexp, partial); break;
     case 3: launch_force_pm<3>(L.stream, fp, Xr, XA, ntiles, Y0r, mpad, pose, qexp, partial); break;
+    case 4: launch_force_pm<4>(L.stream, fp, Xr, XA, ntiles, Y0r, mpad, pose, qexp, partial); break;
     default: launch_force_pm<0>(L.stream, fp, Xr, XA, ntiles, Y0r, mpad, pose, qexp, partial); break;
   }
   if (L.counter) ++*L.counter;
@@ -422,6 +442,7 @@ cudaError_t launch_force_batch(Launch L, int pmode, int P, int nitems, const int
     case 1: launch_force_batch_pm<1>(L.stream, P, nitems, items, pairs, Xr, XA, Y0r, poses, qexp, partial, chunk_tiles); break;
     case 2: launch_force_batch_pm<2>(L.stream, P, nitems, items, pairs, Xr, XA, Y0r, poses, qexp, partial, chunk_tiles); break;
     case 3: launch_force_batch_pm<3>(L.stream, P, nitems, items, pairs, Xr, XA, Y0r, poses, qexp, partial, chunk_tiles); break;
+    case 4: launch_force_batch_pm<4>(L.stream, P, nitems, items, pairs, Xr, XA, Y0r, poses, qexp, partial, chunk_tiles); break;
     default: launch_force_batch_pm<0>(L.stream, P, nitems, items, pairs, Xr, XA, Y0r, poses, qexp, partial, chunk_tiles); break;
   }
   if (L.counter) ++*L.counter;

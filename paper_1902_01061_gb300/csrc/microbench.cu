@@ -1,6 +1,6 @@
 // Throughput microbenchmarks of the units the force kernel is bound by: the
 // FP32 FMA pipe (scalar FFMA and packed fma.f32x2) and the special-function
-// unit (ex2, sqrt, lg2).  Each thread runs 8 independent dependency chains so
+// unit (ex2, sqrt, lg2, rsqrt, and ex2 mixed with rsqrt).  Each thread runs 8 independent dependency chains so
 // that latency is hidden; the grid fills every SM.  The results give the
 // measured denominators of the force kernel's roofline.
 #include <cuda_runtime.h>
@@ -49,9 +49,21 @@ __global__ void __launch_bounds__(MB_TPB) microbench_kernel(float* __restrict__ 
         float r;
         asm volatile("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x[c]));
         x[c] = r;
-      } else {
+      } else if (KIND == 4) {
         float r;
         asm volatile("lg2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x[c]));
+        x[c] = r;
+      } else if (KIND == 5) {
+        float r;
+        asm volatile("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x[c]));
+        x[c] = r;
+      } else {
+        // ex2 on even chains, rsqrt on odd ones: whether the two share one unit
+        float r;
+        if (c % 2 == 0)
+          asm volatile("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(-x[c]));
+        else
+          asm volatile("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x[c]));
         x[c] = r;
       }
     }
@@ -64,13 +76,14 @@ __global__ void __launch_bounds__(MB_TPB) microbench_kernel(float* __restrict__ 
 
 }  // namespace
 
-// kind: 0 FFMA, 1 packed fma.f32x2, 2 MUFU ex2, 3 MUFU sqrt, 4 MUFU lg2.
+// kind: 0 FFMA, 1 packed fma.f32x2, 2 MUFU ex2, 3 MUFU sqrt, 4 MUFU lg2, 5 MUFU rsqrt,
+// 6 ex2 and rsqrt interleaved.
 // lane_ops: FP32 lane operations (an f32x2 FMA counts 2) or MUFU results;
 // ms: device time of one launch on `out_dev` (blocks x 256 floats of scratch
 // supplied by the caller, blocks = 8 x SM count).
 extern "C" scgr_status scgr_microbench(int kind, int blocks, float* out_dev, void* cuda_stream,
                                        int64_t* lane_ops, double* ms) {
-  if (!out_dev || !lane_ops || !ms || blocks < 1 || kind < 0 || kind > 4) return SCGR_ERR_INVALID_ARG;
+  if (!out_dev || !lane_ops || !ms || blocks < 1 || kind < 0 || kind > 6) return SCGR_ERR_INVALID_ARG;
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess) return SCGR_ERR_CUDA;
@@ -86,7 +99,9 @@ extern "C" scgr_status scgr_microbench(int kind, int blocks, float* out_dev, voi
       case 1: microbench_kernel<1><<<blocks, MB_TPB, 0, st>>>(out_dev, 0.999f, 1e-3f); break;
       case 2: microbench_kernel<2><<<blocks, MB_TPB, 0, st>>>(out_dev, 0.5f, 0.f); break;
       case 3: microbench_kernel<3><<<blocks, MB_TPB, 0, st>>>(out_dev, 1.5f, 0.f); break;
-      default: microbench_kernel<4><<<blocks, MB_TPB, 0, st>>>(out_dev, 1.5f, 0.f); break;
+      case 4: microbench_kernel<4><<<blocks, MB_TPB, 0, st>>>(out_dev, 1.5f, 0.f); break;
+      case 5: microbench_kernel<5><<<blocks, MB_TPB, 0, st>>>(out_dev, 1.5f, 0.f); break;
+      default: microbench_kernel<6><<<blocks, MB_TPB, 0, st>>>(out_dev, 1.5f, 0.f); break;
     }
     cudaEventRecord(e1, st);
     if (cudaEventSynchronize(e1) != cudaSuccess) {

@@ -255,80 +255,153 @@ cudaError_t launch_force_vjp(Launch L, const float4* Xr, const float2* XA, int n
 }
 
 // ---- stored pair terms (comparison variant of the adjoint) -----------------
-// Forward: every pair weight w_ij = g d^(p-1) is written to W[i][n] (float32,
-// M x N, coalesced along j) and the potential U = sum aY w d^2 / (p + 1) is
-// summed per block.  Backward: one block per template point streams its row
-// back from HBM and forms the same per-point sums (sum w, sum w X') that the
-// force kernel accumulates, so the adjoint reduction is shared.
+// Forward: every pair weight w_ij = g d^(p-1) is written to W[i][npad]
+// (float32, M rows of the padded reference length; padding records carry
+// weight 0) and the potential U = sum aY w d^2 / (p + 1) is summed per block.
+// Backward: a block streams ST_RROWS rows back from HBM and forms the same
+// per-point sums (sum w, sum w X') that the force kernel accumulates, so the
+// adjoint reduction is shared.  Both passes move 16 bytes per thread access:
+// a thread owns four consecutive reference points.
 constexpr int ST_TPB = 256;
+constexpr int ST_JB = 4 * ST_TPB;  // reference points per block column (npad is a multiple of it or of 256)
 
-// Block (i-block of ST_ROWS template points, j-tile of ST_TPB reference
-// points): the tile's records are read once, each thread owns one j and
-// walks the block's template points, so every row segment is written as
-// ST_TPB consecutive floats.
+// Block (ST_ROWS template points x ST_JB reference points): the records are
+// read once, each thread walks the block's template points and writes each
+// row segment as one float4.
 constexpr int ST_ROWS = 64;
 
+__device__ __forceinline__ float st_ex2(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float st_lg2(float x) {
+  float y;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// w = 2^-(u^2 - L) d^(p-1) with d^(p-1) = 2^(qexp log2 d^2), qexp = (p-1)/2.
+__device__ __forceinline__ float st_weight(float d2, float ep, float qexp) {
+  if (qexp == 0.f) return st_ex2(-ep);
+  return st_ex2(fmaf(qexp, st_lg2(d2), -ep));  // d2 = 0: lg2 = -inf, weight 0
+}
+
 __global__ void __launch_bounds__(ST_TPB)
-    store_pairs_kernel(const float* __restrict__ Xr, const float* __restrict__ XA, int n, int m,
+    store_pairs_kernel(const float* __restrict__ Xr, const float* __restrict__ XA, int npad, int m,
                        const float4* __restrict__ Y0r, const double* __restrict__ aY64, int g_mode,
                        const DevPose* __restrict__ ps, float qexp, float* __restrict__ Wst,
                        double* __restrict__ Upart) {
   __shared__ double sh[1][RED_THREADS];
-  const int j = blockIdx.y * ST_TPB + threadIdx.x;
+  const int j0 = blockIdx.y * ST_JB + threadIdx.x * 4;
   const int i0 = blockIdx.x * ST_ROWS;
   float A[9], b[3];
 #pragma unroll
   for (int q = 0; q < 9; ++q) A[q] = ps->A[q];
 #pragma unroll
   for (int q = 0; q < 3; ++q) b[q] = ps->b[q];
-  float x = 0.f, y = 0.f, z = 0.f, ah = 0.f, nl = INFINITY;
-  if (j < n) {
-    const size_t t = (size_t)(j / FORCE_TJ), r = (size_t)(j % FORCE_TJ);
+  float4 x4 = make_float4(0.f, 0.f, 0.f, 0.f), y4 = x4, z4 = x4, a4 = x4;
+  float4 l4 = make_float4(INFINITY, INFINITY, INFINITY, INFINITY);
+  const bool live = j0 < npad;
+  if (live) {
+    const size_t t = (size_t)(j0 / FORCE_TJ), r = (size_t)(j0 % FORCE_TJ);
     const float* xr = Xr + t * 4 * FORCE_TJ + r;
     const float* xa = XA + t * 2 * FORCE_TJ + r;
-    x = xr[0];
-    y = xr[FORCE_TJ];
-    z = xr[2 * FORCE_TJ];
-    ah = xa[0];
-    nl = xa[FORCE_TJ];
+    x4 = *reinterpret_cast<const float4*>(xr);
+    y4 = *reinterpret_cast<const float4*>(xr + FORCE_TJ);
+    z4 = *reinterpret_cast<const float4*>(xr + 2 * FORCE_TJ);
+    a4 = *reinterpret_cast<const float4*>(xa);
+    l4 = *reinterpret_cast<const float4*>(xa + FORCE_TJ);
   }
+  const float xs[4] = {x4.x, x4.y, x4.z, x4.w}, ys[4] = {y4.x, y4.y, y4.z, y4.w};
+  const float zs[4] = {z4.x, z4.y, z4.z, z4.w}, as[4] = {a4.x, a4.y, a4.z, a4.w};
+  const float ls[4] = {l4.x, l4.y, l4.z, l4.w};
+  // U terms are summed in FP32 over runs of 16 rows and the runs in FP64
+  // (FP64 arithmetic per pair would cost more than the pair itself).
   double u[1] = {0.0};
   const int iend = min(m, i0 + ST_ROWS);
-  for (int i = i0; i < iend; ++i) {
-    const float4 y0 = Y0r[i];
-    float yx, yy, yz;
-    tpoint(y0, A, b, yx, yy, yz);
-    const float rx = yx - x, ry = yy - y, rz = yz - z;
-    const float d2 = fmaf(rz, rz, fmaf(ry, ry, rx * rx));
-    const float uu = ah - y0.w;
-    const float ep = fmaf(uu, uu, nl);
-    const float w = d2 > 0.f ? exp2f(fmaf(qexp, log2f(d2), -ep)) : (qexp == 0.f ? exp2f(-ep) : 0.f);
-    if (j < n) Wst[(size_t)i * n + j] = w;
-    const double ay = g_mode == 1 ? aY64[i] : 1.0;
-    u[0] += ay * (double)w * (double)d2;
+  for (int ib = i0; ib < iend; ib += 16) {
+    float run = 0.f;
+    const int ie = min(iend, ib + 16);
+    for (int i = ib; i < ie; ++i) {
+      const float4 y0 = Y0r[i];
+      float yx, yy, yz;
+      tpoint(y0, A, b, yx, yy, yz);
+      const float ay = g_mode == 1 ? (float)aY64[i] : 1.f;
+      float w[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const float rx = yx - xs[k], ry = yy - ys[k], rz = yz - zs[k];
+        const float d2 = fmaf(rz, rz, fmaf(ry, ry, rx * rx));
+        const float uu = as[k] - y0.w;
+        w[k] = st_weight(d2, fmaf(uu, uu, ls[k]), qexp);
+        run = fmaf(ay * w[k], d2, run);
+      }
+      if (live) *reinterpret_cast<float4*>(Wst + (size_t)i * npad + j0) = make_float4(w[0], w[1], w[2], w[3]);
+    }
+    u[0] += (double)run;
   }
   block_sum<1>(u, sh);
   if (threadIdx.x == 0) Upart[(size_t)blockIdx.x * gridDim.y + blockIdx.y] = u[0];
 }
 
-__global__ void __launch_bounds__(ST_TPB)
-    stored_rows_kernel(const float* __restrict__ Wst, int n, const float* __restrict__ Xr,
+// Backward from the stored weights: a block owns ST_RROWS template rows and
+// each thread four consecutive reference points per step, so every weight is
+// read once as part of a float4 (all ST_RROWS loads of a step are issued
+// before they are used) and each reference record once per block.  The last
+// block re-reads row m-1 for its missing rows and discards those sums.
+constexpr int ST_RROWS = 8;
+
+__global__ void __launch_bounds__(ST_TPB, 2)
+    stored_rows_kernel(const float* __restrict__ Wst, int npad, int m, const float* __restrict__ Xr,
                        float4* __restrict__ partial) {
-  __shared__ double sh[4][RED_THREADS];
-  const int i = blockIdx.x;
-  double v[4] = {0, 0, 0, 0};
-  const float* row = Wst + (size_t)i * n;
-  for (int j = threadIdx.x; j < n; j += ST_TPB) {
-    const double w = row[j];
-    const size_t t = (size_t)(j / FORCE_TJ), r = (size_t)(j % FORCE_TJ);
-    const float* xr = Xr + t * 4 * FORCE_TJ + r;
-    v[0] += w;
-    v[1] += w * xr[0];
-    v[2] += w * xr[FORCE_TJ];
-    v[3] += w * xr[2 * FORCE_TJ];
+  __shared__ double red[ST_TPB / 32][ST_RROWS * 4];
+  const int r0 = blockIdx.x * ST_RROWS;
+  const int nr = min(ST_RROWS, m - r0);
+  const float* rows[ST_RROWS];
+#pragma unroll
+  for (int r = 0; r < ST_RROWS; ++r) rows[r] = Wst + (size_t)min(r0 + r, m - 1) * npad;
+  float acc[ST_RROWS][4];
+#pragma unroll
+  for (int r = 0; r < ST_RROWS; ++r) acc[r][0] = acc[r][1] = acc[r][2] = acc[r][3] = 0.f;
+  for (int j0 = threadIdx.x * 4; j0 < npad; j0 += ST_JB) {
+    float4 w4[ST_RROWS];
+#pragma unroll
+    for (int r = 0; r < ST_RROWS; ++r) w4[r] = *reinterpret_cast<const float4*>(rows[r] + j0);
+    const size_t t = (size_t)(j0 / FORCE_TJ), q = (size_t)(j0 % FORCE_TJ);
+    const float* xr = Xr + t * 4 * FORCE_TJ + q;
+    const float4 x = *reinterpret_cast<const float4*>(xr);
+    const float4 y = *reinterpret_cast<const float4*>(xr + FORCE_TJ);
+    const float4 z = *reinterpret_cast<const float4*>(xr + 2 * FORCE_TJ);
+#pragma unroll
+    for (int r = 0; r < ST_RROWS; ++r) {
+      const float4 w = w4[r];
+      acc[r][0] += (w.x + w.y) + (w.z + w.w);
+      acc[r][1] = fmaf(w.w, x.w, fmaf(w.z, x.z, fmaf(w.y, x.y, fmaf(w.x, x.x, acc[r][1]))));
+      acc[r][2] = fmaf(w.w, y.w, fmaf(w.z, y.z, fmaf(w.y, y.y, fmaf(w.x, y.x, acc[r][2]))));
+      acc[r][3] = fmaf(w.w, z.w, fmaf(w.z, z.z, fmaf(w.y, z.y, fmaf(w.x, z.x, acc[r][3]))));
+    }
   }
-  block_sum<4>(v, sh);
-  if (threadIdx.x == 0) partial[i] = make_float4((float)v[0], (float)v[1], (float)v[2], (float)v[3]);
+  // block reduction: FP32 warp shuffles, then the warps' sums in FP64
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int r = 0; r < ST_RROWS; ++r)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      float v = acc[r][c];
+      for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+      if (lane == 0) red[warp][r * 4 + c] = v;
+    }
+  __syncthreads();
+  if (threadIdx.x < ST_RROWS * 4) {
+    double v = 0.0;
+    for (int w = 0; w < ST_TPB / 32; ++w) v += red[w][threadIdx.x];
+    red[0][threadIdx.x] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < nr)
+    partial[r0 + threadIdx.x] = make_float4((float)red[0][threadIdx.x * 4], (float)red[0][threadIdx.x * 4 + 1],
+                                            (float)red[0][threadIdx.x * 4 + 2], (float)red[0][threadIdx.x * 4 + 3]);
 }
 
 __global__ void __launch_bounds__(RED_THREADS) sum_rows_kernel(const double* __restrict__ part, int64_t count,
@@ -340,21 +413,25 @@ __global__ void __launch_bounds__(RED_THREADS) sum_rows_kernel(const double* __r
   if (threadIdx.x == 0) out[0] = v[0];
 }
 
-cudaError_t launch_store_pairs(Launch L, const float2* XA, const float4* Xr, int n, const float4* Y0r,
+cudaError_t launch_store_pairs(Launch L, const float2* XA, const float4* Xr, int npad, const float4* Y0r,
                                const double* aY64, int g_mode, int m, const DevPose* ps, float qexp, float* Wst,
                                double* Upart, double* Uout) {
-  const int nb = (n + ST_TPB - 1) / ST_TPB;
+  const int nb = store_pairs_columns(npad);
   const int ib = (m + ST_ROWS - 1) / ST_ROWS;
   store_pairs_kernel<<<dim3(ib, nb), ST_TPB, 0, L.stream>>>(reinterpret_cast<const float*>(Xr),
-                                                           reinterpret_cast<const float*>(XA), n, m, Y0r, aY64,
+                                                           reinterpret_cast<const float*>(XA), npad, m, Y0r, aY64,
                                                            g_mode, ps, qexp, Wst, Upart);
   sum_rows_kernel<<<1, RED_THREADS, 0, L.stream>>>(Upart, (int64_t)nb * ib, Uout);
   if (L.counter) *L.counter += 2;
   return cudaGetLastError();
 }
 
-cudaError_t launch_stored_rows(Launch L, const float* Wst, int n, int m, const float4* Xr, float4* partial) {
-  stored_rows_kernel<<<m, ST_TPB, 0, L.stream>>>(Wst, n, reinterpret_cast<const float*>(Xr), partial);
+int store_pairs_columns(int npad) { return (npad + ST_JB - 1) / ST_JB; }
+int store_pairs_row_blocks(int m) { return (m + ST_ROWS - 1) / ST_ROWS; }
+
+cudaError_t launch_stored_rows(Launch L, const float* Wst, int npad, int m, const float4* Xr, float4* partial) {
+  stored_rows_kernel<<<(m + ST_RROWS - 1) / ST_RROWS, ST_TPB, 0, L.stream>>>(Wst, npad, m,
+                                                                            reinterpret_cast<const float*>(Xr), partial);
   if (L.counter) ++*L.counter;
   return cudaGetLastError();
 }

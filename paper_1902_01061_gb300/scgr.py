@@ -31,7 +31,7 @@ EXPORTED = (
     "scgr_set_curvature", "scgr_set_force_timing", "scgr_get_force_timing", "scgr_forces_static",
     "scgr_potential", "scgr_batch_run", "scgr_set_tuning", "scgr_set_row_range", "scgr_step_partials",
     "scgr_step_apply", "scgr_get_plan", "scgr_microbench", "scgr_set_neighbourhood", "scgr_nearest",
-    "scgr_change_mask", "scgr_force_vjp", "scgr_potential_stored",
+    "scgr_change_mask", "scgr_force_vjp", "scgr_potential_stored", "scgr_debug_fail_allocations",
 )
 SCGR_TUNE_BATCH_CHUNK_TILES = 1
 SCGR_TUNE_KNN_GRID_MIN = 2
@@ -41,6 +41,7 @@ SCGR_TUNE_FORCE_SPLITS = 5
 SCGR_TUNE_REUSE_POSE_FREE = 6
 SCGR_TUNE_FORCE_OCC = 7
 SCGR_TUNE_BATCH_P = 8
+SCGR_TUNE_FORCE_RSQRT = 9
 
 
 class scgr_params(Structure):
@@ -113,6 +114,7 @@ def load():
         "scgr_get_plan": (S, [ctx, POINTER(c_int)]),
         "scgr_set_neighbourhood": (S, [ctx, c_int, c_double, c_double]),
         "scgr_force_vjp": (S, [ctx, c_void_p, c_void_p]),
+        "scgr_debug_fail_allocations": (S, [c_int]),
         "scgr_potential_stored": (S, [ctx, POINTER(c_double), POINTER(c_double), POINTER(c_double), c_void_p]),
         "scgr_nearest": (S, [ctx, c_void_p, c_int64, c_void_p, c_void_p]),
         "scgr_change_mask": (S, [ctx, c_double, c_void_p, c_void_p]),
@@ -330,7 +332,8 @@ def scgr_step_apply(ctx, totals) -> None:
 
 def scgr_microbench(kind: int, stream=None):
     """(lane_ops, ms) of one throughput-microbenchmark launch filling the GPU:
-    kind 0 FFMA, 1 fma.f32x2, 2 ex2, 3 sqrt, 4 lg2."""
+    kind 0 FFMA, 1 fma.f32x2, 2 ex2, 3 sqrt, 4 lg2, 5 rsqrt, 6 ex2 and rsqrt
+    interleaved."""
     import torch
     blocks = 8 * torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
     out = torch.empty(blocks * 256, dtype=torch.float32, device="cuda")
@@ -353,6 +356,10 @@ def scgr_get_plan(ctx) -> dict:
 
 def scgr_set_tuning(ctx, key: int, value: int) -> None:
     _check(load().scgr_set_tuning(ctx, int(key), int(value)), ctx)
+
+
+def scgr_debug_fail_allocations(count: int) -> None:
+    _check(load().scgr_debug_fail_allocations(int(count)))
 
 
 def scgr_force_vjp(ctx, v, grad_out) -> None:

@@ -68,6 +68,15 @@ def test_batch_matches_single_pair_runs(p):
         assert close(r, single, synth.bbox_diag(X)), (r.as_numpy(), single.as_numpy())
 
 
+def test_one_pair_batch_matches_single_run():
+    pairs = make_pairs([1800], seed=21)
+    res, _ = run_batch(pairs, 20, p=2.0)
+    X, Y = pairs[0]
+    with Gpu(X, Y, p=2.0) as g:
+        single = g.run(20)
+    assert len(res) == 1 and close(res[0], single, synth.bbox_diag(X))
+
+
 def test_batch_matches_oracle_on_small_pairs():
     pairs = make_pairs([300, 140, 420], seed=9)
     iters = 20
@@ -88,11 +97,12 @@ def test_batch_graph_replay_equals_eager():
 
 def test_batch_chunk_tuning_keeps_results_close():
     pairs = make_pairs([3000, 700], seed=17)
-    a, _ = run_batch(pairs, 10)
-    ctx = scgr.scgr_create(scgr.scgr_default_params())
+    a, _ = run_batch(pairs, 10, p=2.0)
+    ctx = scgr.scgr_create(scgr.scgr_default_params(p=2.0))
     try:
         scgr.scgr_set_tuning(ctx, scgr.SCGR_TUNE_BATCH_CHUNK_TILES, 3)
         scgr.scgr_set_tuning(ctx, scgr.SCGR_TUNE_BATCH_P, 2)
+        scgr.scgr_set_tuning(ctx, scgr.SCGR_TUNE_FORCE_RSQRT, 1)       # p = 2 through rsqrt
         ro = np.cumsum([0] + [len(x) for x, _ in pairs])
         to = np.cumsum([0] + [len(y) for _, y in pairs])
         b = scgr.scgr_batch_run(ctx, ro, torch.from_numpy(np.concatenate([x for x, _ in pairs])).cuda(), to,

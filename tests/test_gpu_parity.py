@@ -290,3 +290,24 @@ def test_errors_are_reported_not_raised_on_device():
         assert scgr.scgr_get_result(ctx).iterations == 3
     finally:
         scgr.scgr_destroy(ctx)
+
+
+def test_injected_allocation_failure_is_reported_and_recoverable():
+    """Host-side fault injection: workspace allocations fail as if out of
+    memory; the call reports SCGR_ERR_OOM and the context stays usable."""
+    case = synth.mild(n=400)
+    ctx = scgr.scgr_create(scgr.scgr_default_params())
+    try:
+        scgr.scgr_set_reference(ctx, torch.from_numpy(case.X).cuda())
+        scgr.scgr_set_template(ctx, torch.from_numpy(case.Y0).cuda())
+        scgr.scgr_debug_fail_allocations(1)
+        with pytest.raises(scgr.ScgrError) as e:
+            scgr.scgr_compute_descriptors(ctx)
+        assert e.value.status == 4                     # SCGR_ERR_OOM
+        assert "memory" in scgr.scgr_last_error(ctx)
+        scgr.scgr_compute_descriptors(ctx)             # the hook is spent: works again
+        scgr.scgr_run(ctx, 3)
+        assert scgr.scgr_get_result(ctx).iterations == 3
+    finally:
+        scgr.scgr_debug_fail_allocations(0)
+        scgr.scgr_destroy(ctx)

@@ -41,6 +41,30 @@ def test_every_tile_shape_matches_oracle(P, tpb, splits, occ):
     assert rel_l2(f4[:, 3], W_ref) <= 1e-5
 
 
+@pytest.mark.parametrize("P,tpb", [(1, 128), (2, 256), (4, 256)])
+def test_rsqrt_distance_form_matches_oracle(P, tpb):
+    """p = 2 with d = d^2 rsqrt(d^2): same parity bar.  The template holds
+    exact copies of reference points (d^2 = 0 pairs), which must give weight
+    0, not NaN."""
+    sc = synth.scale_case()
+    X = sc.X[synth.subsample(sc.X, 2600, 63)]
+    Y0 = np.concatenate([sc.Y0[synth.subsample(sc.Y0, 1500, 64)], X[:300]])
+    d = O.descriptors(X, Y0, O.Params(p=2.0))
+    f_ref, W_ref = O.forces(Y0, X, d["aY"], d["aX"], d["sigma"], 2.0, 1)
+    with Gpu(X, Y0, p=2.0) as g:
+        scgr.scgr_set_tuning(g.ctx, scgr.SCGR_TUNE_FORCE_P, P)
+        scgr.scgr_set_tuning(g.ctx, scgr.SCGR_TUNE_FORCE_TPB, tpb)
+        scgr.scgr_set_tuning(g.ctx, scgr.SCGR_TUNE_FORCE_RSQRT, 1)
+        f_rs = g.forces()
+        scgr.scgr_set_tuning(g.ctx, scgr.SCGR_TUNE_FORCE_RSQRT, 2)
+        f_sq = g.forces()
+        with pytest.raises(scgr.ScgrError):
+            scgr.scgr_set_tuning(g.ctx, scgr.SCGR_TUNE_FORCE_RSQRT, 3)
+    assert np.isfinite(f_rs).all()
+    assert rel_l2(f_rs[:, :3], f_ref) <= 1e-5 and rel_l2(f_rs[:, 3], W_ref) <= 1e-5
+    assert rel_l2(f_rs, f_sq) <= 1e-5
+
+
 def test_autotuner_picks_and_caches(tmp_path, monkeypatch):
     monkeypatch.setenv("SCGR_TUNE_CACHE", str(tmp_path / "tune.json"))
     case = synth.mild(n=3000)
@@ -49,7 +73,7 @@ def test_autotuner_picks_and_caches(tmp_path, monkeypatch):
                                     candidates=[(1, 128, 0), (2, 256, 1)], reps=2)
         plan = scgr.scgr_get_plan(g.ctx)
         assert (plan["P"], plan["tpb"]) == (best["P"], best["tpb"])
-        assert len(best["tried"]) == 2 and best["ms"] > 0
+        assert len(best["tried"]) == 4 and best["ms"] > 0          # two shapes, then both again in rsqrt form
     with Gpu(case.X, case.Y0, p=2.0) as g:
         hit = autotune.apply_cached_single(g.ctx, len(case.X), len(case.Y0), 2.0)
         assert hit is not None and hit["P"] == best["P"]
