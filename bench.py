@@ -158,7 +158,8 @@ def profile_traffic():
 def measured_peaks(scgr, num_sms, sm_mhz):
     """Unit throughputs measured by the library's microbenchmark at the
     current clock: FP32 lane-FMAs and MUFU results per clock per SM."""
-    names = ["ffma", "ffma2_f32x2", "mufu_ex2", "mufu_sqrt", "mufu_lg2", "mufu_rsqrt", "mufu_ex2_rsqrt_mixed"]
+    names = ["ffma", "ffma2_f32x2", "mufu_ex2", "mufu_sqrt", "mufu_lg2", "mufu_rsqrt", "mufu_ex2_rsqrt_mixed",
+             "mix_6ffma2_ex2_sqrt"]
     out = {}
     for kind, name in enumerate(names):
         ops, ms = scgr.scgr_microbench(kind)
@@ -267,18 +268,23 @@ def bench_batch(args, scgr, torch, dev, steps, warmup):
     import numpy as np
     from paper_1902_01061_gb300 import synth
     pairs = synth.batch_case()
-    iters = 100
+    iters = getattr(args, "batch_iters", 100)
     ro = np.cumsum([0] + [len(pp.X) for pp in pairs]).astype(np.int64)
     to = np.cumsum([0] + [len(pp.Y0) for pp in pairs]).astype(np.int64)
     Xc = torch.from_numpy(np.concatenate([pp.X for pp in pairs])).to(dev)
     Yc = torch.from_numpy(np.concatenate([pp.Y0 for pp in pairs])).to(dev)
     pair_work = int(sum(len(pp.X) * len(pp.Y0) for pp in pairs))
-    params = scgr.scgr_default_params(p=2.0, g_mode=1, k=16, use_graph=1)
+    params = scgr.scgr_default_params(p=2.0, g_mode=1, k=16, use_graph=0 if getattr(args, "batch_eager", False) else 1)
     stream = torch.cuda.current_stream()
     ctx = scgr.scgr_create(params, stream)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     tuned = None
-    if not args.no_autotune:
+    if getattr(args, "batch_plan", None):
+        bP, bC = [int(v) for v in args.batch_plan.split(",")]
+        scgr.scgr_set_tuning(ctx, scgr.SCGR_TUNE_BATCH_P, bP)
+        scgr.scgr_set_tuning(ctx, scgr.SCGR_TUNE_BATCH_CHUNK_TILES, bC)
+        tuned = {"P": bP, "chunk_tiles": bC, "pinned": True}
+    elif not args.no_autotune:
         from paper_1902_01061_gb300 import autotune
         tuned = autotune.tune_batch(ctx, ro, Xc, to, Yc, 2.0, iterations=3)
 
@@ -307,6 +313,20 @@ def bench_batch(args, scgr, torch, dev, steps, warmup):
     desc_s = sum(dtimes) / len(dtimes)
     scgr.scgr_destroy(ctx)
 
+    out = {"workload": "512 pairs, 500-20,000 points log-uniform, rotation <= 90 deg, scale 0.7-1.4, "
+                       f"0-15% outliers, p=2, k=16, {iters} iterations "
+                       + ("with eager launches" if getattr(args, "batch_eager", False) else "in one CUDA graph"),
+           "npairs": len(pairs), "points": int(ro[-1] + to[-1]), "pair_interactions_per_iteration": pair_work,
+           "registrations_per_s": len(pairs) / batch_s, "ms_per_batch": batch_s * 1e3,
+           "descriptors_ms": desc_s * 1e3,
+           "registrations_per_s_without_descriptors": len(pairs) / max(batch_s - desc_s, 1e-9),
+           "pair_interactions_per_s": pair_work * iters / batch_s,
+           "launches_per_batch": int(batch_launches),
+           "autotuned": tuned,
+           "timing": "host wall clock around each synchronising call, L2 flushed before each"}
+    if getattr(args, "batch_only", False):
+        return out
+
     # one call per pair, same method parameters, eager launches (capturing a
     # graph per pair costs more than it saves at 100 iterations)
     ctx1 = scgr.scgr_create(scgr.scgr_default_params(p=2.0, g_mode=1, k=16), stream)
@@ -327,20 +347,11 @@ def bench_batch(args, scgr, torch, dev, steps, warmup):
     per_pair()
     single_s = time.perf_counter() - t0
     scgr.scgr_destroy(ctx1)
-    return {"workload": "512 pairs, 500-20,000 points log-uniform, rotation <= 90 deg, scale 0.7-1.4, "
-                        "0-15% outliers, p=2, k=16, 100 iterations in one CUDA graph",
-            "npairs": len(pairs), "points": int(ro[-1] + to[-1]), "pair_interactions_per_iteration": pair_work,
-            "registrations_per_s": len(pairs) / batch_s, "ms_per_batch": batch_s * 1e3,
-            "descriptors_ms": desc_s * 1e3,
-            "registrations_per_s_without_descriptors": len(pairs) / max(batch_s - desc_s, 1e-9),
-            "pair_interactions_per_s": pair_work * iters / batch_s,
-            "launches_per_batch": int(batch_launches),
-            "one_call_per_pair_registrations_per_s": len(pairs) / single_s,
-            "speedup_vs_one_call_per_pair": single_s / batch_s,
-            "autotuned": tuned,
-            "one_call_per_pair": "scgr_set_reference/template + compute_descriptors + run(100) + get_result "
-                                 "per pair, eager launches",
-            "timing": "host wall clock around each synchronising call, L2 flushed before each"}
+    out.update({"one_call_per_pair_registrations_per_s": len(pairs) / single_s,
+                "speedup_vs_one_call_per_pair": single_s / batch_s,
+                "one_call_per_pair": "scgr_set_reference/template + compute_descriptors + run(100) + get_result "
+                                     "per pair, eager launches"})
+    return out
 
 
 def _timed(fn, steps, warmup, torch):
@@ -462,6 +473,11 @@ def main():
     ap.add_argument("--diff-only", action="store_true",
                     help="run only the differentiation leg (potential, recomputing and stored adjoints) and print it")
     ap.add_argument("--diff-n", type=int, default=50_000, help="points per cloud of the differentiation leg")
+    ap.add_argument("--batch-only", action="store_true",
+                    help="run only the batched leg (no one-call-per-pair comparison) and print it")
+    ap.add_argument("--batch-iters", type=int, default=100, help="iterations of the batched leg")
+    ap.add_argument("--batch-plan", default=None, help="pin the batched force kernel 'P,CHUNK_TILES' (no autotuning)")
+    ap.add_argument("--batch-eager", action="store_true", help="batched leg without the CUDA graph (for profilers)")
     ap.add_argument("--plan", default=None, help="pin the force kernel 'P,TPB[,OCC[,RSQRT]]' (no autotuning), e.g. 2,256,0,1")
     args = ap.parse_args()
     ws, rank, local = dist_env()
@@ -479,6 +495,11 @@ def main():
     if ws > 1:
         dist.init_process_group("nccl")
     scgr.load()                      # fails loudly if the CUDA library is missing
+    if args.batch_only:
+        if rank == 0:
+            out = bench_batch(args, scgr, torch, torch.device("cuda", local), args.steps, args.warmup)
+            print(json.dumps({"leg": "batch", "steps": args.steps, "warmup": args.warmup, **out}), flush=True)
+        return 0
     if args.diff_only:
         if rank == 0:
             out = bench_diff(args, scgr, torch, torch.device("cuda", local), args.steps, args.warmup)

@@ -71,6 +71,10 @@ scgr_status scgr_batch_run(scgr_ctx* c, int npairs, const int64_t* ref_off, cons
     for (int64_t q0 = 0; q0 < bp.m; q0 += 128) tabY.push_back(make_int2(p, (int)q0));
   }
   std::stable_sort(items.begin(), items.end(), [](const int4& a, const int4& b) { return a.w > b.w; });
+  // kNN blocks scan their whole cloud: biggest clouds first, so the small
+  // ones fill the last wave
+  std::stable_sort(tabX.begin(), tabX.end(), [&](const int2& a, const int2& b) { return pairs[a.x].n > pairs[b.x].n; });
+  std::stable_sort(tabY.begin(), tabY.end(), [&](const int2& a, const int2& b) { return pairs[a.x].m > pairs[b.x].m; });
   std::vector<int64_t> xoff(ref_off, ref_off + npairs + 1), yoff(tmp_off, tmp_off + npairs + 1);
 
   // ---- device buffers

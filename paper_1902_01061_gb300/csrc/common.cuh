@@ -86,6 +86,39 @@ __device__ __forceinline__ void block_sum(double (&v)[NV], double (*sh)[RED_THRE
   for (int q = 0; q < NV; ++q) v[q] = sh[q][0];
 }
 
+// Packed FP32 pairs (Blackwell add/sub/mul/fma .f32x2): each instruction
+// works on two float32 lanes with the same per-lane IEEE rounding as the
+// scalar .rn instruction (no contraction, subnormals kept).
+typedef unsigned long long u64;  // two packed float32 lanes (low, high)
+
+__device__ __forceinline__ u64 pk2(float lo, float hi) {
+  u64 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ void upk2(u64 v, float& lo, float& hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ u64 add2(u64 a, u64 b) {
+  u64 d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ u64 sub2(u64 a, u64 b) {
+  u64 d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ u64 mul2(u64 a, u64 b) {
+  u64 d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ u64 fma2(u64 a, u64 b, u64 c) {
+  u64 d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
 // Symmetric 3x3 eigenvalues by cyclic Jacobi rotations (float64), ascending.
 __host__ __device__ inline void sym3_eigenvalues(const double* Ain, double* lam) {
   double a[3][3];
@@ -120,6 +153,43 @@ __host__ __device__ inline void sym3_eigenvalues(const double* Ain, double* lam)
   if (l1 > l2) { tmp = l1; l1 = l2; l2 = tmp; }
   if (l0 > l1) { tmp = l0; l0 = l1; l1 = tmp; }
   lam[0] = l0; lam[1] = l1; lam[2] = l2;
+}
+
+// Smallest eigenvalue of a symmetric positive semi-definite 3x3 C (row-major)
+// as the smallest root of its characteristic polynomial
+//   f(l) = det(C - l I) = p0 - p1 l + p2 l^2 - l^3
+// by Newton's method from l = 0.  On [0, l_min] f is positive, decreasing and
+// convex, so the iterates rise monotonically to l_min with no overshoot
+// (quadratically for a simple root).  A few FP64 steps replace the sweeps of
+// Jacobi rotations, each with square roots and divisions.  Where the root is
+// (nearly) multiple, Newton slows down and f near the root is lost in
+// rounding, so after 12 steps, or when f reaches its rounding level without
+// a quadratic last step, the Jacobi solver takes over.
+// Returns 0 when C is singular to rounding (f(0) <= 0 or p1 = 0).
+__host__ __device__ inline double sym3_min_eigenvalue(const double* C) {
+  const double c00 = C[0], c11 = C[4], c22 = C[8];
+  const double c01 = 0.5 * (C[1] + C[3]), c02 = 0.5 * (C[2] + C[6]), c12 = 0.5 * (C[5] + C[7]);
+  const double p2 = c00 + c11 + c22;
+  const double m00 = c11 * c22 - c12 * c12, m11 = c00 * c22 - c02 * c02, m22 = c00 * c11 - c01 * c01;
+  const double p1 = m00 + m11 + m22;
+  const double p0 = c00 * m00 - c01 * (c01 * c22 - c12 * c02) + c02 * (c01 * c12 - c11 * c02);
+  if (!(p0 > 0.0) || !(p1 > 0.0)) return 0.0;
+  double l = 0.0, last = p2;
+  for (int it = 0; it < 12; ++it) {
+    const double f = p0 + l * (-p1 + l * (p2 - l));
+    const double df = -p1 + l * (2.0 * p2 - 3.0 * l);
+    if (!(f > 0.0) || !(df < 0.0)) {  // f is at its rounding level
+      if (last <= 1e-9 * p2) return l;  // after a quadratic step: l is the root
+      break;                            // slow (multiple root): rounding limits l
+    }
+    const double step = -f / df;
+    l += step;
+    if (step <= 1e-17 * p2) return l;
+    last = step;
+  }
+  double lam[3];
+  sym3_eigenvalues(C, lam);
+  return lam[0];
 }
 
 // One registration pair of a batch: where its points, padded records,

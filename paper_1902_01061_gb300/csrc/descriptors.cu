@@ -46,57 +46,134 @@ cudaError_t launch_pack(Launch L, const float* xyz, int64_t n, float4* out, int*
 constexpr int KNN_TPB = 128;
 constexpr int KNN_TILE = 1024;
 
-// Scan candidates P[base .. base + n) in index order for one query q held by
-// this thread; tile staging is shared by the block (all threads of the block
-// must call this with the same base and n).  Indices written are global.
+// Insert (key, idx) into the sorted list kd/ki of KC entries if it beats the
+// KC-th key; a key equal to an entry stays behind it (candidates arrive in
+// increasing index order, so ties keep the lower index first).
 template <int KC>
-__device__ __forceinline__ void knn_scan(const float4* __restrict__ P, int64_t base, int n, float4 q, float* kd,
-                                         int* ki, float4* tile) {
+__device__ __forceinline__ void knn_insert(float key, int idx, float* kd, int* ki) {
+  if (key < kd[KC - 1]) {
+    kd[KC - 1] = key;
+    ki[KC - 1] = idx;
 #pragma unroll
-  for (int m = 0; m < KC; ++m) {
-    kd[m] = INFINITY;
-    ki[m] = INT_MAX;
-  }
-  for (int t0 = 0; t0 < n; t0 += KNN_TILE) {
-    const int cnt = min(KNN_TILE, n - t0);
-    __syncthreads();
-    for (int t = threadIdx.x; t < cnt; t += KNN_TPB) tile[t] = P[base + t0 + t];
-    __syncthreads();
-#pragma unroll 4
-    for (int jj = 0; jj < cnt; ++jj) {
-      const float4 c = tile[jj];
-      const float dx = __fsub_rn(q.x, c.x);
-      const float dy = __fsub_rn(q.y, c.y);
-      const float dz = __fsub_rn(q.z, c.z);
-      const float key = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
-      if (key < kd[KC - 1]) {
-        kd[KC - 1] = key;
-        ki[KC - 1] = (int)(base + t0 + jj);
-#pragma unroll
-        for (int m = KC - 1; m > 0; --m) {
-          if (kd[m] < kd[m - 1]) {
-            const float tk = kd[m];
-            kd[m] = kd[m - 1];
-            kd[m - 1] = tk;
-            const int ti = ki[m];
-            ki[m] = ki[m - 1];
-            ki[m - 1] = ti;
-          }
-        }
+    for (int m = KC - 1; m > 0; --m) {
+      if (kd[m] < kd[m - 1]) {
+        const float tk = kd[m];
+        kd[m] = kd[m - 1];
+        kd[m - 1] = tk;
+        const int ti = ki[m];
+        ki[m] = ki[m - 1];
+        ki[m - 1] = ti;
       }
     }
   }
 }
 
+__device__ __forceinline__ float knn_key(float4 q, float4 c) {
+  const float dx = __fsub_rn(q.x, c.x);
+  const float dy = __fsub_rn(q.y, c.y);
+  const float dz = __fsub_rn(q.z, c.z);
+  return __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+}
+
+// Candidates that beat the KC-th key wait in a short per-thread queue; the
+// warp merges all queues into the sorted lists together once any queue could
+// overflow.  Inserting at once costs a 16-step pass for the whole warp
+// whenever a single lane improves; queueing lets the lanes share that cost.
+// The merge applies the exact test against the live list in candidate
+// order, so the result is the same as inserting at once.  Four candidates
+// are keyed per step with packed .f32x2 arithmetic (the same per-operation
+// rounding as the scalar key), and the warp skips the queue code unless one
+// of its lanes has a hit among them.
+constexpr int KNN_QL = 8;  // queue capacity
+constexpr int KNN_U = 4;   // candidates per step (KNN_TILE is a multiple)
+
+__device__ __forceinline__ u64 knn_key2(u64 qx, u64 qy, u64 qz, u64 cx, u64 cy, u64 cz) {
+  const u64 dx = sub2(qx, cx), dy = sub2(qy, cy), dz = sub2(qz, cz);
+  return add2(add2(mul2(dx, dx), mul2(dy, dy)), mul2(dz, dz));
+}
+
+// Scan candidates P[base .. base + n) in index order for one query q held by
+// this thread; tile staging is shared by the block (all threads of the block
+// must call this with the same base and n, so the warp votes are uniform).
+// The tile is stored as three coordinate arrays.  Indices written are global.
 template <int KC>
-__global__ void __launch_bounds__(KNN_TPB) knn_brute_kernel(const float4* __restrict__ P, int n,
+__device__ __forceinline__ void knn_scan(const float4* __restrict__ P, int64_t base, int n, float4 q, float* kd,
+                                         int* ki, float* tile, float* qks, int* qis) {
+  float* tx = tile;
+  float* ty = tile + KNN_TILE;
+  float* tz = tile + 2 * KNN_TILE;
+#pragma unroll
+  for (int m = 0; m < KC; ++m) {
+    kd[m] = INFINITY;
+    ki[m] = INT_MAX;
+  }
+  // this thread's queue: slot s at [s * KNN_TPB + threadIdx.x] (conflict-free)
+  float* qk = qks + threadIdx.x;
+  int* qi = qis + threadIdx.x;
+  int qn = 0;
+  float thr = INFINITY;
+  const u64 qx = pk2(q.x, q.x), qy = pk2(q.y, q.y), qz = pk2(q.z, q.z);
+  for (int t0 = 0; t0 < n; t0 += KNN_TILE) {
+    const int cnt = min(KNN_TILE, n - t0);
+    __syncthreads();
+    for (int t = threadIdx.x; t < cnt; t += KNN_TPB) {
+      const float4 c = P[base + t0 + t];
+      tx[t] = c.x;
+      ty[t] = c.y;
+      tz[t] = c.z;
+    }
+    __syncthreads();
+    const int idx0 = (int)(base + t0);
+    int jj = 0;
+    if (KC == 1) {
+      for (; jj < cnt; ++jj) knn_insert<KC>(knn_key(q, make_float4(tx[jj], ty[jj], tz[jj], 0.f)), idx0 + jj, kd, ki);
+      continue;
+    }
+    for (; jj + KNN_U <= cnt; jj += KNN_U) {
+      const ulonglong2 X = *reinterpret_cast<const ulonglong2*>(tx + jj);
+      const ulonglong2 Y = *reinterpret_cast<const ulonglong2*>(ty + jj);
+      const ulonglong2 Z = *reinterpret_cast<const ulonglong2*>(tz + jj);
+      float key[KNN_U];
+      upk2(knn_key2(qx, qy, qz, X.x, Y.x, Z.x), key[0], key[1]);
+      upk2(knn_key2(qx, qy, qz, X.y, Y.y, Z.y), key[2], key[3]);
+      const bool hit = (key[0] < thr) | (key[1] < thr) | (key[2] < thr) | (key[3] < thr);
+      if (__any_sync(0xffffffffu, hit)) {
+#pragma unroll
+        for (int u = 0; u < KNN_U; ++u) {
+          if (key[u] < thr) {
+            qk[qn * KNN_TPB] = key[u];
+            qi[qn * KNN_TPB] = idx0 + jj + u;
+            ++qn;
+          }
+        }
+        if (__any_sync(0xffffffffu, qn > KNN_QL - KNN_U)) {
+          for (int sl = 0; sl < qn; ++sl) knn_insert<KC>(qk[sl * KNN_TPB], qi[sl * KNN_TPB], kd, ki);
+          qn = 0;
+          thr = kd[KC - 1];
+        }
+      }
+    }
+    if (jj < cnt) {  // ragged end of the last tile: empty the queue, then insert directly
+      for (int sl = 0; sl < qn; ++sl) knn_insert<KC>(qk[sl * KNN_TPB], qi[sl * KNN_TPB], kd, ki);
+      qn = 0;
+      for (; jj < cnt; ++jj) knn_insert<KC>(knn_key(q, make_float4(tx[jj], ty[jj], tz[jj], 0.f)), idx0 + jj, kd, ki);
+      thr = kd[KC - 1];
+    }
+  }
+  for (int sl = 0; sl < qn; ++sl) knn_insert<KC>(qk[sl * KNN_TPB], qi[sl * KNN_TPB], kd, ki);
+}
+
+template <int KC>
+__global__ void __launch_bounds__(KNN_TPB, KC > 16 ? 2 : 4) knn_brute_kernel(const float4* __restrict__ P, int n,
                                                             int k, int32_t* __restrict__ out) {
-  __shared__ float4 tile[KNN_TILE];
+  __shared__ __align__(16) float tile[3 * KNN_TILE];
+  __shared__ float qks[KNN_QL * KNN_TPB];
+  __shared__ int qis[KNN_QL * KNN_TPB];
   const int qi = blockIdx.x * KNN_TPB + threadIdx.x;
   const float4 q = P[qi < n ? qi : n - 1];
   float kd[KC];
   int ki[KC];
-  knn_scan<KC>(P, 0, n, q, kd, ki, tile);
+  knn_scan<KC>(P, 0, n, q, kd, ki, tile, qks, qis);
   if (qi < n) {
 #pragma unroll
     for (int m = 0; m < KC; ++m)
@@ -107,11 +184,13 @@ __global__ void __launch_bounds__(KNN_TPB) knn_brute_kernel(const float4* __rest
 // Many clouds in one launch: block b handles queries [q0, q0 + KNN_TPB) of
 // cloud c = table[b].x (q0 = table[b].y), each against its own cloud only.
 template <int KC>
-__global__ void __launch_bounds__(KNN_TPB) knn_brute_multi_kernel(const float4* __restrict__ P,
+__global__ void __launch_bounds__(KNN_TPB, KC > 16 ? 2 : 4) knn_brute_multi_kernel(const float4* __restrict__ P,
                                                                   const int64_t* __restrict__ off,
                                                                   const int2* __restrict__ table, int k,
                                                                   int32_t* __restrict__ out) {
-  __shared__ float4 tile[KNN_TILE];
+  __shared__ __align__(16) float tile[3 * KNN_TILE];
+  __shared__ float qks[KNN_QL * KNN_TPB];
+  __shared__ int qis[KNN_QL * KNN_TPB];
   const int2 e = table[blockIdx.x];
   const int64_t base = off[e.x];
   const int n = (int)(off[e.x + 1] - base);
@@ -119,7 +198,7 @@ __global__ void __launch_bounds__(KNN_TPB) knn_brute_multi_kernel(const float4* 
   const float4 q = P[base + (ql < n ? ql : n - 1)];
   float kd[KC];
   int ki[KC];
-  knn_scan<KC>(P, base, n, q, kd, ki, tile);
+  knn_scan<KC>(P, base, n, q, kd, ki, tile, qks, qis);
   if (ql < n) {
 #pragma unroll
     for (int m = 0; m < KC; ++m)
@@ -132,13 +211,13 @@ __global__ void __launch_bounds__(KNN_TPB) knn_brute_multi_kernel(const float4* 
 __global__ void __launch_bounds__(KNN_TPB) nearest_kernel(const float4* __restrict__ P, int n,
                                                           const float* __restrict__ q3, int nq,
                                                           int32_t* __restrict__ idx_out, float* __restrict__ key_out) {
-  __shared__ float4 tile[KNN_TILE];
+  __shared__ __align__(16) float tile[3 * KNN_TILE];
   const int qi = blockIdx.x * KNN_TPB + threadIdx.x;
   const int qc = qi < nq ? qi : nq - 1;
   const float4 q = make_float4(q3[3 * (size_t)qc], q3[3 * (size_t)qc + 1], q3[3 * (size_t)qc + 2], 0.f);
   float kd[1];
   int ki[1];
-  knn_scan<1>(P, 0, n, q, kd, ki, tile);
+  knn_scan<1>(P, 0, n, q, kd, ki, tile, nullptr, nullptr);
   if (qi < nq) {
     if (idx_out) idx_out[qi] = ki[0];
     if (key_out) key_out[qi] = kd[0];
@@ -211,10 +290,9 @@ __global__ void curvature_kernel(const float4* __restrict__ P, const int32_t* __
   }
   C[0] /= k; C[1] /= k; C[2] /= k; C[4] /= k; C[5] /= k; C[8] /= k;
   C[3] = C[1]; C[6] = C[2]; C[7] = C[5];
-  double lam[3];
-  sym3_eigenvalues(C, lam);
+  const double lmin = sym3_min_eigenvalue(C);
   const double tr = C[0] + C[4] + C[8];
-  const double a = tr > 0.0 ? fmax(lam[0], 0.0) / tr : 0.0;
+  const double a = tr > 0.0 ? fmax(lmin, 0.0) / tr : 0.0;
   a64[i] = a;
   a32[i] = (float)a;
 }
@@ -297,10 +375,9 @@ __global__ void __launch_bounds__(RAD_TPB)
   C[0] = S[3] / k - mx * mx; C[1] = S[4] / k - mx * my; C[2] = S[5] / k - mx * mz;
   C[4] = S[6] / k - my * my; C[5] = S[7] / k - my * mz; C[8] = S[8] / k - mz * mz;
   C[3] = C[1]; C[6] = C[2]; C[7] = C[5];
-  double lam[3];
-  sym3_eigenvalues(C, lam);
+  const double lmin = sym3_min_eigenvalue(C);
   const double tr = C[0] + C[4] + C[8];
-  const double a = tr > 0.0 ? fmax(lam[0], 0.0) / tr : 0.0;
+  const double a = tr > 0.0 ? fmax(lmin, 0.0) / tr : 0.0;
   a64[i] = a;
   a32[i] = (float)a;
   if (count_out) count_out[i] = cnt;

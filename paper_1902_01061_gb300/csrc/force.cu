@@ -33,36 +33,6 @@
 
 namespace scgr {
 
-typedef unsigned long long u64;  // two packed float32 lanes: low = point j, high = point j+1
-
-__device__ __forceinline__ u64 pk2(float lo, float hi) {
-  u64 r;
-  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
-  return r;
-}
-__device__ __forceinline__ void upk2(u64 v, float& lo, float& hi) {
-  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
-}
-__device__ __forceinline__ u64 add2(u64 a, u64 b) {
-  u64 d;
-  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-  return d;
-}
-__device__ __forceinline__ u64 sub2(u64 a, u64 b) {
-  u64 d;
-  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-  return d;
-}
-__device__ __forceinline__ u64 mul2(u64 a, u64 b) {
-  u64 d;
-  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-  return d;
-}
-__device__ __forceinline__ u64 fma2(u64 a, u64 b, u64 c) {
-  u64 d;
-  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-  return d;
-}
 // 2^-x
 __device__ __forceinline__ float ex2_neg(float x) {
   float y;
@@ -591,19 +561,48 @@ cudaError_t launch_combine_moments(Launch L, const double* mom, int m, int mpad,
 }
 
 // ---- combine: splits -> per-point force -> per-block (F, W, T) -------------
-constexpr int CMB_TPB = RED_THREADS;
+// A block covers 256 template slots with 64 threads of 4 points each.  Per
+// point, the split partials are added with Kahan compensation and
+// f = aY (S - Y' W) is formed with an exact product (fma) and an exact sum,
+// so f is as accurate as float allows even when S and Y' W nearly cancel;
+// f (x) c and the other block terms are FP32 products of accurate factors.  A
+// thread's four points are added in FP32, and every sum across threads and
+// blocks is FP64 in a fixed order.  (FP64 arithmetic per point would make
+// this kernel FP64-bound: GB300 issues FP64 at a small fraction of FP32.)
+constexpr int CMB_TPB = 64;
+constexpr int CMB_PPT = 4;  // points per thread: CMB_TPB * CMB_PPT = 256 slots per block
+
+// Reduce 16 doubles over a warp by recursive halving: lane L ends with the
+// warp total of quantity 8 b4 + 4 b3 + 2 b2 + b1 (b_k = bit k of L), 16
+// additions per lane instead of 80 for a butterfly per quantity.
+__device__ __forceinline__ void warp_reduce16(double (&v)[16]) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int lvl = 0; lvl < 4; ++lvl) {
+    const int off = 16 >> lvl;
+    const int half = 8 >> lvl;
+    const bool upper = (lane & off) != 0;
+#pragma unroll
+    for (int q = 0; q < half; ++q) {
+      const double send = upper ? v[q] : v[q + half];
+      const double keep = upper ? v[q + half] : v[q];
+      v[q] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+    }
+  }
+  v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
+}
 
 // BATCH = true: block b belongs to pair cpair[b]; its 256 template slots are
-// that pair's slots (b - cblk0) * 256 + threadIdx.x.
+// that pair's slots (b - cblk0) * 256 + threadIdx.x + 64 k, k < 4.
 template <bool BATCH>
-__global__ void __launch_bounds__(CMB_TPB)
+__global__ void __launch_bounds__(CMB_TPB, 8)
     combine_kernel(const float4* __restrict__ partial, int S, int mpad, int m,
                    const float4* __restrict__ Y0r, const double* __restrict__ aY64, int g_mode,
                    const DevPose* __restrict__ pose, float4* __restrict__ f4out,
                    double* __restrict__ blockpart, const int* __restrict__ cpair,
                    const BatchPair* __restrict__ pairs) {
-  __shared__ double sh[13][RED_THREADS];
-  int i, mm, SS;
+  __shared__ double sh[CMB_TPB / 32][16];
+  int i0, mm, SS;
   size_t pstride;
   const float4* pbase;
   const float4* ybase;
@@ -612,7 +611,7 @@ __global__ void __launch_bounds__(CMB_TPB)
   if (BATCH) {
     const int p = cpair[blockIdx.x];
     const BatchPair& bp = pairs[p];
-    i = (blockIdx.x - bp.cblk0) * CMB_TPB + threadIdx.x;
+    i0 = (blockIdx.x - bp.cblk0) * (CMB_TPB * CMB_PPT);
     mm = (int)bp.m;
     SS = bp.chunks;
     pstride = (size_t)bp.mpad;
@@ -621,7 +620,7 @@ __global__ void __launch_bounds__(CMB_TPB)
     abase = aY64 + bp.y0;
     ps = pose + p;
   } else {
-    i = blockIdx.x * CMB_TPB + threadIdx.x;
+    i0 = blockIdx.x * (CMB_TPB * CMB_PPT);
     mm = m;
     SS = S;
     pstride = (size_t)mpad;
@@ -630,49 +629,93 @@ __global__ void __launch_bounds__(CMB_TPB)
     abase = aY64;
     ps = pose;
   }
-  double v[13];
+  float A[9], b[3], ch[3], cl[3];
 #pragma unroll
-  for (int q = 0; q < 13; ++q) v[q] = 0.0;
-  if (i < mm) {
-    double W = 0, Sx = 0, Sy = 0, Sz = 0;
-    for (int s = 0; s < SS; ++s) {
-      const float4 pp = pbase[(size_t)s * pstride + i];
-      W += pp.x;
-      Sx += pp.y;
-      Sy += pp.z;
-      Sz += pp.w;
-    }
-    float A[9], b[3];
+  for (int q = 0; q < 9; ++q) A[q] = ps->A[q];
 #pragma unroll
-    for (int q = 0; q < 9; ++q) A[q] = ps->A[q];
-#pragma unroll
-    for (int q = 0; q < 3; ++q) b[q] = ps->b[q];
-    float yx, yy, yz;
-    template_point(ybase[i], A, b, yx, yy, yz);
-    const double ay = g_mode == 1 ? abase[i] : 1.0;
-    const double f[3] = {ay * (Sx - (double)yx * W), ay * (Sy - (double)yy * W),
-                         ay * (Sz - (double)yz * W)};
-    const double Wi = ay * W;
-    const double c[3] = {(double)yx - ps->ybs[0], (double)yy - ps->ybs[1],
-                         (double)yz - ps->ybs[2]};
-    v[0] = f[0];
-    v[1] = f[1];
-    v[2] = f[2];
-    v[3] = Wi;
-#pragma unroll
-    for (int a = 0; a < 3; ++a)
-#pragma unroll
-      for (int bb = 0; bb < 3; ++bb) v[4 + 3 * a + bb] = f[a] * c[bb];
-    if (f4out) f4out[i] = make_float4((float)f[0], (float)f[1], (float)f[2], (float)Wi);
+  for (int q = 0; q < 3; ++q) {
+    b[q] = ps->b[q];
+    const double yb = ps->ybs[q];  // template mean (centred frame) as a float pair
+    ch[q] = (float)yb;
+    cl[q] = (float)(yb - (double)ch[q]);
   }
-  block_sum<13>(v, sh);
-  if (threadIdx.x == 0) {
+  float acc[13];
 #pragma unroll
-    for (int q = 0; q < 13; ++q) blockpart[(size_t)blockIdx.x * 13 + q] = v[q];
+  for (int q = 0; q < 13; ++q) acc[q] = 0.f;
+#pragma unroll
+  for (int k = 0; k < CMB_PPT; ++k) {
+    const int i = i0 + k * CMB_TPB + threadIdx.x;
+    if (i < mm) {
+      float Wh = 0.f, Wc = 0.f, Sh[3] = {0.f, 0.f, 0.f}, Sc[3] = {0.f, 0.f, 0.f};
+      // splits in order; four loads issued together
+      int s = 0;
+      for (; s + 4 <= SS; s += 4) {
+        float4 pp[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) pp[u] = pbase[(size_t)(s + u) * pstride + i];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          kahan_add(Wh, Wc, pp[u].x);
+          kahan_add(Sh[0], Sc[0], pp[u].y);
+          kahan_add(Sh[1], Sc[1], pp[u].z);
+          kahan_add(Sh[2], Sc[2], pp[u].w);
+        }
+      }
+      for (; s < SS; ++s) {
+        const float4 pp = pbase[(size_t)s * pstride + i];
+        kahan_add(Wh, Wc, pp.x);
+        kahan_add(Sh[0], Sc[0], pp.y);
+        kahan_add(Sh[1], Sc[1], pp.z);
+        kahan_add(Sh[2], Sc[2], pp.w);
+      }
+      float y[3];
+      template_point(ybase[i], A, b, y[0], y[1], y[2]);
+      const float ay = g_mode == 1 ? (float)abase[i] : 1.f;
+      float f[3];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        // D = (Sh - Sc) - y (Wh - Wc): y Wh = p + pe exactly, Sh - p = dh + dl exactly
+        const float p = y[a] * Wh;
+        const float pe = fmaf(y[a], Wh, -p);
+        const float dh = Sh[a] - p;
+        const float bv = dh - Sh[a];
+        const float dl = (Sh[a] - (dh - bv)) + (-p - bv);
+        const float D = dh + ((dl - pe) + fmaf(y[a], Wc, -Sc[a]));
+        f[a] = ay * D;
+      }
+      const float Wi = ay * (Wh - Wc);
+      float c[3];
+#pragma unroll
+      for (int q = 0; q < 3; ++q) c[q] = (y[q] - ch[q]) - cl[q];
+      acc[0] += f[0];
+      acc[1] += f[1];
+      acc[2] += f[2];
+      acc[3] += Wi;
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int bb = 0; bb < 3; ++bb) acc[4 + 3 * a + bb] = fmaf(f[a], c[bb], acc[4 + 3 * a + bb]);
+      if (f4out) f4out[i] = make_float4(f[0], f[1], f[2], Wi);
+    }
+  }
+  double v[16];
+#pragma unroll
+  for (int q = 0; q < 13; ++q) v[q] = (double)acc[q];
+  v[13] = v[14] = v[15] = 0.0;
+  warp_reduce16(v);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int qid = ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 + ((lane >> 1) & 1);
+  if ((lane & 1) == 0) sh[warp][qid] = v[0];
+  __syncthreads();
+  if (threadIdx.x < 13) {
+    double t = sh[0][threadIdx.x];
+#pragma unroll
+    for (int w = 1; w < CMB_TPB / 32; ++w) t += sh[w][threadIdx.x];
+    blockpart[(size_t)blockIdx.x * 13 + threadIdx.x] = t;
   }
 }
 
-int combine_blocks(int64_t mpad) { return (int)((mpad + CMB_TPB - 1) / CMB_TPB); }
+int combine_blocks(int64_t mpad) { return (int)((mpad + CMB_TPB * CMB_PPT - 1) / (CMB_TPB * CMB_PPT)); }
 
 cudaError_t launch_combine(Launch L, const float4* partial, int S, int mpad, int m,
                            const float4* Y0r, const double* aY64, int g_mode, const DevPose* pose,

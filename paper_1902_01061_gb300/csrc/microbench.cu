@@ -57,6 +57,18 @@ __global__ void __launch_bounds__(MB_TPB) microbench_kernel(float* __restrict__ 
         float r;
         asm volatile("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x[c]));
         x[c] = r;
+      } else if (KIND == 7) {
+        // the force kernel's instruction mix: 6 packed FMAs, one ex2 and one
+        // sqrt per step.  If the FP32 pipe and the special-function unit
+        // overlapped perfectly this would run at the special-function bound
+        // (12 unit cycles per 32 steps); if a packed FMA holds the issue
+        // port for two cycles, at 14 cycles.
+#pragma unroll
+        for (int f = 0; f < 6; ++f) y[c] = mb_fma2(y[c], a2, b2);
+        float r, w;
+        asm volatile("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(-x[c]));
+        asm volatile("sqrt.approx.ftz.f32 %0, %1;" : "=f"(w) : "f"(r));
+        x[c] = w;
       } else {
         // ex2 on even chains, rsqrt on odd ones: whether the two share one unit
         float r;
@@ -77,13 +89,14 @@ __global__ void __launch_bounds__(MB_TPB) microbench_kernel(float* __restrict__ 
 }  // namespace
 
 // kind: 0 FFMA, 1 packed fma.f32x2, 2 MUFU ex2, 3 MUFU sqrt, 4 MUFU lg2, 5 MUFU rsqrt,
-// 6 ex2 and rsqrt interleaved.
+// 6 ex2 and rsqrt interleaved, 7 the force kernel's mix (6 fma.f32x2 + ex2 + sqrt;
+// lane_ops counts steps).
 // lane_ops: FP32 lane operations (an f32x2 FMA counts 2) or MUFU results;
 // ms: device time of one launch on `out_dev` (blocks x 256 floats of scratch
 // supplied by the caller, blocks = 8 x SM count).
 extern "C" scgr_status scgr_microbench(int kind, int blocks, float* out_dev, void* cuda_stream,
                                        int64_t* lane_ops, double* ms) {
-  if (!out_dev || !lane_ops || !ms || blocks < 1 || kind < 0 || kind > 6) return SCGR_ERR_INVALID_ARG;
+  if (!out_dev || !lane_ops || !ms || blocks < 1 || kind < 0 || kind > 7) return SCGR_ERR_INVALID_ARG;
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess) return SCGR_ERR_CUDA;
@@ -101,7 +114,8 @@ extern "C" scgr_status scgr_microbench(int kind, int blocks, float* out_dev, voi
       case 3: microbench_kernel<3><<<blocks, MB_TPB, 0, st>>>(out_dev, 1.5f, 0.f); break;
       case 4: microbench_kernel<4><<<blocks, MB_TPB, 0, st>>>(out_dev, 1.5f, 0.f); break;
       case 5: microbench_kernel<5><<<blocks, MB_TPB, 0, st>>>(out_dev, 1.5f, 0.f); break;
-      default: microbench_kernel<6><<<blocks, MB_TPB, 0, st>>>(out_dev, 1.5f, 0.f); break;
+      case 6: microbench_kernel<6><<<blocks, MB_TPB, 0, st>>>(out_dev, 1.5f, 0.f); break;
+      default: microbench_kernel<7><<<blocks, MB_TPB, 0, st>>>(out_dev, 0.5f, 1e-3f); break;
     }
     cudaEventRecord(e1, st);
     if (cudaEventSynchronize(e1) != cudaSuccess) {

@@ -1,7 +1,8 @@
 // Pose update in float64 (Eq. 5.5, Eq. 6, Eq. 8, Eq. 9, Eq. 12): one block
 // reduces the per-block (F, W, T) partials in a fixed order, then one thread
-// forms the step, the Kabsch rotation by a one-sided Jacobi SVD, the scale,
-// the composed pose and its polar re-orthonormalisation.  The pose never
+// forms the step, the Kabsch rotation (the polar factor of C^ by Newton's
+// iteration, or a one-sided Jacobi SVD in the reflection and near-singular
+// cases), the scale, the composed pose and its re-orthonormalisation.  The pose never
 // leaves the device, so a run of iterations is a plain sequence of launches.
 #include <cmath>
 
@@ -113,6 +114,86 @@ __device__ void polar3(const double* R, double* out) {
       out[r * 3 + c] = U[r * 3] * V[c * 3] + U[r * 3 + 1] * V[c * 3 + 1] + U[r * 3 + 2] * V[c * 3 + 2];
 }
 
+// Orthogonal polar factor Q of A (A = Q H, H symmetric positive definite)
+// for det A > 0 by Newton's iteration X <- (g X + X^-T / g) / 2 with
+// Frobenius-norm scaling g = (|X^-1| / |X|)^(1/2) while far from the limit
+// (Higham, "Computing the polar decomposition -- with applications", 1986).
+// X^-T is the cofactor matrix over the determinant.  Each step is a short
+// chain of FP64 operations, where a Jacobi SVD needs several square roots and
+// divisions per rotation; on GB300, whose FP64 unit is narrow, that chain
+// length is what one finalize thread waits on.  Returns false (the caller
+// then takes the SVD) when det A <= 0, when |A|_F |A^-1|_F > 1e6, or when the
+// iteration has not settled in 40 steps.
+__device__ bool polar_newton(const double* A, double* Q) {
+  double X[9];
+  for (int q = 0; q < 9; ++q) X[q] = A[q];
+  bool scale = true, settled = false;
+  for (int it = 0; it < 40; ++it) {
+    double C[9];
+    C[0] = X[4] * X[8] - X[5] * X[7];
+    C[1] = X[5] * X[6] - X[3] * X[8];
+    C[2] = X[3] * X[7] - X[4] * X[6];
+    C[3] = X[2] * X[7] - X[1] * X[8];
+    C[4] = X[0] * X[8] - X[2] * X[6];
+    C[5] = X[1] * X[6] - X[0] * X[7];
+    C[6] = X[1] * X[5] - X[2] * X[4];
+    C[7] = X[2] * X[3] - X[0] * X[5];
+    C[8] = X[0] * X[4] - X[1] * X[3];
+    const double det = X[0] * C[0] + X[1] * C[1] + X[2] * C[2];
+    if (!(det > 0.0) || !isfinite(det)) return false;
+    const double id = 1.0 / det;
+    double nx = 0.0, ny = 0.0;
+    for (int q = 0; q < 9; ++q) {
+      C[q] *= id;  // now X^-T
+      nx += X[q] * X[q];
+      ny += C[q] * C[q];
+    }
+    if (it == 0 && !(nx * ny <= 1e12)) return false;
+    const double g = scale ? sqrt(sqrt(ny / nx)) : 1.0;
+    const double ig = 1.0 / g;
+    double diff = 0.0, nn = 0.0;
+    for (int q = 0; q < 9; ++q) {
+      const double xn = 0.5 * (g * X[q] + ig * C[q]);
+      diff += (xn - X[q]) * (xn - X[q]);
+      nn += xn * xn;
+      X[q] = xn;
+    }
+    if (settled) break;                   // one plain step after the change fell below 1e-9
+    if (diff <= 1e-18 * nn) settled = true;
+    scale = diff > 1e-4 * nn;
+    if (it == 39) return false;
+  }
+  for (int q = 0; q < 9; ++q) Q[q] = X[q];
+  return true;
+}
+
+// Re-orthonormalise a rotation that is orthogonal to rounding error:
+// Newton-Schulz steps R <- R (3 I - R^T R) / 2, quadratically convergent to
+// the orthogonal polar factor; the SVD route when R is further off.
+__device__ void reorthonormalise(const double* Rin, double* out) {
+  double R[9];
+  for (int q = 0; q < 9; ++q) R[q] = Rin[q];
+  for (int step = 0; step < 2; ++step) {
+    double M[9];
+    double dev = 0.0;
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) {
+        const double g = R[a] * R[b] + R[3 + a] * R[3 + b] + R[6 + a] * R[6 + b];  // (R^T R)_ab
+        const double e = g - (a == b ? 1.0 : 0.0);
+        dev = fmax(dev, fabs(e));
+        M[a * 3 + b] = (a == b ? 1.0 : 0.0) - 0.5 * e;
+      }
+    if (step == 0 && !(dev <= 1e-6)) {
+      polar3(Rin, out);
+      return;
+    }
+    double Rn[9];
+    mul3(R, M, Rn);
+    for (int q = 0; q < 9; ++q) R[q] = Rn[q];
+  }
+  for (int q = 0; q < 9; ++q) out[q] = R[q];
+}
+
 // Derived float32 map and template mean for the current pose.
 __device__ void refresh_pose(DevPose* ps, const DevStats* st) {
   for (int q = 0; q < 9; ++q) ps->A[q] = (float)(ps->s * ps->R[q]);
@@ -151,6 +232,105 @@ cudaError_t launch_pose_refresh(Launch L, DevPose* pose, const DevStats* stats) 
   return cudaGetLastError();
 }
 
+// ---- warp-parallel 3x3 algebra -------------------------------------------
+// GB300 issues an FP64 warp instruction at a small fraction of the FP32 rate
+// whatever the number of active lanes, so the finalize step spreads its 3x3
+// matrices over a warp: lane l < 9 owns entry (l / 3, l % 3) (lanes 9..31
+// mirror entry 8; their results are never stored).  A 3x3 product is then 3
+// FP64 instructions for the warp instead of 27 for one thread.  Every
+// function here must be called by all 32 lanes of the warp together.
+constexpr unsigned WFULL = 0xffffffffu;
+
+struct Lane3 {
+  int q, r, c;
+};
+__device__ __forceinline__ Lane3 lane3() {
+  const int q = min((int)(threadIdx.x & 31), 8);
+  return {q, q / 3, q % 3};
+}
+__device__ __forceinline__ double wget(double v, int idx) { return __shfl_sync(WFULL, v, idx); }
+
+// (A B)_rc and (A^T B)_rc for lane-owned A and B
+__device__ __forceinline__ double wmul(double a, double b, Lane3 L) {
+  const double acc = wget(a, L.r * 3) * wget(b, L.c);
+  return fma(wget(a, L.r * 3 + 2), wget(b, 6 + L.c), fma(wget(a, L.r * 3 + 1), wget(b, 3 + L.c), acc));
+}
+__device__ __forceinline__ double wmul_ta(double a, double b, Lane3 L) {
+  const double acc = wget(a, L.r) * wget(b, L.c);
+  return fma(wget(a, 6 + L.r), wget(b, 6 + L.c), fma(wget(a, 3 + L.r), wget(b, 3 + L.c), acc));
+}
+
+// Sum and maximum over lanes 0..8, the same value in every lane (lane 0's).
+__device__ __forceinline__ float wsum9(float v) {
+  if ((threadIdx.x & 31) >= 9) v = 0.f;
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(WFULL, v, off);
+  return __shfl_sync(WFULL, v, 0);
+}
+__device__ __forceinline__ double wsum9d(double v) {
+  if ((threadIdx.x & 31) >= 9) v = 0.0;
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(WFULL, v, off);
+  return __shfl_sync(WFULL, v, 0);
+}
+__device__ __forceinline__ float wmax9(float v) {
+  if ((threadIdx.x & 31) >= 9) v = 0.f;
+  for (int off = 16; off > 0; off >>= 1) v = fmaxf(v, __shfl_xor_sync(WFULL, v, off));
+  return __shfl_sync(WFULL, v, 0);
+}
+
+// 1/x for x > 0 in float64 from the float32 reciprocal and two Newton steps.
+__device__ __forceinline__ double wrcp(double x) {
+  double r = (double)(1.0f / (float)x);
+  r = fma(r, fma(-x, r, 1.0), r);
+  return fma(r, fma(-x, r, 1.0), r);
+}
+
+// Warp form of polar_newton (same iteration and exits): Q's entry in each
+// lane.  The input is first scaled to unit Frobenius norm, which leaves the
+// polar factor unchanged and keeps the FP32 norms below in range.  The
+// scaling factor g and the stop test use FP32 sums: any positive weights
+// (a X + b X^-T) / 2 keep the polar factor, so they only steer convergence;
+// the last steps use a = b = 1 exactly.
+__device__ bool polar_newton_warp(double A, Lane3 L, double& Q) {
+  const double n2 = wsum9d(A * A);
+  if (!(n2 > 0.0) || !isfinite(n2)) return false;
+  double X = A * (1.0 / sqrt(n2));
+  const int r1 = (L.r + 1) % 3, r2 = (L.r + 2) % 3, c1 = (L.c + 1) % 3, c2 = (L.c + 2) % 3;
+  bool scale = true, settled = false;
+  for (int it = 0; it < 40; ++it) {
+    double C = fma(-wget(X, r1 * 3 + c2), wget(X, r2 * 3 + c1), wget(X, r1 * 3 + c1) * wget(X, r2 * 3 + c2));
+    const double det = fma(wget(X, 2), wget(C, 2), fma(wget(X, 1), wget(C, 1), wget(X, 0) * wget(C, 0)));
+    if (!(det > 1e-30) || !isfinite(det)) return false;
+    C *= wrcp(det);  // X^-T
+    const float fx = (float)X, fc = (float)C;
+    const float nx = wsum9(fx * fx), ny = wsum9(fc * fc);
+    if (it == 0 && !(nx * ny <= 1e12f)) return false;
+    const float g = scale ? sqrtf(sqrtf(ny / nx)) : 1.f;
+    const double Xn = fma(0.5 * (double)g, X, (double)(0.5f / g) * C);
+    const float dx = (float)(Xn - X), fn = (float)Xn;
+    const float dd = wsum9(dx * dx), nn = wsum9(fn * fn);
+    X = Xn;
+    if (settled) break;  // one plain step after the change fell below 1e-9
+    if (dd <= 1e-18f * nn) settled = true;
+    scale = dd > 1e-4f * nn;
+    if (it == 39) return false;
+  }
+  Q = X;
+  return true;
+}
+
+// Warp form of reorthonormalise: two Newton-Schulz steps; false (the caller
+// takes the SVD route) when R^T R is further than 1e-6 from I.
+__device__ bool reorth_warp(double R, Lane3 L, double& out) {
+  const double I = (L.r == L.c) ? 1.0 : 0.0;
+  for (int step = 0; step < 2; ++step) {
+    const double e = wmul_ta(R, R, L) - I;
+    if (step == 0 && !(wmax9(fabsf((float)e)) <= 1e-6f)) return false;
+    R = wmul(R, fma(-0.5, e, I), L);
+  }
+  out = R;
+  return true;
+}
+
 __device__ void finalize_body(const double* __restrict__ blockpart, int nblocks, DevPose* ps,
                               const DevStats* __restrict__ st, StepParams sp, int* err,
                               double (*sh)[RED_THREADS]) {
@@ -162,11 +342,14 @@ __device__ void finalize_body(const double* __restrict__ blockpart, int nblocks,
     for (int q = 0; q < 13; ++q) v[q] += blockpart[(size_t)bidx * 13 + q];
   }
   block_sum<13>(v, sh);
-  if (threadIdx.x != 0) return;
+  __syncthreads();  // every thread has read the totals: sh is scratch from here on
+  if (threadIdx.x >= 32) return;
 
-  const double F[3] = {v[0], v[1], v[2]};
+  // Warp 0 forms the update; lane (r, c) owns entry (r, c) of each 3x3.
+  const Lane3 L = lane3();
+  const int lane = threadIdx.x;
   const double W = v[3];
-  const double* T = v + 4;  // T[a][b] = sum_i f_i[a] (Y_i - ybar)[b]
+  const double Tq = v[4 + L.q];  // T[a][b] = sum_i f_i[a] (Y_i - ybar)[b]
   const int it = ps->it;
   const double E = (double)ps->E;
   // Eq. 12, 0-based iteration index
@@ -180,44 +363,54 @@ __device__ void finalize_body(const double* __restrict__ blockpart, int nblocks,
     kappa = G * sp.time * sp.time;
   }
   const double s = ps->s;
-  const double* R = ps->R;
-  double d[3], ybar[3];
+  const double Rq = ps->R[L.q];
+  // template mean at this pose (every lane, all three components)
+  double yb[3], tt[3];
   for (int c = 0; c < 3; ++c) {
-    d[c] = kappa * F[c] / (double)sp.M;  // Eq. 5.5, unit masses, v = 0
-    ybar[c] = s * (st->ybar0[0] * R[c] + st->ybar0[1] * R[3 + c] + st->ybar0[2] * R[6 + c]) + ps->t[c];
+    tt[c] = ps->t[c];
+    yb[c] = fma(s, fma(st->ybar0[2], ps->R[6 + c], fma(st->ybar0[1], ps->R[3 + c], st->ybar0[0] * ps->R[c])), tt[c]);
   }
+  const double dc = kappa * v[L.c] / (double)sp.M;  // Eq. 5.5, unit masses, v = 0 (component c)
   // C^ = Y_D^T Y_c = s^2 R^T S0 R + kappa T   (Eq. 6 with the displaced cloud)
-  double SR[9], Syy[9], Ch[9];
-  mul3(st->S0, R, SR);
-  for (int a = 0; a < 3; ++a)
-    for (int b2 = 0; b2 < 3; ++b2) {
-      double acc = 0.0;
-      for (int r = 0; r < 3; ++r) acc += R[r * 3 + a] * SR[r * 3 + b2];
-      Syy[a * 3 + b2] = s * s * acc;
+  const double SR = wmul(st->S0[L.q], Rq, L);
+  const double Ch = fma(kappa, Tq, s * s * wmul_ta(Rq, SR, L));
+  bad = bad || !isfinite(Ch) || !isfinite(dc);
+  if (__any_sync(WFULL, bad)) {
+    if (lane == 0) {
+      atomicOr(err, ERR_NUMERIC);
+      ps->it = it + 1;
     }
-  for (int q = 0; q < 9; ++q) Ch[q] = Syy[q] + kappa * T[q];
-  for (int q = 0; q < 9; ++q)
-    if (!isfinite(Ch[q])) bad = true;
-  for (int c = 0; c < 3; ++c)
-    if (!isfinite(d[c])) bad = true;
-  if (bad) {
-    atomicOr(err, ERR_NUMERIC);
-    ps->it = it + 1;
     return;
   }
-  // Eq. 6: C^ = U S V^T, dd = sign det(V U^T), R_inc = V diag(1, 1, dd) U^T
-  double U[9], Sg[3], V[9], Rinc[9];
-  svd3(Ch, U, Sg, V);
-  if (!(Sg[0] > 0.0) || Sg[1] <= 1e-12 * Sg[0]) {
-    for (int q = 0; q < 9; ++q) Rinc[q] = (q % 4 == 0) ? 1.0 : 0.0;
-    ps->degenerate += 1;
+  // Eq. 6: C^ = U S V^T, dd = sign det(V U^T), R_inc = V diag(1, 1, dd) U^T.
+  // For det C^ > 0 (dd = 1) that is Q^T, Q the orthogonal polar factor of C^
+  // (C^ = (U V^T)(V S V^T)), taken by Newton's iteration; the SVD handles
+  // det C^ <= 0, near-singular C^ and the degenerate case.
+  double Rinc, Qp;
+  if (polar_newton_warp(Ch, L, Qp)) {
+    Rinc = wget(Qp, L.c * 3 + L.r);
   } else {
-    const double dd = (det3(V) * det3(U)) >= 0.0 ? 1.0 : -1.0;
-    const double D[3] = {1.0, 1.0, dd};
-    for (int r = 0; r < 3; ++r)
-      for (int c = 0; c < 3; ++c)
-        Rinc[r * 3 + c] = V[r * 3] * D[0] * U[c * 3] + V[r * 3 + 1] * D[1] * U[c * 3 + 1] +
-                          V[r * 3 + 2] * D[2] * U[c * 3 + 2];
+    double* scr = &sh[0][0];
+    if (lane < 9) scr[lane] = Ch;
+    __syncwarp();
+    if (lane == 0) {
+      double U[9], Sg[3], V[9], Ri[9];
+      svd3(scr, U, Sg, V);
+      if (!(Sg[0] > 0.0) || Sg[1] <= 1e-12 * Sg[0]) {
+        for (int q = 0; q < 9; ++q) Ri[q] = (q % 4 == 0) ? 1.0 : 0.0;
+        ps->degenerate += 1;
+      } else {
+        const double dd = (det3(V) * det3(U)) >= 0.0 ? 1.0 : -1.0;
+        const double D[3] = {1.0, 1.0, dd};
+        for (int r = 0; r < 3; ++r)
+          for (int c = 0; c < 3; ++c)
+            Ri[r * 3 + c] = V[r * 3] * D[0] * U[c * 3] + V[r * 3 + 1] * D[1] * U[c * 3 + 1] +
+                            V[r * 3 + 2] * D[2] * U[c * 3 + 2];
+      }
+      for (int q = 0; q < 9; ++q) scr[16 + q] = Ri[q];
+    }
+    __syncwarp();
+    Rinc = scr[16 + L.q];
   }
   // scale model (Sec. III-B): c from the largest covariance eigenvalues
   const double eY = s * s * st->eY0;
@@ -225,28 +418,46 @@ __device__ void finalize_body(const double* __restrict__ blockpart, int nblocks,
   if (sp.scale_mode == 0) cs = sqrt(st->eX / eY);
   else if (sp.scale_mode == 1) cs = st->eX / eY;
   // Eq. 8, Eq. 9: Y(t+1) = c (Y - ybar) R_inc + ybar + d, composed into the pose
-  double tn[3];
-  for (int c = 0; c < 3; ++c) {
-    double acc = 0.0;
-    for (int r = 0; r < 3; ++r) acc += (ps->t[r] - ybar[r]) * Rinc[r * 3 + c];
-    tn[c] = cs * acc + ybar[c] + d[c];
+  double acc = (tt[0] - yb[0]) * wget(Rinc, L.c);
+  acc = fma(tt[1] - yb[1], wget(Rinc, 3 + L.c), acc);
+  acc = fma(tt[2] - yb[2], wget(Rinc, 6 + L.c), acc);
+  const double tn = fma(cs, acc, yb[L.c] + dc);  // component c
+  const double RR = wmul(Rq, Rinc, L);
+  double Rn;
+  if (!reorth_warp(RR, L, Rn)) {
+    double* scr = &sh[0][0];
+    if (lane < 9) scr[32 + lane] = RR;
+    __syncwarp();
+    if (lane == 0) polar3(scr + 32, scr + 48);
+    __syncwarp();
+    Rn = scr[48 + L.q];
   }
-  double RR[9], Rn[9];
-  mul3(R, Rinc, RR);
-  polar3(RR, Rn);
-  bool ok = isfinite(cs);
-  for (int q = 0; q < 9; ++q) ok = ok && isfinite(Rn[q]);
-  for (int c = 0; c < 3; ++c) ok = ok && isfinite(tn[c]);
-  if (!ok) {
-    atomicOr(err, ERR_NUMERIC);
-    ps->it = it + 1;
+  const bool ok = isfinite(cs) && isfinite(Rn) && isfinite(tn);
+  if (!__all_sync(WFULL, ok)) {
+    if (lane == 0) {
+      atomicOr(err, ERR_NUMERIC);
+      ps->it = it + 1;
+    }
     return;
   }
-  for (int q = 0; q < 9; ++q) ps->R[q] = Rn[q];
-  for (int c = 0; c < 3; ++c) ps->t[c] = tn[c];
-  ps->s = cs * s;
-  ps->it = it + 1;
-  refresh_pose(ps, st);
+  // new pose and its derived float32 map (the warp form of refresh_pose)
+  const double sn = cs * s;
+  const double ybs = fma(sn, fma(st->ybar0[2], wget(Rn, 6 + L.c), fma(st->ybar0[1], wget(Rn, 3 + L.c),
+                                                                         st->ybar0[0] * wget(Rn, L.c))),
+                         tn) - st->xbar[L.c];
+  if (lane < 9) {
+    ps->R[lane] = Rn;
+    ps->A[lane] = (float)(sn * Rn);
+  }
+  if (lane < 3) {
+    ps->t[lane] = tn;
+    ps->b[lane] = (float)(tn - st->xbar[lane]);
+    ps->ybs[lane] = ybs;
+  }
+  if (lane == 0) {
+    ps->s = sn;
+    ps->it = it + 1;
+  }
 }
 
 __global__ void __launch_bounds__(RED_THREADS)

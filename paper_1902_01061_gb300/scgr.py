@@ -333,7 +333,8 @@ def scgr_step_apply(ctx, totals) -> None:
 def scgr_microbench(kind: int, stream=None):
     """(lane_ops, ms) of one throughput-microbenchmark launch filling the GPU:
     kind 0 FFMA, 1 fma.f32x2, 2 ex2, 3 sqrt, 4 lg2, 5 rsqrt, 6 ex2 and rsqrt
-    interleaved."""
+    interleaved, 7 the force kernel's mix (6 fma.f32x2 + ex2 + sqrt per step;
+    counts steps)."""
     import torch
     blocks = 8 * torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
     out = torch.empty(blocks * 256, dtype=torch.float32, device="cuda")
