@@ -280,10 +280,13 @@ def bench_batch(args, scgr, torch, dev, steps, warmup):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     tuned = None
     if getattr(args, "batch_plan", None):
-        bP, bC = [int(v) for v in args.batch_plan.split(",")]
+        vals = [int(v) for v in args.batch_plan.split(",")]
+        bP, bC = vals[0], vals[1]
+        bQ = vals[2] if len(vals) > 2 else 0
         scgr.scgr_set_tuning(ctx, scgr.SCGR_TUNE_BATCH_P, bP)
         scgr.scgr_set_tuning(ctx, scgr.SCGR_TUNE_BATCH_CHUNK_TILES, bC)
-        tuned = {"P": bP, "chunk_tiles": bC, "pinned": True}
+        scgr.scgr_set_tuning(ctx, scgr.SCGR_TUNE_BATCH_PERSISTENT, bQ)
+        tuned = {"P": bP, "chunk_tiles": bC, "persistent": bQ, "pinned": True}
     elif not args.no_autotune:
         from paper_1902_01061_gb300 import autotune
         tuned = autotune.tune_batch(ctx, ro, Xc, to, Yc, 2.0, iterations=3)
@@ -476,7 +479,7 @@ def main():
     ap.add_argument("--batch-only", action="store_true",
                     help="run only the batched leg (no one-call-per-pair comparison) and print it")
     ap.add_argument("--batch-iters", type=int, default=100, help="iterations of the batched leg")
-    ap.add_argument("--batch-plan", default=None, help="pin the batched force kernel 'P,CHUNK_TILES' (no autotuning)")
+    ap.add_argument("--batch-plan", default=None, help="pin the batched force kernel 'P,CHUNK_TILES[,PERSISTENT]' (no autotuning)")
     ap.add_argument("--batch-eager", action="store_true", help="batched leg without the CUDA graph (for profilers)")
     ap.add_argument("--plan", default=None, help="pin the force kernel 'P,TPB[,OCC[,RSQRT]]' (no autotuning), e.g. 2,256,0,1")
     args = ap.parse_args()

@@ -329,6 +329,11 @@ SCGR_EXPORT scgr_status scgr_step_apply(scgr_ctx* ctx, const double tot13[13]);
                                          batched force kernels; results agree to rounding.  On GB300
                                          rsqrt costs the special-function unit as much as sqrt, so form 1
                                          only adds a multiply; the autotuner times both */
+#define SCGR_TUNE_BATCH_PERSISTENT 10 /* batched force pass: 0 (default) one block per work item, the
+                                         items ordered longest first; 1 one persistent block per resident
+                                         slot, each taking the next item (same order) from a queue head in
+                                         device memory that is cleared before every launch.  Results are
+                                         bit-identical: an item's sums do not depend on which block takes it */
 #define SCGR_TUNE_REUSE_POSE_FREE 6   /* 1 (default): odd integer p skips the per-iteration all-pairs pass.
                                          p = 1: the pair weights do not depend on the pose, so scgr_run
                                          computes the force sums once per call and reuses them

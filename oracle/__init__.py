@@ -46,6 +46,9 @@ Functions and their pins (the tests under ``tests/test_oracle_*.py``):
 * ``register``       - the whole iteration (Eq. 5-12); pinned to the fixed
                        point at the aligned pose and to recovery of known
                        synthetic transforms.
+* ``register_from_partials`` - ``register`` with each iteration's totals
+                       added from row blocks (so a process pool can share the
+                       force pass); pinned to ``register``.
 """
 from .scgr_oracle import (  # noqa: F401
     Params,
@@ -65,6 +68,7 @@ from .scgr_oracle import (  # noqa: F401
     scale_factor,
     polar,
     register,
+    register_from_partials,
     step_once,
     partial_sums,
     update_from_totals,

@@ -476,6 +476,38 @@ def update_from_totals(Y, totals, prm: Params, it: int, E: int, eX: float):
     return c * Yc @ Rinc + mu + dvec, dict(c=c, Rinc=Rinc, mu=mu, d=dvec, degenerate=degenerate)
 
 
+def register_from_partials(X, Y0, prm: Params, iterations: int, desc, row_blocks, map_partials=map):
+    """`register` with each iteration's totals (F, W, T; Eq. 5, 5.5, 6) added
+    from `partial_sums` over a partition of the template rows, in block order,
+    and the update taken by `update_from_totals`.  `map_partials(fn, args)`
+    evaluates fn(args[b]) = partial_sums(Y, X, desc, prm, row_blocks[b]) for
+    every block; the builtin map runs them in turn, a process pool's map runs
+    them in parallel with the same result.  Returns R, t, s and the template,
+    composed as in `register`."""
+    X64 = np.asarray(X, dtype=np.float64)
+    Y = np.asarray(Y0, dtype=np.float64).copy()
+    E = prm.E if prm.E > 0 else iterations
+    _, _, eX = cloud_stats(X64)
+    s, R, t = 1.0, np.eye(3), np.zeros(3)
+    for it in range(iterations):
+        parts = list(map_partials(_partials_task, [(Y, X64, desc, prm, rows) for rows in row_blocks]))
+        totals = np.zeros(13)
+        for part in parts:                                          # block order
+            totals = totals + part
+        Ynext, info = update_from_totals(Y, totals, prm, it, E, eX)
+        c, Rinc, mu, dvec = info["c"], info["Rinc"], info["mu"], info["d"]
+        t = c * (t - mu) @ Rinc + mu + dvec
+        R = polar(R @ Rinc)
+        s = c * s
+        Y = Ynext
+    return dict(R=R, t=t, s=s, Y=Y, iterations=iterations, E=E)
+
+
+def _partials_task(args):
+    Y, X, desc, prm, rows = args
+    return partial_sums(Y, X, desc, prm, rows)
+
+
 def register(X, Y0, prm: Params | None = None, iterations: int = 100, desc=None,
              keep_history: bool = False, record_forces_at=()):
     """Run the method: descriptors once (R14), then `iterations` updates.

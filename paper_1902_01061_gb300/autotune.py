@@ -115,41 +115,40 @@ def tune_single(ctx, n: int, m: int, p: float, candidates=None, reps: int = 3, s
 
 
 def tune_batch(ctx, ref_off, ref_xyz, tmp_off, tmp_xyz, p: float, iterations: int = 3, store: bool = True) -> dict:
-    """Time scgr_batch_run for each work-item chunk length; leave the best."""
+    """Time scgr_batch_run for each work-item chunk length and points per
+    thread, then the best of those with the persistent force kernel (and, for
+    p = 2, with the rsqrt distance form); leave the best."""
     import numpy as np
     import torch
     ro = np.asarray(ref_off, dtype=np.int64)
     to = np.asarray(tmp_off, dtype=np.int64)
     work = int(np.sum(np.diff(ro) * np.diff(to)))
-    results = []
-    for P in BATCH_P:
-        for ct in BATCH_CHUNKS:
-            scgr.scgr_set_tuning(ctx, scgr.SCGR_TUNE_BATCH_P, P)
-            scgr.scgr_set_tuning(ctx, scgr.SCGR_TUNE_BATCH_CHUNK_TILES, ct)
-            scgr.scgr_batch_run(ctx, ro, ref_xyz, to, tmp_xyz, 1)           # warm
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            scgr.scgr_batch_run(ctx, ro, ref_xyz, to, tmp_xyz, iterations)
-            results.append((time.perf_counter() - t0, ct, P))
-    results = [(t, c, q, 0) for t, c, q in results]
-    results.sort()
-    if float(p) == 2.0:
-        _, ct, P, _ = results[0]
+
+    def timed(ct, P, rsq, pers):
         scgr.scgr_set_tuning(ctx, scgr.SCGR_TUNE_BATCH_P, P)
         scgr.scgr_set_tuning(ctx, scgr.SCGR_TUNE_BATCH_CHUNK_TILES, ct)
-        scgr.scgr_set_tuning(ctx, scgr.SCGR_TUNE_FORCE_RSQRT, 1)
-        scgr.scgr_batch_run(ctx, ro, ref_xyz, to, tmp_xyz, 1)
+        scgr.scgr_set_tuning(ctx, scgr.SCGR_TUNE_FORCE_RSQRT, rsq)
+        scgr.scgr_set_tuning(ctx, scgr.SCGR_TUNE_BATCH_PERSISTENT, pers)
+        scgr.scgr_batch_run(ctx, ro, ref_xyz, to, tmp_xyz, 1)           # warm
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         scgr.scgr_batch_run(ctx, ro, ref_xyz, to, tmp_xyz, iterations)
-        results.append((time.perf_counter() - t0, ct, P, 1))
-        results.sort()
-    best_s, ct, P, rsq = results[0]
+        return (time.perf_counter() - t0, ct, P, rsq, pers)
+
+    results = [timed(ct, P, 0, 0) for P in BATCH_P for ct in BATCH_CHUNKS]
+    results.sort()
+    _, ct, P, _, _ = results[0]
+    results.append(timed(ct, P, 0, 1))
+    if float(p) == 2.0:
+        results.append(timed(ct, P, 1, 0))
+    results.sort()
+    best_s, ct, P, rsq, pers = results[0]
     scgr.scgr_set_tuning(ctx, scgr.SCGR_TUNE_BATCH_P, P)
     scgr.scgr_set_tuning(ctx, scgr.SCGR_TUNE_BATCH_CHUNK_TILES, ct)
     scgr.scgr_set_tuning(ctx, scgr.SCGR_TUNE_FORCE_RSQRT, rsq)
-    best = {"chunk_tiles": ct, "P": P, "rsqrt": rsq, "s": best_s, "iterations": iterations,
-            "tried": [{"chunk_tiles": c, "P": q, "rsqrt": r, "s": t} for t, c, q, r in results],
+    scgr.scgr_set_tuning(ctx, scgr.SCGR_TUNE_BATCH_PERSISTENT, pers)
+    best = {"chunk_tiles": ct, "P": P, "rsqrt": rsq, "persistent": pers, "s": best_s, "iterations": iterations,
+            "tried": [{"chunk_tiles": c, "P": q, "rsqrt": r, "persistent": e, "s": t} for t, c, q, r, e in results],
             "when": time.strftime("%Y-%m-%d %H:%M:%S")}
     if store:
         _store(batch_key(gpu_name(), len(ro) - 1, work, p), best)
@@ -169,4 +168,5 @@ def apply_cached_batch(ctx, npairs: int, work: int, p: float) -> dict | None:
         scgr.scgr_set_tuning(ctx, scgr.SCGR_TUNE_BATCH_CHUNK_TILES, hit["chunk_tiles"])
         scgr.scgr_set_tuning(ctx, scgr.SCGR_TUNE_BATCH_P, hit.get("P", 1))
         scgr.scgr_set_tuning(ctx, scgr.SCGR_TUNE_FORCE_RSQRT, hit.get("rsqrt", 0))
+        scgr.scgr_set_tuning(ctx, scgr.SCGR_TUNE_BATCH_PERSISTENT, hit.get("persistent", 0))
     return hit

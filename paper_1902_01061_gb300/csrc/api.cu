@@ -92,7 +92,7 @@ void scgr_destroy(scgr_ctx* c) {
                     &c->aY32, &c->Xr, &c->XA, &c->Y0r, &c->partial, &c->blockpart, &c->moved_stage,
                     &c->bX4, &c->bY4, &c->bknnX, &c->bknnY, &c->baX64, &c->baY64, &c->baX32, &c->baY32,
                     &c->bXr, &c->bXA, &c->bY0r, &c->bpartial, &c->bblockpart, &c->bpairs, &c->bitems,
-                    &c->bcpair, &c->btabX, &c->btabY, &c->bxoff, &c->byoff, &c->bstats, &c->bposes,
+                    &c->bcpair, &c->btabX, &c->btabY, &c->bxoff, &c->byoff, &c->bstats, &c->bposes, &c->bnext,
                     &c->gcell, &c->gcount, &c->gstart, &c->gcursor, &c->gblock, &c->gsorted, &c->gsidx, &c->gbb,
                     &c->cd_key, &c->cd_moved, &c->wstore, &c->wupart, &c->wpartial, &c->mpart, &c->mom};
   for (DevBuf* b : bufs) release(*b);
@@ -457,6 +457,11 @@ scgr_status scgr_set_tuning(scgr_ctx* c, int key, int value) {
   if (key == SCGR_TUNE_BATCH_P) {
     if (value != 1 && value != 2) return fail(c, SCGR_ERR_INVALID_ARG, "batch points per thread must be 1 or 2");
     c->batch_P = value;
+    return SCGR_OK;
+  }
+  if (key == SCGR_TUNE_BATCH_PERSISTENT) {
+    if (value != 0 && value != 1) return fail(c, SCGR_ERR_INVALID_ARG, "value must be 0 or 1");
+    c->batch_persistent = value;
     return SCGR_OK;
   }
   if (key == SCGR_TUNE_BATCH_CHUNK_TILES) {

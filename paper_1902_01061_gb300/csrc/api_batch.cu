@@ -100,6 +100,7 @@ scgr_status scgr_batch_run(scgr_ctx* c, int npairs, const int64_t* ref_off, cons
   SCGR_CK(c, ensure(c->byoff, yoff.size() * sizeof(int64_t)));
   SCGR_CK(c, ensure(c->bstats, (size_t)npairs * sizeof(DevStats)));
   SCGR_CK(c, ensure(c->bposes, (size_t)npairs * sizeof(DevPose)));
+  SCGR_CK(c, ensure(c->bnext, sizeof(int)));
   cudaStream_t st = c->stream;
   SCGR_CK(c, cudaMemcpyAsync(c->bpairs.p, pairs.data(), pairs.size() * sizeof(BatchPair), cudaMemcpyHostToDevice, st));
   SCGR_CK(c, cudaMemcpyAsync(c->bitems.p, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice, st));
@@ -134,11 +135,14 @@ scgr_status scgr_batch_run(scgr_ctx* c, int npairs, const int64_t* ref_off, cons
   // ---- iterations: three launches per iteration for all pairs
   StepParams sp = step_params(c);
   const int pmode = (c->prm.p == 1.0) ? 1 : (c->prm.p == 2.0) ? (c->ftune.rsq == 1 ? 4 : 2) : (c->prm.p == 3.0) ? 3 : 0;
+  int pgrid = 0;  // persistent form: one resident block per slot (queried before any capture)
+  if (c->batch_persistent) SCGR_CK(c, force_batch_slots(pmode, c->batch_P, &pgrid));
   auto enqueue = [&](Launch LL) -> scgr_status {
     for (int t = 0; t < iterations; ++t) {
       SCGR_CK(c, launch_force_batch(LL, pmode, c->batch_P, (int)items.size(), (const int4*)c->bitems.p, dpairs,
                                     (const float4*)c->bXr.p, (const float2*)c->bXA.p, (const float4*)c->bY0r.p,
-                                    (const DevPose*)c->bposes.p, c->qexp, (float4*)c->bpartial.p, CT));
+                                    (const DevPose*)c->bposes.p, c->qexp, (float4*)c->bpartial.p, CT, pgrid,
+                                    (int*)c->bnext.p));
       SCGR_CK(c, launch_combine_batch(LL, cb, (const int*)c->bcpair.p, dpairs, (const float4*)c->bpartial.p,
                                       (const float4*)c->bY0r.p, (const double*)c->baY64.p, c->prm.g_mode,
                                       (const DevPose*)c->bposes.p, (double*)c->bblockpart.p));

@@ -301,7 +301,9 @@ cudaError_t launch_combine_moments(Launch L, const double* mom, int m, int mpad,
                                    double* blockpart);
 cudaError_t launch_force_batch(Launch L, int pmode, int P, int nitems, const int4* items, const BatchPair* pairs,
                                const float4* Xr, const float2* XA, const float4* Y0r, const DevPose* poses,
-                               float qexp, float4* partial, int chunk_tiles);
+                               float qexp, float4* partial, int chunk_tiles, int grid, int* next);
+// Resident blocks of the persistent batched force kernel (its `grid`).
+cudaError_t force_batch_slots(int pmode, int P, int* slots);
 cudaError_t launch_combine_batch(Launch L, int nblocks, const int* cpair, const BatchPair* pairs,
                                  const float4* partial, const float4* Y0r, const double* aY64, int g_mode,
                                  const DevPose* poses, double* blockpart);

@@ -74,9 +74,10 @@ struct scgr_ctx {
 
   // batch workspace
   DevBuf bX4, bY4, bknnX, bknnY, baX64, baY64, baX32, baY32, bXr, bXA, bY0r, bpartial, bblockpart,
-      bpairs, bitems, bcpair, btabX, btabY, bxoff, byoff, bstats, bposes;
+      bpairs, bitems, bcpair, btabX, btabY, bxoff, byoff, bstats, bposes, bnext;
   int batch_chunk_tiles = 16;   // reference tiles per batched work item (tunable)
   int batch_P = 1;              // template points per thread in the batched force kernel (tunable)
+  int batch_persistent = 0;     // 1: persistent batched force kernel with a work queue (tunable)
   int64_t knn_grid_min = 65536; // clouds with at least this many points use the grid kNN (tunable)
   ForceTuning ftune;            // force-plan overrides (tunable)
   int reuse_pose_free = 1;      // p = 1: one force pass per scgr_run (tunable)

@@ -122,39 +122,15 @@ __device__ __forceinline__ void pair2(u64 xv, u64 yv, u64 zv, u64 nv, u64 av, u6
   Sz = fma2(w, zv, Sz);
 }
 
-// BATCH = false: one problem, grid (template blocks, reference splits).
-// BATCH = true: one block per work item {pair, template block, reference
-// chunk} of a batch of independent problems (items[], pairs[], one pose per
-// pair); tiles_per_split is then the chunk length in tiles.
-template <int P, int PM, int TPB, int TJ, int MINB, bool BATCH>
-__global__ void __launch_bounds__(TPB, MINB)
-    force_tile_kernel(const float* __restrict__ Xr, const float* __restrict__ XA, int ntiles,
-                      int tiles_per_split, const float4* __restrict__ Y0r, int mpad,
-                      const DevPose* __restrict__ pose, float qexp, float4* __restrict__ partial,
-                      const int4* __restrict__ items, const BatchPair* __restrict__ pairs) {
-  __shared__ __align__(16) float sT[6][TJ];
+// The work of one block: template points [ibase, ibase + P*TPB) of the
+// padded record array against reference tiles [t0, t1), at pose *ps; writes
+// one float4 partial per template point to outbase[0 .. P*TPB).
+template <int P, int PM, int TPB, int TJ>
+__device__ __forceinline__ void force_block(float (&sT)[6][TJ], const float* __restrict__ Xr,
+                                            const float* __restrict__ XA, int t0, int t1,
+                                            const float4* __restrict__ Y0r, int ibase, const DevPose* ps,
+                                            float qexp, float4* __restrict__ outbase) {
   const int tid = threadIdx.x;
-  int ibase, t0, t1;
-  const DevPose* ps;
-  float4* outbase;
-  if (BATCH) {
-    const int4 it = items[blockIdx.x];
-    const BatchPair& bp = pairs[it.x];
-    const int lt0 = it.z * tiles_per_split;
-    const int local = it.y * (TPB * P);
-    t0 = (int)bp.xtile0 + lt0;
-    t1 = (int)bp.xtile0 + min(bp.ntiles, lt0 + tiles_per_split);
-    ibase = (int)bp.ybase + local;
-    ps = pose + it.x;
-    outbase = partial + bp.pbase + (size_t)it.z * bp.mpad + local;
-  } else {
-    ibase = blockIdx.x * (TPB * P);
-    t0 = blockIdx.y * tiles_per_split;
-    t1 = min(ntiles, t0 + tiles_per_split);
-    ps = pose;
-    outbase = partial + (size_t)blockIdx.y * mpad + ibase;
-  }
-
   float A[9], b[3];
 #pragma unroll
   for (int q = 0; q < 9; ++q) A[q] = ps->A[q];
@@ -234,6 +210,78 @@ __global__ void __launch_bounds__(TPB, MINB)
 #pragma unroll
   for (int q = 0; q < P; ++q)
     out[q * TPB] = make_float4(hW[q] - cW[q], hx[q] - cx[q], hy[q] - cy[q], hz[q] - cz[q]);
+}
+
+// Work item {pair, template block, reference chunk} of a batch: the block's
+// template range, tile range, pose and output slot.
+template <int P, int TPB>
+__device__ __forceinline__ void batch_item(const int4 it, const BatchPair* __restrict__ pairs,
+                                           int tiles_per_split, const DevPose* __restrict__ pose,
+                                           float4* __restrict__ partial, int& ibase, int& t0, int& t1,
+                                           const DevPose*& ps, float4*& outbase) {
+  const BatchPair& bp = pairs[it.x];
+  const int lt0 = it.z * tiles_per_split;
+  const int local = it.y * (TPB * P);
+  t0 = (int)bp.xtile0 + lt0;
+  t1 = (int)bp.xtile0 + min(bp.ntiles, lt0 + tiles_per_split);
+  ibase = (int)bp.ybase + local;
+  ps = pose + it.x;
+  outbase = partial + bp.pbase + (size_t)it.z * bp.mpad + local;
+}
+
+// BATCH = false: one problem, grid (template blocks, reference splits).
+// BATCH = true: one block per work item {pair, template block, reference
+// chunk} of a batch of independent problems (items[], pairs[], one pose per
+// pair); tiles_per_split is then the chunk length in tiles.
+template <int P, int PM, int TPB, int TJ, int MINB, bool BATCH>
+__global__ void __launch_bounds__(TPB, MINB)
+    force_tile_kernel(const float* __restrict__ Xr, const float* __restrict__ XA, int ntiles,
+                      int tiles_per_split, const float4* __restrict__ Y0r, int mpad,
+                      const DevPose* __restrict__ pose, float qexp, float4* __restrict__ partial,
+                      const int4* __restrict__ items, const BatchPair* __restrict__ pairs) {
+  __shared__ __align__(16) float sT[6][TJ];
+  int ibase, t0, t1;
+  const DevPose* ps;
+  float4* outbase;
+  if (BATCH) {
+    batch_item<P, TPB>(items[blockIdx.x], pairs, tiles_per_split, pose, partial, ibase, t0, t1, ps, outbase);
+  } else {
+    ibase = blockIdx.x * (TPB * P);
+    t0 = blockIdx.y * tiles_per_split;
+    t1 = min(ntiles, t0 + tiles_per_split);
+    ps = pose;
+    outbase = partial + (size_t)blockIdx.y * mpad + ibase;
+  }
+  force_block<P, PM, TPB, TJ>(sT, Xr, XA, t0, t1, Y0r, ibase, ps, qexp, outbase);
+}
+
+// Persistent form of the batched pass: a grid of resident blocks takes work
+// items from a queue in index order (items are sorted longest first, so the
+// blocks finish close together: greedy longest-processing-time scheduling).
+// *next is the queue head; it must be 0 at launch (the caller clears it).
+// Each item's result depends only on the item, so which block takes it does
+// not change any bit of the output.  No block waits for another.
+template <int P, int PM, int TPB, int TJ, int MINB>
+__global__ void __launch_bounds__(TPB, MINB)
+    force_batch_persistent_kernel(const float* __restrict__ Xr, const float* __restrict__ XA,
+                                  int tiles_per_split, const float4* __restrict__ Y0r,
+                                  const DevPose* __restrict__ pose, float qexp, float4* __restrict__ partial,
+                                  const int4* __restrict__ items, int nitems, const BatchPair* __restrict__ pairs,
+                                  int* __restrict__ next) {
+  __shared__ __align__(16) float sT[6][TJ];
+  __shared__ int s_item;
+  for (;;) {
+    if (threadIdx.x == 0) s_item = atomicAdd(next, 1);
+    __syncthreads();
+    const int item = s_item;
+    if (item >= nitems) break;
+    int ibase, t0, t1;
+    const DevPose* ps;
+    float4* outbase;
+    batch_item<P, TPB>(items[item], pairs, tiles_per_split, pose, partial, ibase, t0, t1, ps, outbase);
+    force_block<P, PM, TPB, TJ>(sT, Xr, XA, t0, t1, Y0r, ibase, ps, qexp, outbase);
+    __syncthreads();  // every thread has read s_item before thread 0 takes the next one
+  }
 }
 
 // ---- planning --------------------------------------------------------------
@@ -389,34 +437,75 @@ cudaError_t launch_force(Launch L, const ForcePlan& fp, const float4* Xr, const 
   return cudaGetLastError();
 }
 
-// Batched force pass: one block of 128 threads (P template points each) per item.
+// Batched force pass, 128 threads (P template points each) per block: one
+// block per item (grid == 0), or a persistent grid of `grid` resident blocks
+// taking items from the queue head *next, which is cleared first.
+template <int P, int PM>
+static void launch_force_batch_p(cudaStream_t st, int nitems, const int4* items, const BatchPair* pairs,
+                                 const float4* Xr, const float2* XA, const float4* Y0r, const DevPose* poses,
+                                 float qexp, float4* partial, int chunk_tiles, int grid, int* next) {
+  const float* xr = reinterpret_cast<const float*>(Xr);
+  const float* xa = reinterpret_cast<const float*>(XA);
+  if (grid <= 0)
+    force_tile_kernel<P, PM, 128, FORCE_TJ, 2, true><<<nitems, 128, 0, st>>>(xr, xa, 0, chunk_tiles, Y0r, 0, poses,
+                                                                             qexp, partial, items, pairs);
+  else
+    force_batch_persistent_kernel<P, PM, 128, FORCE_TJ, 2><<<grid < nitems ? grid : nitems, 128, 0, st>>>(
+        xr, xa, chunk_tiles, Y0r, poses, qexp, partial, items, nitems, pairs, next);
+}
+
 template <int PM>
 static void launch_force_batch_pm(cudaStream_t st, int P, int nitems, const int4* items, const BatchPair* pairs,
                                   const float4* Xr, const float2* XA, const float4* Y0r, const DevPose* poses,
-                                  float qexp, float4* partial, int chunk_tiles) {
+                                  float qexp, float4* partial, int chunk_tiles, int grid, int* next) {
   if (P == 2)
-    force_tile_kernel<2, PM, 128, FORCE_TJ, 2, true><<<nitems, 128, 0, st>>>(
-        reinterpret_cast<const float*>(Xr), reinterpret_cast<const float*>(XA), 0, chunk_tiles, Y0r, 0, poses, qexp,
-        partial, items, pairs);
+    launch_force_batch_p<2, PM>(st, nitems, items, pairs, Xr, XA, Y0r, poses, qexp, partial, chunk_tiles, grid, next);
   else
-    force_tile_kernel<1, PM, 128, FORCE_TJ, 2, true><<<nitems, 128, 0, st>>>(
-        reinterpret_cast<const float*>(Xr), reinterpret_cast<const float*>(XA), 0, chunk_tiles, Y0r, 0, poses, qexp,
-        partial, items, pairs);
+    launch_force_batch_p<1, PM>(st, nitems, items, pairs, Xr, XA, Y0r, poses, qexp, partial, chunk_tiles, grid, next);
 }
 
 cudaError_t launch_force_batch(Launch L, int pmode, int P, int nitems, const int4* items, const BatchPair* pairs,
                                const float4* Xr, const float2* XA, const float4* Y0r, const DevPose* poses,
-                               float qexp, float4* partial, int chunk_tiles) {
+                               float qexp, float4* partial, int chunk_tiles, int grid, int* next) {
   if (nitems <= 0) return cudaSuccess;
+  if (grid > 0) {
+    if (!next) return cudaErrorInvalidValue;
+    const cudaError_t e = cudaMemsetAsync(next, 0, sizeof(int), L.stream);
+    if (e != cudaSuccess) return e;
+  }
   switch (pmode) {
-    case 1: launch_force_batch_pm<1>(L.stream, P, nitems, items, pairs, Xr, XA, Y0r, poses, qexp, partial, chunk_tiles); break;
-    case 2: launch_force_batch_pm<2>(L.stream, P, nitems, items, pairs, Xr, XA, Y0r, poses, qexp, partial, chunk_tiles); break;
-    case 3: launch_force_batch_pm<3>(L.stream, P, nitems, items, pairs, Xr, XA, Y0r, poses, qexp, partial, chunk_tiles); break;
-    case 4: launch_force_batch_pm<4>(L.stream, P, nitems, items, pairs, Xr, XA, Y0r, poses, qexp, partial, chunk_tiles); break;
-    default: launch_force_batch_pm<0>(L.stream, P, nitems, items, pairs, Xr, XA, Y0r, poses, qexp, partial, chunk_tiles); break;
+    case 1: launch_force_batch_pm<1>(L.stream, P, nitems, items, pairs, Xr, XA, Y0r, poses, qexp, partial, chunk_tiles, grid, next); break;
+    case 2: launch_force_batch_pm<2>(L.stream, P, nitems, items, pairs, Xr, XA, Y0r, poses, qexp, partial, chunk_tiles, grid, next); break;
+    case 3: launch_force_batch_pm<3>(L.stream, P, nitems, items, pairs, Xr, XA, Y0r, poses, qexp, partial, chunk_tiles, grid, next); break;
+    case 4: launch_force_batch_pm<4>(L.stream, P, nitems, items, pairs, Xr, XA, Y0r, poses, qexp, partial, chunk_tiles, grid, next); break;
+    default: launch_force_batch_pm<0>(L.stream, P, nitems, items, pairs, Xr, XA, Y0r, poses, qexp, partial, chunk_tiles, grid, next); break;
   }
   if (L.counter) ++*L.counter;
   return cudaGetLastError();
+}
+
+// Resident blocks of the persistent batched force kernel on the current device.
+template <int PM>
+static cudaError_t batch_slots_pm(int P, int* slots) {
+  int dev = 0, sms = 0, nb = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess)
+    e = P == 2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, force_batch_persistent_kernel<2, PM, 128, FORCE_TJ, 2>, 128, 0)
+               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, force_batch_persistent_kernel<1, PM, 128, FORCE_TJ, 2>, 128, 0);
+  if (e != cudaSuccess) return e;
+  *slots = sms * (nb > 0 ? nb : 1);
+  return cudaSuccess;
+}
+
+cudaError_t force_batch_slots(int pmode, int P, int* slots) {
+  switch (pmode) {
+    case 1: return batch_slots_pm<1>(P, slots);
+    case 2: return batch_slots_pm<2>(P, slots);
+    case 3: return batch_slots_pm<3>(P, slots);
+    case 4: return batch_slots_pm<4>(P, slots);
+    default: return batch_slots_pm<0>(P, slots);
+  }
 }
 
 // ---- p = 3: moments of the pair weights over the reference ------------------

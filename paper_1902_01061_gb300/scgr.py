@@ -41,6 +41,7 @@ SCGR_TUNE_FORCE_SPLITS = 5
 SCGR_TUNE_REUSE_POSE_FREE = 6
 SCGR_TUNE_FORCE_OCC = 7
 SCGR_TUNE_BATCH_P = 8
+SCGR_TUNE_BATCH_PERSISTENT = 10
 SCGR_TUNE_FORCE_RSQRT = 9
 
 

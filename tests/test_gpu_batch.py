@@ -9,7 +9,7 @@ import torch
 
 import oracle as O
 from paper_1902_01061_gb300 import scgr, synth
-from tests.gpu_helpers import Gpu, rot_err_deg
+from tests.gpu_helpers import Gpu, check, pose_errors
 
 pytestmark = pytest.mark.gpu
 
@@ -35,9 +35,11 @@ def make_pairs(sizes, seed=5):
     return out
 
 
-def run_batch(pairs, iters, **prm):
+def run_batch(pairs, iters, tuning=(), **prm):
     ctx = scgr.scgr_create(scgr.scgr_default_params(**prm))
     try:
+        for key, value in tuning:
+            scgr.scgr_set_tuning(ctx, key, value)
         ro = np.cumsum([0] + [len(x) for x, _ in pairs])
         to = np.cumsum([0] + [len(y) for _, y in pairs])
         Xc = torch.from_numpy(np.concatenate([x for x, _ in pairs])).cuda()
@@ -49,10 +51,15 @@ def run_batch(pairs, iters, **prm):
     return res, launches
 
 
-def close(a, b, diag, rot=0.5, t=1e-3, s=1e-5):
+def close(a, b, diag, what, rot=0.5, t=1e-3, s=1e-5):
+    """the pose tolerances, each error recorded by check()"""
     Ra, ta, sa = a.as_numpy()
     Rb, tb, sb = b.as_numpy() if hasattr(b, "as_numpy") else b
-    return rot_err_deg(Ra, Rb) <= rot and np.linalg.norm(ta - tb) <= t * diag and abs(sa - sb) <= s * abs(sb)
+    er, et, es = pose_errors(Ra, ta, sa, Rb, tb, sb, diag)
+    check(f"{what}: rotation (deg)", er, rot)
+    check(f"{what}: translation / bbox diagonal", et, t)
+    check(f"{what}: scale (relative)", es, s)
+    return True
 
 
 @pytest.mark.parametrize("p", [2.0, 1.0])
@@ -65,7 +72,7 @@ def test_batch_matches_single_pair_runs(p):
         with Gpu(X, Y, p=p) as g:
             single = g.run(iters)
         assert r.iterations == iters
-        assert close(r, single, synth.bbox_diag(X)), (r.as_numpy(), single.as_numpy())
+        assert close(r, single, synth.bbox_diag(X), f"batched vs one call per pair (p={p:g})")
 
 
 def test_one_pair_batch_matches_single_run():
@@ -74,7 +81,7 @@ def test_one_pair_batch_matches_single_run():
     X, Y = pairs[0]
     with Gpu(X, Y, p=2.0) as g:
         single = g.run(20)
-    assert len(res) == 1 and close(res[0], single, synth.bbox_diag(X))
+    assert len(res) == 1 and close(res[0], single, synth.bbox_diag(X), "one-pair batch vs single run")
 
 
 def test_batch_matches_oracle_on_small_pairs():
@@ -83,13 +90,29 @@ def test_batch_matches_oracle_on_small_pairs():
     res, _ = run_batch(pairs, iters)
     for (X, Y), r in zip(pairs, res):
         o = O.register(X, Y, O.Params(), iterations=iters)
-        assert close(r, (o["R"], o["t"], o["s"]), synth.bbox_diag(X))
+        assert close(r, (o["R"], o["t"], o["s"]), synth.bbox_diag(X), "batched pose vs oracle")
 
 
 def test_batch_graph_replay_equals_eager():
     pairs = make_pairs([400, 1200, 33, 800], seed=13)
     a, la = run_batch(pairs, 15)
     b, lb = run_batch(pairs, 15, use_graph=1)
+    assert la == lb
+    for ra, rb in zip(a, b):
+        assert list(ra.R) == list(rb.R) and list(ra.t) == list(rb.t) and ra.s == rb.s
+
+
+@pytest.mark.parametrize("P,chunk,use_graph", [(1, 16, 0), (2, 3, 1), (2, 16, 1)])
+def test_persistent_batch_kernel_is_bit_identical(P, chunk, use_graph):
+    """The persistent batched force kernel (resident blocks taking work items
+    from a queue) gives every pair the same bits as one block per item: an
+    item's sums do not depend on which block takes it.  Uneven sizes, many
+    more items than resident blocks in the chunk-3 case, and graph replay
+    (the queue head is cleared before every launch)."""
+    pairs = make_pairs([2600, 257, 16, 1900, 700, 3100, 90], seed=29)
+    base = ((scgr.SCGR_TUNE_BATCH_P, P), (scgr.SCGR_TUNE_BATCH_CHUNK_TILES, chunk))
+    a, la = run_batch(pairs, 12, tuning=base, p=2.0, use_graph=use_graph)
+    b, lb = run_batch(pairs, 12, tuning=base + ((scgr.SCGR_TUNE_BATCH_PERSISTENT, 1),), p=2.0, use_graph=use_graph)
     assert la == lb
     for ra, rb in zip(a, b):
         assert list(ra.R) == list(rb.R) and list(ra.t) == list(rb.t) and ra.s == rb.s
@@ -112,7 +135,7 @@ def test_batch_chunk_tuning_keeps_results_close():
     finally:
         scgr.scgr_destroy(ctx)
     for (X, _), ra, rb in zip(pairs, a, b):
-        assert close(ra, rb, synth.bbox_diag(X))
+        assert close(ra, rb, synth.bbox_diag(X), "batched, chunk 3 / P 2 / rsqrt vs defaults")
 
 
 def test_batch_rejects_bad_offsets():

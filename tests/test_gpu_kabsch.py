@@ -8,7 +8,7 @@ import pytest
 
 import oracle as O
 from paper_1902_01061_gb300 import scgr, synth
-from tests.gpu_helpers import Gpu
+from tests.gpu_helpers import Gpu, check
 
 pytestmark = pytest.mark.gpu
 
@@ -62,6 +62,7 @@ def test_step_from_totals_matches_oracle(kind):
         moved = g.moved()
     t_ref = -info["c"] * info["mu"] @ info["Rinc"] + info["mu"] + info["d"]
     np.testing.assert_allclose(R, info["Rinc"], atol=1e-9)
+    check(f"Kabsch step ({kind}): max |R - R_oracle|", np.abs(R - info["Rinc"]).max(), 1e-9)
     assert abs(np.linalg.det(R) - 1.0) <= 1e-12
     np.testing.assert_allclose(R.T @ R, np.eye(3), atol=1e-13)
     assert s == pytest.approx(info["c"], rel=1e-10)

@@ -6,7 +6,7 @@ import pytest
 
 import oracle as O
 from paper_1902_01061_gb300 import scgr, synth
-from tests.gpu_helpers import Gpu, rot_err_deg
+from tests.gpu_helpers import Gpu, check, check_pose
 
 pytestmark = pytest.mark.gpu
 
@@ -16,10 +16,10 @@ def _lib(scgr_lib):
     return scgr_lib
 
 
-def pose_close(res, o, diag):
+def pose_close(res, o, diag, what):
     R, t, s = res.as_numpy()
-    return (rot_err_deg(R, o["R"]) <= 0.5 and np.linalg.norm(t - o["t"]) <= 1e-3 * diag
-            and abs(s - o["s"]) <= 1e-5 * o["s"])
+    check_pose(what, R, t, s, o["R"], o["t"], o["s"], diag)
+    return True
 
 
 @pytest.mark.parametrize("scale", [1.0, 0.35])
@@ -27,7 +27,11 @@ def test_radius_curvature_matches_oracle(scale):
     case = synth.mild(n=1500)
     with Gpu(case.X, case.Y0, neigh_mode=1, radius_scale=scale) as g:
         for which, P in ((0, case.X), (1, case.Y0)):
-            np.testing.assert_allclose(g.curv64(which), O.curvature_radius(P, scale), rtol=1e-5, atol=1e-10)
+            a_ref = O.curvature_radius(P, scale)
+            a_got = g.curv64(which)
+            np.testing.assert_allclose(a_got, a_ref, rtol=1e-5, atol=1e-10)
+            check("radius curvature: max |da| / (|a| + 1e-5)", np.max(np.abs(a_got - a_ref) / (np.abs(a_ref) + 1e-5)),
+                  1e-5)
         assert g.sigma() == pytest.approx(O.sigma_auto(O.curvature_radius(case.X, scale)), rel=1e-5)
 
 
@@ -36,7 +40,7 @@ def test_radius_mode_registration_matches_oracle():
     prm = O.Params(neigh_mode=1, radius_scale=0.4)
     o = O.register(case.X, case.Y0, prm, iterations=20)
     with Gpu(case.X, case.Y0, neigh_mode=1, radius_scale=0.4) as g:
-        assert pose_close(g.run(20), o, synth.bbox_diag(case.X))
+        assert pose_close(g.run(20), o, synth.bbox_diag(case.X), "pose, radius neighbourhood")
 
 
 @pytest.mark.parametrize("mode", [0, 1])
@@ -51,7 +55,7 @@ def test_pyramid_matches_oracle(mode):
     with Gpu(case.X, case.Y0, neigh_mode=mode, E=30) as g:
         res = scgr.run_pyramid(g.ctx, levels)
     assert res.iterations == 30
-    assert pose_close(res, o, synth.bbox_diag(case.X))
+    assert pose_close(res, o, synth.bbox_diag(case.X), f"pose, pyramidal schedule (mode {mode})")
 
 
 def test_set_neighbourhood_rejects_bad_values():

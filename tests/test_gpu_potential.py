@@ -9,7 +9,7 @@ import torch
 
 import oracle as O
 from paper_1902_01061_gb300 import scgr, synth
-from tests.gpu_helpers import Gpu, rel_l2
+from tests.gpu_helpers import Gpu, check, rel_l2
 
 pytestmark = pytest.mark.gpu
 
@@ -42,9 +42,9 @@ def test_potential_and_adjoint_match_oracle_analytic(p):
             gx = torch.empty((g.m, 3), dtype=torch.float32, device="cuda")
             U, g7 = scgr.scgr_potential(g.ctx, pose, want_grad=True, grad_xyz_out=gx)
             Uo, g7o, gY0o = O.pose_potential_and_grad(pose, case.Y0, case.X, d["aY"], d["aX"], d["sigma"], p, 1)
-            assert abs(U - Uo) <= 1e-6 * abs(Uo)
-            assert max(block_rel(g7, g7o)) <= 1e-4, (block_rel(g7, g7o))
-            assert rel_l2(gx.cpu().numpy(), gY0o) <= 1e-5
+            check(f"potential U (p={p:g}): relative error", abs(U - Uo) / abs(Uo), 1e-6)
+            check(f"pose gradient (p={p:g}) vs oracle: worst block relative L2", max(block_rel(g7, g7o)), 1e-4)
+            check(f"template-point gradient (p={p:g}) vs oracle: relative L2", rel_l2(gx.cpu().numpy(), gY0o), 1e-5)
             U2, none = scgr.scgr_potential(g.ctx, pose, want_grad=False)
             assert U2 == U and none is None
 
@@ -68,7 +68,7 @@ def test_adjoint_matches_central_differences_of_oracle_potential():
         fd[q] = (Up - Um) / (2 * h)
     with Gpu(X, Y0, p=p) as g:
         _, g7 = scgr.scgr_potential(g.ctx, pose)
-    assert max(block_rel(g7, fd)) <= 1e-4, block_rel(g7, fd)
+    check("pose gradient vs central differences (h = 1e-4): worst block relative L2", max(block_rel(g7, fd)), 1e-4)
 
 
 def test_autograd_function_backward():
@@ -81,9 +81,9 @@ def test_autograd_function_backward():
         U = scgr.potential(pose, Y0, g.ctx)
         (3.0 * U).backward()
         Uo, g7o, gY0o = O.pose_potential_and_grad(POSES[0], case.Y0, case.X, d["aY"], d["aX"], d["sigma"], p, 1)
-        assert abs(U.item() - Uo) <= 1e-6 * abs(Uo)
-        assert max(block_rel(pose.grad.numpy(), 3.0 * g7o)) <= 1e-4
-        assert rel_l2(Y0.grad.cpu().numpy(), 3.0 * gY0o) <= 1e-5
+        check("autograd potential: relative error", abs(U.item() - Uo) / abs(Uo), 1e-6)
+        check("autograd pose gradient: worst block relative L2", max(block_rel(pose.grad.numpy(), 3.0 * g7o)), 1e-4)
+        check("autograd template-point gradient: relative L2", rel_l2(Y0.grad.cpu().numpy(), 3.0 * gY0o), 1e-5)
 
 
 def test_full_size_50k_sampled_rows_and_identities():
@@ -105,9 +105,9 @@ def test_full_size_50k_sampled_rows_and_identities():
         f4 = g.forces()
     rows = np.sort(rng.choice(len(dc.Y0), size=64, replace=False))
     fr, _ = O.forces_rows(dc.Y0, dc.X, aY, aX, sigma, p, 1, rows)
-    assert rel_l2(gx.cpu().numpy()[rows], -fr) <= 1e-5
+    check("template-point gradient, 50k x 50k sampled rows: relative L2", rel_l2(gx.cpu().numpy()[rows], -fr), 1e-5)
     F = f4[:, :3].astype(np.float64).sum(axis=0)
-    assert rel_l2(g7[3:6], -F) <= 1e-5
+    check("dU/dt + F, 50k x 50k: relative L2", rel_l2(g7[3:6], -F), 1e-5)
     assert U > 0 and np.isfinite(g7).all()
 
 
@@ -121,7 +121,7 @@ def test_force_vjp_matches_oracle(p):
         out = torch.empty((g.m, 3), dtype=torch.float32, device="cuda")
         scgr.scgr_force_vjp(g.ctx, torch.from_numpy(v).cuda(), out)
         got = out.cpu().numpy()
-    assert rel_l2(got, ref) <= 1e-5
+    check(f"force VJP (p={p:g}) vs oracle: relative L2", rel_l2(got, ref), 1e-5)
 
 
 @pytest.mark.parametrize("p", [2.0, 1.0])
@@ -135,6 +135,9 @@ def test_stored_pair_terms_match_recomputation(p):
         U_r, g_r = scgr.scgr_potential(g.ctx, pose, grad_xyz_out=gx_r)
         U_s, g_s = scgr.scgr_potential_stored(g.ctx, pose, grad_xyz_out=gx_s)
     Uo, g7o, gY0o = O.pose_potential_and_grad(pose, case.Y0, case.X, d["aY"], d["aX"], d["sigma"], p, 1)
-    assert abs(U_s - Uo) <= 1e-6 * abs(Uo) and abs(U_r - Uo) <= 1e-6 * abs(Uo)
-    assert max(block_rel(g_s, g7o)) <= 1e-4 and max(block_rel(g_r, g7o)) <= 1e-4
-    assert rel_l2(gx_s.cpu().numpy(), gY0o) <= 1e-5
+    check(f"potential, stored pair terms (p={p:g}): relative error", abs(U_s - Uo) / abs(Uo), 1e-6)
+    check(f"potential, recomputed tiles (p={p:g}): relative error", abs(U_r - Uo) / abs(Uo), 1e-6)
+    check(f"pose gradient, stored pair terms (p={p:g}): worst block relative L2", max(block_rel(g_s, g7o)), 1e-4)
+    check(f"pose gradient, recomputed tiles (p={p:g}): worst block relative L2", max(block_rel(g_r, g7o)), 1e-4)
+    check(f"template-point gradient, stored pair terms (p={p:g}): relative L2",
+          rel_l2(gx_s.cpu().numpy(), gY0o), 1e-5)

@@ -2,12 +2,11 @@
 template rows (two ranks emulated in one process; the host adds their
 partial sums in rank order), and the result equals the unsharded run within
 the pose tolerance while both "ranks" hold identical poses."""
-import numpy as np
 import pytest
 import torch
 
 from paper_1902_01061_gb300 import scgr, shard, synth
-from tests.gpu_helpers import Gpu, rot_err_deg
+from tests.gpu_helpers import Gpu, check_pose
 
 pytestmark = pytest.mark.gpu
 
@@ -40,7 +39,7 @@ def test_two_row_shards_match_unsharded_run():
     Ra, ta, sa = a.as_numpy()
     Rr, tr, sr = ref.as_numpy()
     diag = synth.bbox_diag(case.X)
-    assert rot_err_deg(Ra, Rr) <= 0.5 and np.linalg.norm(ta - tr) <= 1e-3 * diag and abs(sa - sr) <= 1e-5 * sr
+    check_pose("two row shards vs unsharded", Ra, ta, sa, Rr, tr, sr, diag)
 
 
 def test_row_range_guards():

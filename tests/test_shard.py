@@ -95,3 +95,18 @@ def test_two_gloo_ranks_match_single_rank():
     case = synth.mild(n=300)
     ref = O.register(case.X, case.Y0, O.Params(E=iters), iterations=iters)
     np.testing.assert_allclose(out[0], ref["Y"], atol=1e-10)
+
+
+def test_register_from_partials_equals_register():
+    """The row-block form of the iteration (used to spread the oracle's force
+    pass over a process pool) gives the pose of the plain iteration."""
+    case = synth.mild(n=400)
+    prm = O.Params(p=2.0)
+    desc = O.descriptors(case.X, case.Y0, prm)
+    a = O.register(case.X, case.Y0, prm, iterations=15, desc=desc)
+    blocks = np.array_split(np.arange(len(case.Y0)), 3)
+    b = O.register_from_partials(case.X, case.Y0, prm, 15, desc, blocks)
+    np.testing.assert_allclose(b["R"], a["R"], atol=1e-11)
+    np.testing.assert_allclose(b["t"], a["t"], atol=1e-11)
+    assert abs(b["s"] - a["s"]) <= 1e-12 * a["s"]
+    np.testing.assert_allclose(b["Y"], a["Y"], atol=1e-10)
