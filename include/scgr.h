@@ -321,9 +321,16 @@ SCGR_EXPORT scgr_status scgr_step_apply(scgr_ctx* ctx, const double tot13[13]);
 #define SCGR_TUNE_FORCE_P 3           /* force kernel template points per thread: 0 auto, 1, 2, 4 */
 #define SCGR_TUNE_FORCE_TPB 4         /* force kernel threads per block: 0 auto, 128, 256 */
 #define SCGR_TUNE_FORCE_SPLITS 5      /* force kernel reference splits: 0 auto (wave-filling), >= 1 */
-#define SCGR_TUNE_BATCH_P 8           /* template points per thread in the batched force kernel: 1 (default), 2 */
-#define SCGR_TUNE_FORCE_OCC 7         /* 1: force kernel variant with a tighter register budget and more
-                                         resident blocks per SM (3 at 256 threads, 4 at 128); 0 default */
+#define SCGR_TUNE_BATCH_P 8           /* template points per thread in the batched force kernel: 1 (default),
+                                         2, or 4 (running sums in shared memory; each pair's template is
+                                         then padded to a multiple of 512 points) */
+#define SCGR_TUNE_FORCE_OCC 7         /* force kernel variant: 0 registers only, 2 resident blocks per SM;
+                                         1 a tighter register budget and more resident blocks per SM (3 at
+                                         256 threads, 4 at 128); 2 the per-point running sums in shared
+                                         memory and 512 reference points staged per step (for 4 points x
+                                         128 threads, 3 blocks per SM, and 2 points x 256 threads; other
+                                         shapes use 0).  Until set: 2 for the 4 x 128 shape that templates
+                                         of >= 311,296 points get (152 SMs), else 0 */
 #define SCGR_TUNE_FORCE_RSQRT 9       /* p = 2 distance factor d = sqrt(d^2): 0 automatic (the square
                                          root), 1 d^2 * rsqrt(d^2), 2 the square root; all-pairs and
                                          batched force kernels; results agree to rounding.  On GB300

@@ -17,9 +17,9 @@ import time
 from . import scgr
 
 SINGLE_CANDIDATES = [(P, tpb, occ) for P in (1, 2, 4) for tpb in (128, 256) for occ in (0, 1)
-                     if not (P == 4 and tpb == 256 and occ == 1)]
+                     if not (P == 4 and tpb == 256 and occ == 1)] + [(4, 128, 2), (2, 256, 2)]
 BATCH_CHUNKS = (8, 16, 32)
-BATCH_P = (1, 2)
+BATCH_P = (1, 2, 4)
 
 
 def cache_path() -> str:

@@ -429,7 +429,7 @@ scgr_status scgr_set_tuning(scgr_ctx* c, int key, int value) {
     return c->have_desc ? replan(c) : SCGR_OK;
   }
   if (key == SCGR_TUNE_FORCE_OCC) {
-    if (value != 0 && value != 1) return fail(c, SCGR_ERR_INVALID_ARG, "occupancy variant must be 0 or 1");
+    if (value < 0 || value > 2) return fail(c, SCGR_ERR_INVALID_ARG, "occupancy variant must be 0, 1 or 2");
     c->ftune.occ = value;
     return c->have_desc ? replan(c) : SCGR_OK;
   }
@@ -455,7 +455,8 @@ scgr_status scgr_set_tuning(scgr_ctx* c, int key, int value) {
     return SCGR_OK;
   }
   if (key == SCGR_TUNE_BATCH_P) {
-    if (value != 1 && value != 2) return fail(c, SCGR_ERR_INVALID_ARG, "batch points per thread must be 1 or 2");
+    if (value != 1 && value != 2 && value != 4)
+      return fail(c, SCGR_ERR_INVALID_ARG, "batch points per thread must be 1, 2 or 4");
     c->batch_P = value;
     return SCGR_OK;
   }

@@ -50,7 +50,8 @@ scgr_status scgr_batch_run(scgr_ctx* c, int npairs, const int64_t* ref_off, cons
     bp.ntiles = (int)((bp.n + FORCE_TJ - 1) / FORCE_TJ);
     bp.xtile0 = xt;
     xt += bp.ntiles;
-    bp.mpad = (bp.m + 255) / 256 * 256;
+    const int64_t round = FB > 256 ? FB : 256;  // whole force blocks and combine blocks
+    bp.mpad = (bp.m + round - 1) / round * round;
     bp.ybase = yb;
     yb += bp.mpad;
     bp.chunks = (bp.ntiles + CT - 1) / CT;

@@ -265,7 +265,8 @@ struct ForcePlan {
   int splits;     // reference-range splits (grid.y)
   int tiles_per_split;
   int iblocks;    // grid.x
-  int occ;        // 0: >= 2 resident blocks per SM; 1: more (3 for 256 threads and P <= 2, 4 for 128 threads)
+  int occ;        // 0: >= 2 resident blocks per SM; 1: more (3 for 256 threads and P <= 2, 4 for 128 threads);
+                  // 2: running sums in shared memory, 2 record tiles per stage (P = 4 x 128, P = 2 x 256)
 };
 
 // Overrides of the force plan (0: automatic), set by the autotuner.
@@ -273,7 +274,8 @@ struct ForceTuning {
   int P = 0;       // template points per thread: 1, 2 or 4
   int tpb = 0;     // threads per block: 128 or 256
   int splits = 0;  // reference splits
-  int occ = 0;     // 1: the higher-occupancy variant (tighter register budget)
+  int occ = -1;    // -1 automatic; 0 default; 1 the higher-occupancy variant (tighter register budget);
+                   // 2 shared-memory sums
   int rsq = 0;     // p = 2 distance factor: 0 / 2 sqrt, 1 d^2 * rsqrt(d^2)
 };
 

@@ -122,11 +122,64 @@ __device__ __forceinline__ void pair2(u64 xv, u64 yv, u64 zv, u64 nv, u64 av, u6
   Sz = fma2(w, zv, Sz);
 }
 
+// Running per-point sums of the force kernel and their Kahan compensations:
+// in registers (KS = false) or in shared memory (KS = true, which frees 8
+// registers per template point for more pair updates in flight).  The
+// shared-memory form keeps value v of point q of thread tid at
+// sk[(8 q + v) TPB + tid], so a warp's accesses are consecutive.
+template <int P, int TPB, bool KS>
+struct RunningSums {
+  float h[P][4], c[P][4];
+  float* sk;
+  __device__ __forceinline__ RunningSums(float* sk_) : sk(sk_) {
+#pragma unroll
+    for (int q = 0; q < P; ++q)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        if (KS) {
+          sk[(8 * q + v) * TPB + threadIdx.x] = 0.f;
+          sk[(8 * q + 4 + v) * TPB + threadIdx.x] = 0.f;
+        } else {
+          h[q][v] = c[q][v] = 0.f;
+        }
+      }
+  }
+  // add the tile sums (two packed lanes each) of point q
+  __device__ __forceinline__ void add(int q, u64 w, u64 x, u64 y, u64 z) {
+    const u64 in[4] = {w, x, y, z};
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      float l0, l1;
+      upk2(in[v], l0, l1);
+      if (KS) {
+        float* hs = sk + (8 * q + v) * TPB + threadIdx.x;
+        float* cs = sk + (8 * q + 4 + v) * TPB + threadIdx.x;
+        float hv = *hs, cv = *cs;
+        kahan_add(hv, cv, l0 + l1);
+        *hs = hv;
+        *cs = cv;
+      } else {
+        kahan_add(h[q][v], c[q][v], l0 + l1);
+      }
+    }
+  }
+  __device__ __forceinline__ float4 result(int q) const {
+    if (KS) {
+      const float* hs = sk + 8 * q * TPB + threadIdx.x;
+      return make_float4(hs[0] - hs[4 * TPB], hs[TPB] - hs[5 * TPB], hs[2 * TPB] - hs[6 * TPB],
+                         hs[3 * TPB] - hs[7 * TPB]);
+    }
+    return make_float4(h[q][0] - c[q][0], h[q][1] - c[q][1], h[q][2] - c[q][2], h[q][3] - c[q][3]);
+  }
+};
+
 // The work of one block: template points [ibase, ibase + P*TPB) of the
 // padded record array against reference tiles [t0, t1), at pose *ps; writes
-// one float4 partial per template point to outbase[0 .. P*TPB).
-template <int P, int PM, int TPB, int TJ>
-__device__ __forceinline__ void force_block(float (&sT)[6][TJ], const float* __restrict__ Xr,
+// one float4 partial per template point to outbase[0 .. P*TPB).  SUB record
+// tiles of TJ points are staged together (sT holds SUB*TJ points per row);
+// a stage past t1 is filled with zero-weight entries (-L = +inf).
+template <int P, int PM, int TPB, int TJ, bool KS, int SUB>
+__device__ __forceinline__ void force_block(float (&sT)[6][TJ * SUB], float* sk, const float* __restrict__ Xr,
                                             const float* __restrict__ XA, int t0, int t1,
                                             const float4* __restrict__ Y0r, int ibase, const DevPose* ps,
                                             float qexp, float4* __restrict__ outbase) {
@@ -152,24 +205,29 @@ __device__ __forceinline__ void force_block(float (&sT)[6][TJ], const float* __r
   }
   const u64 nq = pk2(-qexp, -qexp);
 
-  float hW[P], hx[P], hy[P], hz[P];  // running sums
-  float cW[P], cx[P], cy[P], cz[P];  // Kahan compensations
-#pragma unroll
-  for (int q = 0; q < P; ++q) {
-    hW[q] = hx[q] = hy[q] = hz[q] = 0.f;
-    cW[q] = cx[q] = cy[q] = cz[q] = 0.f;
-  }
+  RunningSums<P, TPB, KS> run(sk);
 
-  for (int t = t0; t < t1; ++t) {
+  constexpr int Q4 = TJ / 4;  // float4s per row of one record tile
+  for (int t = t0; t < t1; t += SUB) {
     __syncthreads();
-    {
-      const float4* g4 = reinterpret_cast<const float4*>(Xr + (size_t)t * 4 * TJ);
-      const float4* a4 = reinterpret_cast<const float4*>(XA + (size_t)t * 2 * TJ);
-      float4* s4 = reinterpret_cast<float4*>(&sT[0][0]);
 #pragma unroll
-      for (int u = tid; u < TJ; u += TPB) s4[u] = g4[u];                 // rows 0..3
+    for (int sub = 0; sub < SUB; ++sub) {
+      if (t + sub < t1) {
+        const float4* g4 = reinterpret_cast<const float4*>(Xr + (size_t)(t + sub) * 4 * TJ);
+        const float4* a4 = reinterpret_cast<const float4*>(XA + (size_t)(t + sub) * 2 * TJ);
 #pragma unroll
-      for (int u = tid; u < TJ / 2; u += TPB) s4[TJ + u] = a4[u];        // rows 4..5
+        for (int u = tid; u < 4 * Q4; u += TPB)                            // rows 0..3
+          *reinterpret_cast<float4*>(&sT[u / Q4][sub * TJ + 4 * (u % Q4)]) = g4[u];
+#pragma unroll
+        for (int u = tid; u < 2 * Q4; u += TPB)                            // rows 4..5
+          *reinterpret_cast<float4*>(&sT[4 + u / Q4][sub * TJ + 4 * (u % Q4)]) = a4[u];
+      } else {
+        for (int u = tid; u < TJ; u += TPB) {
+#pragma unroll
+          for (int r = 0; r < 5; ++r) sT[r][sub * TJ + u] = 0.f;
+          sT[5][sub * TJ + u] = INFINITY;
+        }
+      }
     }
     __syncthreads();
 
@@ -177,8 +235,11 @@ __device__ __forceinline__ void force_block(float (&sT)[6][TJ], const float* __r
 #pragma unroll
     for (int q = 0; q < P; ++q) aW[q] = ax[q] = ay[q] = az[q] = 0ull;  // +0.0f in both lanes
 
-#pragma unroll 2
-    for (int jq = 0; jq < TJ; jq += 4) {
+    // two 4-point steps per unrolled body; one for the 4-point shape with
+    // shared-memory sums (its 16 pair updates per step fill 112 registers)
+    constexpr int UNR = (KS && P >= 4) ? 1 : 2;
+#pragma unroll UNR
+    for (int jq = 0; jq < TJ * SUB; jq += 4) {
       const ulonglong2 X = *reinterpret_cast<const ulonglong2*>(&sT[0][jq]);
       const ulonglong2 Yv = *reinterpret_cast<const ulonglong2*>(&sT[1][jq]);
       const ulonglong2 Z = *reinterpret_cast<const ulonglong2*>(&sT[2][jq]);
@@ -193,23 +254,12 @@ __device__ __forceinline__ void force_block(float (&sT)[6][TJ], const float* __r
         pair2<PM>(X.y, Yv.y, Z.y, N.y, Av.y, Lv.y, mx[q], my[q], mz[q], ny[q], ah[q], nq, aW[q], ax[q], ay[q], az[q]);
     }
 #pragma unroll
-    for (int q = 0; q < P; ++q) {
-      float l0, l1;
-      upk2(aW[q], l0, l1);
-      kahan_add(hW[q], cW[q], l0 + l1);
-      upk2(ax[q], l0, l1);
-      kahan_add(hx[q], cx[q], l0 + l1);
-      upk2(ay[q], l0, l1);
-      kahan_add(hy[q], cy[q], l0 + l1);
-      upk2(az[q], l0, l1);
-      kahan_add(hz[q], cz[q], l0 + l1);
-    }
+    for (int q = 0; q < P; ++q) run.add(q, aW[q], ax[q], ay[q], az[q]);
   }
 
   float4* out = outbase + tid;
 #pragma unroll
-  for (int q = 0; q < P; ++q)
-    out[q * TPB] = make_float4(hW[q] - cW[q], hx[q] - cx[q], hy[q] - cy[q], hz[q] - cz[q]);
+  for (int q = 0; q < P; ++q) out[q * TPB] = run.result(q);
 }
 
 // Work item {pair, template block, reference chunk} of a batch: the block's
@@ -233,13 +283,15 @@ __device__ __forceinline__ void batch_item(const int4 it, const BatchPair* __res
 // BATCH = true: one block per work item {pair, template block, reference
 // chunk} of a batch of independent problems (items[], pairs[], one pose per
 // pair); tiles_per_split is then the chunk length in tiles.
-template <int P, int PM, int TPB, int TJ, int MINB, bool BATCH>
+// KS, SUB: running sums in shared memory, record tiles staged SUB at a time.
+template <int P, int PM, int TPB, int TJ, int MINB, bool BATCH, bool KS = false, int SUB = 1>
 __global__ void __launch_bounds__(TPB, MINB)
     force_tile_kernel(const float* __restrict__ Xr, const float* __restrict__ XA, int ntiles,
                       int tiles_per_split, const float4* __restrict__ Y0r, int mpad,
                       const DevPose* __restrict__ pose, float qexp, float4* __restrict__ partial,
                       const int4* __restrict__ items, const BatchPair* __restrict__ pairs) {
-  __shared__ __align__(16) float sT[6][TJ];
+  __shared__ __align__(16) float sT[6][TJ * SUB];
+  __shared__ float sK[KS ? 8 * P * TPB : 1];
   int ibase, t0, t1;
   const DevPose* ps;
   float4* outbase;
@@ -252,7 +304,7 @@ __global__ void __launch_bounds__(TPB, MINB)
     ps = pose;
     outbase = partial + (size_t)blockIdx.y * mpad + ibase;
   }
-  force_block<P, PM, TPB, TJ>(sT, Xr, XA, t0, t1, Y0r, ibase, ps, qexp, outbase);
+  force_block<P, PM, TPB, TJ, KS, SUB>(sT, sK, Xr, XA, t0, t1, Y0r, ibase, ps, qexp, outbase);
 }
 
 // Persistent form of the batched pass: a grid of resident blocks takes work
@@ -261,14 +313,15 @@ __global__ void __launch_bounds__(TPB, MINB)
 // *next is the queue head; it must be 0 at launch (the caller clears it).
 // Each item's result depends only on the item, so which block takes it does
 // not change any bit of the output.  No block waits for another.
-template <int P, int PM, int TPB, int TJ, int MINB>
+template <int P, int PM, int TPB, int TJ, int MINB, bool KS = false, int SUB = 1>
 __global__ void __launch_bounds__(TPB, MINB)
     force_batch_persistent_kernel(const float* __restrict__ Xr, const float* __restrict__ XA,
                                   int tiles_per_split, const float4* __restrict__ Y0r,
                                   const DevPose* __restrict__ pose, float qexp, float4* __restrict__ partial,
                                   const int4* __restrict__ items, int nitems, const BatchPair* __restrict__ pairs,
                                   int* __restrict__ next) {
-  __shared__ __align__(16) float sT[6][TJ];
+  __shared__ __align__(16) float sT[6][TJ * SUB];
+  __shared__ float sK[KS ? 8 * P * TPB : 1];
   __shared__ int s_item;
   for (;;) {
     if (threadIdx.x == 0) s_item = atomicAdd(next, 1);
@@ -279,7 +332,7 @@ __global__ void __launch_bounds__(TPB, MINB)
     const DevPose* ps;
     float4* outbase;
     batch_item<P, TPB>(items[item], pairs, tiles_per_split, pose, partial, ibase, t0, t1, ps, outbase);
-    force_block<P, PM, TPB, TJ>(sT, Xr, XA, t0, t1, Y0r, ibase, ps, qexp, outbase);
+    force_block<P, PM, TPB, TJ, KS, SUB>(sT, sK, Xr, XA, t0, t1, Y0r, ibase, ps, qexp, outbase);
     __syncthreads();  // every thread has read s_item before thread 0 takes the next one
   }
 }
@@ -297,14 +350,28 @@ ForcePlan plan_force(int64_t m, int64_t npad, double p, int num_sms, const Force
   ForcePlan fp;
   fp.pmode = (p == 1.0) ? 1 : (p == 2.0) ? (tune.rsq == 1 ? 4 : 2) : (p == 3.0) ? 3 : 0;
   fp.tile_j = FORCE_TJ;
+  // by template size: 4 points per thread in blocks of 128 with the running
+  // sums in shared memory (the fastest shape measured for large templates),
+  // then 2 and 1 points per thread in blocks of 256
   fp.tpb = 256;
-  if (m >= (int64_t)num_sms * 2 * 256 * 4) fp.P = 4;
-  else if (m >= (int64_t)num_sms * 256 * 2) fp.P = 2;
-  else fp.P = 1;
+  if (m >= (int64_t)num_sms * 2 * 256 * 4) {
+    fp.P = 4;
+    fp.tpb = 128;
+  } else if (m >= (int64_t)num_sms * 256 * 2) {
+    fp.P = 2;
+  } else {
+    fp.P = 1;
+  }
   if (m < 4096) fp.tpb = 128;
   if (tune.P == 1 || tune.P == 2 || tune.P == 4) fp.P = tune.P;
   if (tune.tpb == 128 || tune.tpb == 256) fp.tpb = tune.tpb;
-  fp.occ = (tune.occ == 1 && !(fp.tpb == 256 && fp.P == 4)) ? 1 : 0;
+  const int occ = tune.occ >= 0 ? tune.occ : (fp.P == 4 && fp.tpb == 128) ? 2 : 0;
+  if (occ == 1)
+    fp.occ = (fp.tpb == 256 && fp.P == 4) ? 0 : 1;
+  else if (occ == 2)
+    fp.occ = ((fp.P == 4 && fp.tpb == 128) || (fp.P == 2 && fp.tpb == 256)) ? 2 : 0;
+  else
+    fp.occ = 0;
   const int64_t per_block = (int64_t)fp.tpb * fp.P;
   fp.iblocks = (int)((m + per_block - 1) / per_block);
   const int ntiles = (int)(npad / FORCE_TJ);
@@ -343,29 +410,35 @@ int64_t force_mpad(int64_t m, const ForcePlan& fp) {
   return (mp + 255) / 256 * 256;
 }
 
-template <int P, int PM, int TPB, int MINB>
+template <int P, int PM, int TPB, int MINB, bool KS, int SUB>
 static void launch_force_t(cudaStream_t st, const ForcePlan& fp, const float4* Xr,
                            const float2* XA, int ntiles, const float4* Y0r, int mpad,
                            const DevPose* pose, float qexp, float4* partial) {
   dim3 grid(fp.iblocks, fp.splits);
-  force_tile_kernel<P, PM, TPB, FORCE_TJ, MINB, false><<<grid, TPB, 0, st>>>(
+  force_tile_kernel<P, PM, TPB, FORCE_TJ, MINB, false, KS, SUB><<<grid, TPB, 0, st>>>(
       reinterpret_cast<const float*>(Xr), reinterpret_cast<const float*>(XA), ntiles,
       fp.tiles_per_split, Y0r, mpad, pose, qexp, partial, nullptr, nullptr);
 }
 
 // Dispatch on (points per thread, threads, occupancy variant): calls
-// f.template operator()<P, TPB, MINB>() for the kernel instance of the plan.
+// f.template operator()<P, TPB, MINB, KS, SUB>() for the kernel instance of
+// the plan.  Variant 2 keeps the running sums in shared memory and stages
+// two record tiles (512 reference points) at a time.
 template <class F>
 static int with_shape(const ForcePlan& fp, const F& f) {
   const bool hi = fp.occ == 1;
-  if (fp.tpb == 256) {
-    if (fp.P == 4) return f.template operator()<4, 256, 2>();
-    if (fp.P == 2) return hi ? f.template operator()<2, 256, 3>() : f.template operator()<2, 256, 2>();
-    return hi ? f.template operator()<1, 256, 4>() : f.template operator()<1, 256, 2>();
+  if (fp.occ == 2) {
+    if (fp.P == 4 && fp.tpb == 128) return f.template operator()<4, 128, 3, true, 2>();
+    if (fp.P == 2 && fp.tpb == 256) return f.template operator()<2, 256, 2, true, 2>();
   }
-  if (fp.P == 4) return hi ? f.template operator()<4, 128, 4>() : f.template operator()<4, 128, 2>();
-  if (fp.P == 2) return hi ? f.template operator()<2, 128, 4>() : f.template operator()<2, 128, 2>();
-  return hi ? f.template operator()<1, 128, 4>() : f.template operator()<1, 128, 2>();
+  if (fp.tpb == 256) {
+    if (fp.P == 4) return f.template operator()<4, 256, 2, false, 1>();
+    if (fp.P == 2) return hi ? f.template operator()<2, 256, 3, false, 1>() : f.template operator()<2, 256, 2, false, 1>();
+    return hi ? f.template operator()<1, 256, 4, false, 1>() : f.template operator()<1, 256, 2, false, 1>();
+  }
+  if (fp.P == 4) return hi ? f.template operator()<4, 128, 4, false, 1>() : f.template operator()<4, 128, 2, false, 1>();
+  if (fp.P == 2) return hi ? f.template operator()<2, 128, 4, false, 1>() : f.template operator()<2, 128, 2, false, 1>();
+  return hi ? f.template operator()<1, 128, 4, false, 1>() : f.template operator()<1, 128, 2, false, 1>();
 }
 
 template <int PM>
@@ -380,9 +453,9 @@ struct LaunchShape {
   const DevPose* pose;
   float qexp;
   float4* partial;
-  template <int P, int TPB, int MINB>
+  template <int P, int TPB, int MINB, bool KS, int SUB>
   int operator()() const {
-    launch_force_t<P, PM, TPB, MINB>(st, fp, Xr, XA, ntiles, Y0r, mpad, pose, qexp, partial);
+    launch_force_t<P, PM, TPB, MINB, KS, SUB>(st, fp, Xr, XA, ntiles, Y0r, mpad, pose, qexp, partial);
     return 0;
   }
 };
@@ -396,11 +469,11 @@ static void launch_force_pm(cudaStream_t st, const ForcePlan& fp, const float4* 
 
 template <int PM>
 struct OccShape {
-  template <int P, int TPB, int MINB>
+  template <int P, int TPB, int MINB, bool KS, int SUB>
   int operator()() const {
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, force_tile_kernel<P, PM, TPB, FORCE_TJ, MINB, false>, TPB,
-                                                      0) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, force_tile_kernel<P, PM, TPB, FORCE_TJ, MINB, false, KS, SUB>,
+                                                      TPB, 0) != cudaSuccess) {
       cudaGetLastError();
       return 2;
     }
@@ -439,26 +512,38 @@ cudaError_t launch_force(Launch L, const ForcePlan& fp, const float4* Xr, const 
 
 // Batched force pass, 128 threads (P template points each) per block: one
 // block per item (grid == 0), or a persistent grid of `grid` resident blocks
-// taking items from the queue head *next, which is cleared first.
+// taking items from the queue head *next, which is cleared first.  P = 4
+// uses the shared-memory running sums and 512-point stages (3 blocks per SM).
+template <int P>
+struct BatchShape {
+  static constexpr bool KS = P == 4;
+  static constexpr int SUB = P == 4 ? 2 : 1;
+  static constexpr int MINB = P == 4 ? 3 : 2;
+};
+
 template <int P, int PM>
 static void launch_force_batch_p(cudaStream_t st, int nitems, const int4* items, const BatchPair* pairs,
                                  const float4* Xr, const float2* XA, const float4* Y0r, const DevPose* poses,
                                  float qexp, float4* partial, int chunk_tiles, int grid, int* next) {
+  using B = BatchShape<P>;
   const float* xr = reinterpret_cast<const float*>(Xr);
   const float* xa = reinterpret_cast<const float*>(XA);
   if (grid <= 0)
-    force_tile_kernel<P, PM, 128, FORCE_TJ, 2, true><<<nitems, 128, 0, st>>>(xr, xa, 0, chunk_tiles, Y0r, 0, poses,
-                                                                             qexp, partial, items, pairs);
+    force_tile_kernel<P, PM, 128, FORCE_TJ, B::MINB, true, B::KS, B::SUB><<<nitems, 128, 0, st>>>(
+        xr, xa, 0, chunk_tiles, Y0r, 0, poses, qexp, partial, items, pairs);
   else
-    force_batch_persistent_kernel<P, PM, 128, FORCE_TJ, 2><<<grid < nitems ? grid : nitems, 128, 0, st>>>(
-        xr, xa, chunk_tiles, Y0r, poses, qexp, partial, items, nitems, pairs, next);
+    force_batch_persistent_kernel<P, PM, 128, FORCE_TJ, B::MINB, B::KS, B::SUB>
+        <<<grid < nitems ? grid : nitems, 128, 0, st>>>(xr, xa, chunk_tiles, Y0r, poses, qexp, partial, items,
+                                                        nitems, pairs, next);
 }
 
 template <int PM>
 static void launch_force_batch_pm(cudaStream_t st, int P, int nitems, const int4* items, const BatchPair* pairs,
                                   const float4* Xr, const float2* XA, const float4* Y0r, const DevPose* poses,
                                   float qexp, float4* partial, int chunk_tiles, int grid, int* next) {
-  if (P == 2)
+  if (P == 4)
+    launch_force_batch_p<4, PM>(st, nitems, items, pairs, Xr, XA, Y0r, poses, qexp, partial, chunk_tiles, grid, next);
+  else if (P == 2)
     launch_force_batch_p<2, PM>(st, nitems, items, pairs, Xr, XA, Y0r, poses, qexp, partial, chunk_tiles, grid, next);
   else
     launch_force_batch_p<1, PM>(st, nitems, items, pairs, Xr, XA, Y0r, poses, qexp, partial, chunk_tiles, grid, next);
@@ -490,9 +575,15 @@ static cudaError_t batch_slots_pm(int P, int* slots) {
   int dev = 0, sms = 0, nb = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (e == cudaSuccess)
-    e = P == 2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, force_batch_persistent_kernel<2, PM, 128, FORCE_TJ, 2>, 128, 0)
-               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, force_batch_persistent_kernel<1, PM, 128, FORCE_TJ, 2>, 128, 0);
+  if (e == cudaSuccess) {
+    if (P == 4)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+          &nb, force_batch_persistent_kernel<4, PM, 128, FORCE_TJ, BatchShape<4>::MINB, true, 2>, 128, 0);
+    else if (P == 2)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, force_batch_persistent_kernel<2, PM, 128, FORCE_TJ, 2>, 128, 0);
+    else
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, force_batch_persistent_kernel<1, PM, 128, FORCE_TJ, 2>, 128, 0);
+  }
   if (e != cudaSuccess) return e;
   *slots = sms * (nb > 0 ? nb : 1);
   return cudaSuccess;

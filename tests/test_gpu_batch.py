@@ -102,7 +102,7 @@ def test_batch_graph_replay_equals_eager():
         assert list(ra.R) == list(rb.R) and list(ra.t) == list(rb.t) and ra.s == rb.s
 
 
-@pytest.mark.parametrize("P,chunk,use_graph", [(1, 16, 0), (2, 3, 1), (2, 16, 1)])
+@pytest.mark.parametrize("P,chunk,use_graph", [(1, 16, 0), (2, 3, 1), (2, 16, 1), (4, 3, 0), (4, 16, 1)])
 def test_persistent_batch_kernel_is_bit_identical(P, chunk, use_graph):
     """The persistent batched force kernel (resident blocks taking work items
     from a queue) gives every pair the same bits as one block per item: an
@@ -118,13 +118,14 @@ def test_persistent_batch_kernel_is_bit_identical(P, chunk, use_graph):
         assert list(ra.R) == list(rb.R) and list(ra.t) == list(rb.t) and ra.s == rb.s
 
 
-def test_batch_chunk_tuning_keeps_results_close():
+@pytest.mark.parametrize("P", [2, 4])
+def test_batch_chunk_tuning_keeps_results_close(P):
     pairs = make_pairs([3000, 700], seed=17)
     a, _ = run_batch(pairs, 10, p=2.0)
     ctx = scgr.scgr_create(scgr.scgr_default_params(p=2.0))
     try:
         scgr.scgr_set_tuning(ctx, scgr.SCGR_TUNE_BATCH_CHUNK_TILES, 3)
-        scgr.scgr_set_tuning(ctx, scgr.SCGR_TUNE_BATCH_P, 2)
+        scgr.scgr_set_tuning(ctx, scgr.SCGR_TUNE_BATCH_P, P)
         scgr.scgr_set_tuning(ctx, scgr.SCGR_TUNE_FORCE_RSQRT, 1)       # p = 2 through rsqrt
         ro = np.cumsum([0] + [len(x) for x, _ in pairs])
         to = np.cumsum([0] + [len(y) for _, y in pairs])
@@ -135,7 +136,7 @@ def test_batch_chunk_tuning_keeps_results_close():
     finally:
         scgr.scgr_destroy(ctx)
     for (X, _), ra, rb in zip(pairs, a, b):
-        assert close(ra, rb, synth.bbox_diag(X), "batched, chunk 3 / P 2 / rsqrt vs defaults")
+        assert close(ra, rb, synth.bbox_diag(X), f"batched, chunk 3 / P {P} / rsqrt vs defaults")
 
 
 def test_batch_rejects_bad_offsets():

@@ -19,7 +19,8 @@ def _lib(scgr_lib):
 @pytest.mark.parametrize("P,tpb,splits,occ", [(1, 128, 0, 0), (2, 128, 0, 0), (4, 128, 0, 0), (1, 256, 0, 0),
                                               (2, 256, 0, 0), (4, 256, 0, 0), (4, 256, 1, 0), (2, 128, 7, 0),
                                               (1, 128, 0, 1), (2, 128, 0, 1), (4, 128, 0, 1), (1, 256, 0, 1),
-                                              (2, 256, 0, 1)])
+                                              (2, 256, 0, 1), (4, 128, 0, 2), (2, 256, 0, 2), (4, 128, 3, 2),
+                                              (2, 256, 5, 2)])
 def test_every_tile_shape_matches_oracle(P, tpb, splits, occ):
     sc = synth.scale_case()
     X = sc.X[synth.subsample(sc.X, 2600, 61)]
