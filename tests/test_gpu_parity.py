@@ -97,7 +97,7 @@ def force_check(g, X, Y0, aX, aY, sigma, p, g_mode, rows=None, what=""):
     eW = rel_l2(f4[sel, 3], Wr)
     check(f"force f_i (p={p:g}, g mode {g_mode}{what}): relative L2", ef, FORCE_TOL)
     check(f"weight W_i (p={p:g}, g mode {g_mode}{what}): relative L2", eW, FORCE_TOL)
-    return ef, eW
+    return ef, eW, fr, Wr
 
 
 @pytest.mark.parametrize("p,g_mode", [(2.0, 1), (1.0, 1), (3.0, 1), (1.5, 1), (2.0, 0), (1.0, 0)])
@@ -138,8 +138,19 @@ def test_forces_block_shapes_sampled_rows(n, m, p):
     with Gpu(X, Y0, p=p) as g:
         g.set_curvature(0, aX)
         g.set_curvature(1, aY)
+        plan = scgr.scgr_get_plan(g.ctx)
+        if m >= 2048 * torch.cuda.get_device_properties(0).multi_processor_count:
+            # large templates get 4 points x 128 threads with shared-memory running sums
+            assert (plan["P"], plan["tpb"], plan["occ"]) == (4, 128, 2), plan
         rows = np.sort(rng.choice(m, size=300, replace=False))
-        force_check(g, X, Y0, aX, aY, O.sigma_auto(aX), p, 1, rows, what=f", {m // 1000}k template, sampled rows")
+        fr, _ = force_check(g, X, Y0, aX, aY, O.sigma_auto(aX), p, 1, rows,
+                            what=f", {m // 1000}k template, sampled rows")[2:]
+        # the potential's adjoint runs the same plan: at the identity pose its
+        # template-point gradient is -f
+        gx = torch.empty((m, 3), dtype=torch.float32, device="cuda")
+        scgr.scgr_potential(g.ctx, [0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 1.0], grad_xyz_out=gx)
+        check(f"template-point gradient, {m // 1000}k template (p={p:g}), sampled rows: relative L2",
+              rel_l2(gx.cpu().numpy()[rows], -fr), FORCE_TOL)
 
 
 def test_forces_full_size_sampled_rows():
