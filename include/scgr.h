@@ -321,9 +321,9 @@ SCGR_EXPORT scgr_status scgr_step_apply(scgr_ctx* ctx, const double tot13[13]);
 #define SCGR_TUNE_FORCE_P 3           /* force kernel template points per thread: 0 auto, 1, 2, 4 */
 #define SCGR_TUNE_FORCE_TPB 4         /* force kernel threads per block: 0 auto, 128, 256 */
 #define SCGR_TUNE_FORCE_SPLITS 5      /* force kernel reference splits: 0 auto (wave-filling), >= 1 */
-#define SCGR_TUNE_BATCH_P 8           /* template points per thread in the batched force kernel: 1 (default),
-                                         2, or 4 (running sums in shared memory; each pair's template is
-                                         then padded to a multiple of 512 points) */
+#define SCGR_TUNE_BATCH_P 8           /* template points per thread in the batched force kernel: 1 (default)
+                                         or 2 (128 threads per block), or 4 (64 threads per block, running
+                                         sums in shared memory) */
 #define SCGR_TUNE_FORCE_OCC 7         /* force kernel variant: 0 registers only, 2 resident blocks per SM;
                                          1 a tighter register budget and more resident blocks per SM (3 at
                                          256 threads, 4 at 128); 2 the per-point running sums in shared

@@ -34,7 +34,7 @@ scgr_status scgr_batch_run(scgr_ctx* c, int npairs, const int64_t* ref_off, cons
 
   // ---- host plan: per-pair geometry, work items (longest first), tables
   const int CT = c->batch_chunk_tiles;
-  const int FB = 128 * c->batch_P;  // template points per batched force block
+  const int FB = batch_block_threads(c->batch_P) * c->batch_P;  // template points per batched force block
   std::vector<BatchPair> pairs(npairs);
   std::vector<int4> items;
   std::vector<int> cpair;

@@ -306,6 +306,8 @@ cudaError_t launch_force_batch(Launch L, int pmode, int P, int nitems, const int
                                float qexp, float4* partial, int chunk_tiles, int grid, int* next);
 // Resident blocks of the persistent batched force kernel (its `grid`).
 cudaError_t force_batch_slots(int pmode, int P, int* slots);
+// Threads per block of the batched force kernel with P template points per thread.
+int batch_block_threads(int P);
 cudaError_t launch_combine_batch(Launch L, int nblocks, const int* cpair, const BatchPair* pairs,
                                  const float4* partial, const float4* Y0r, const double* aY64, int g_mode,
                                  const DevPose* poses, double* blockpart);

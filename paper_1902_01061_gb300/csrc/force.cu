@@ -510,16 +510,20 @@ cudaError_t launch_force(Launch L, const ForcePlan& fp, const float4* Xr, const 
   return cudaGetLastError();
 }
 
-// Batched force pass, 128 threads (P template points each) per block: one
-// block per item (grid == 0), or a persistent grid of `grid` resident blocks
-// taking items from the queue head *next, which is cleared first.  P = 4
-// uses the shared-memory running sums and 512-point stages (3 blocks per SM).
+// Batched force pass, P template points per thread: one block per item
+// (grid == 0), or a persistent grid of `grid` resident blocks taking items
+// from the queue head *next, which is cleared first.  P = 1, 2: 128 threads.
+// P = 4: 64 threads (a 256-point template block, as for P = 2), the
+// shared-memory running sums and 512-point stages, 6 blocks per SM.
 template <int P>
 struct BatchShape {
   static constexpr bool KS = P == 4;
   static constexpr int SUB = P == 4 ? 2 : 1;
-  static constexpr int MINB = P == 4 ? 3 : 2;
+  static constexpr int TPB = P == 4 ? 64 : 128;
+  static constexpr int MINB = P == 4 ? 6 : 2;
 };
+
+int batch_block_threads(int P) { return P == 4 ? BatchShape<4>::TPB : BatchShape<1>::TPB; }
 
 template <int P, int PM>
 static void launch_force_batch_p(cudaStream_t st, int nitems, const int4* items, const BatchPair* pairs,
@@ -529,12 +533,12 @@ static void launch_force_batch_p(cudaStream_t st, int nitems, const int4* items,
   const float* xr = reinterpret_cast<const float*>(Xr);
   const float* xa = reinterpret_cast<const float*>(XA);
   if (grid <= 0)
-    force_tile_kernel<P, PM, 128, FORCE_TJ, B::MINB, true, B::KS, B::SUB><<<nitems, 128, 0, st>>>(
+    force_tile_kernel<P, PM, B::TPB, FORCE_TJ, B::MINB, true, B::KS, B::SUB><<<nitems, B::TPB, 0, st>>>(
         xr, xa, 0, chunk_tiles, Y0r, 0, poses, qexp, partial, items, pairs);
   else
-    force_batch_persistent_kernel<P, PM, 128, FORCE_TJ, B::MINB, B::KS, B::SUB>
-        <<<grid < nitems ? grid : nitems, 128, 0, st>>>(xr, xa, chunk_tiles, Y0r, poses, qexp, partial, items,
-                                                        nitems, pairs, next);
+    force_batch_persistent_kernel<P, PM, B::TPB, FORCE_TJ, B::MINB, B::KS, B::SUB>
+        <<<grid < nitems ? grid : nitems, B::TPB, 0, st>>>(xr, xa, chunk_tiles, Y0r, poses, qexp, partial, items,
+                                                          nitems, pairs, next);
 }
 
 template <int PM>
@@ -578,7 +582,8 @@ static cudaError_t batch_slots_pm(int P, int* slots) {
   if (e == cudaSuccess) {
     if (P == 4)
       e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-          &nb, force_batch_persistent_kernel<4, PM, 128, FORCE_TJ, BatchShape<4>::MINB, true, 2>, 128, 0);
+          &nb, force_batch_persistent_kernel<4, PM, BatchShape<4>::TPB, FORCE_TJ, BatchShape<4>::MINB, true, 2>,
+          BatchShape<4>::TPB, 0);
     else if (P == 2)
       e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, force_batch_persistent_kernel<2, PM, 128, FORCE_TJ, 2>, 128, 0);
     else
