@@ -383,6 +383,11 @@ def bench_diff(args, scgr, torch, dev, steps, warmup):
         scgr.scgr_set_reference(ctx, torch.from_numpy(case.X).to(dev))
         scgr.scgr_set_template(ctx, torch.from_numpy(case.Y0).to(dev))
         scgr.scgr_compute_descriptors(ctx)
+        tuned = None
+        if not args.no_autotune:
+            from paper_1902_01061_gb300 import autotune
+            tuned = autotune.tune_single(ctx, n, m, 2.0, reps=10)
+            tuned = {k: tuned[k] for k in ("P", "tpb", "occ", "rsqrt", "ms", "plan")}
         pose = [0.1, -0.2, 0.3, 0.05, 0.0, -0.05, 1.02]
         gx = torch.empty((m, 3), dtype=torch.float32, device=dev)
         fwd = _timed(lambda: scgr.scgr_potential(ctx, pose, want_grad=False), steps, warmup, torch)
@@ -394,7 +399,7 @@ def bench_diff(args, scgr, torch, dev, steps, warmup):
             "potential_ms": fwd * 1e3, "potential_and_adjoint_recompute_ms": both * 1e3,
             "potential_and_adjoint_stored_ms": stored * 1e3,
             "stored_pair_terms_bytes": m * ((n + 255) // 256 * 256) * 4,
-            "adjoint_pair_interactions_per_s": 2 * n * m / both,
+            "adjoint_pair_interactions_per_s": 2 * n * m / both, "autotuned": tuned,
             "timing": "host wall clock around each synchronising call"}
 
 
