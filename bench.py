@@ -33,7 +33,9 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-FLOPS_PER_PAIR = 22          # counting convention of the per-pair work
+# counting convention of the per-pair work: r = Y - X (3), d^2 (5), d^(p-1) (1),
+# the similarity exponent and exp (4), x aX (1), x d^(p-1) (1), W (1), f (6)
+FLOPS_PER_PAIR = 22
 FP32_LANES_PER_SM = 128
 L2_FLUSH_BYTES = 256 << 20   # > 129 MB L2
 
