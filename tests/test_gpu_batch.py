@@ -150,3 +150,28 @@ def test_batch_rejects_bad_offsets():
             scgr.scgr_batch_run(ctx, [1, 40], X, [0, 40], X, 3)            # offsets must start at 0
     finally:
         scgr.scgr_destroy(ctx)
+
+
+def test_full_size_batch_in_the_benchmark_configuration():
+    """The benchmark's 512-pair batch (500-20,000 points per cloud, log-uniform;
+    5.4 M points) at full size, in the launch configuration the benchmark's
+    autotuner picks on GB300 (2 points per thread, 16-tile chunks, one CUDA
+    graph), for 20 iterations: the three smallest pairs against the FP64
+    oracle, and three other pairs (largest, median, one more) against
+    one-pair-per-call runs of the same library."""
+    pairs = synth.batch_case()
+    iters = 20
+    tuning = ((scgr.SCGR_TUNE_BATCH_P, 2), (scgr.SCGR_TUNE_BATCH_CHUNK_TILES, 16))
+    res, launches = run_batch([(pp.X, pp.Y0) for pp in pairs], iters, tuning=tuning, p=2.0, use_graph=1)
+    assert len(res) == len(pairs) and all(r.iterations == iters for r in res)
+    sizes = np.array([len(pp.X) for pp in pairs])
+    order = np.argsort(sizes, kind="stable")
+    for i in order[:3]:
+        pp = pairs[i]
+        o = O.register(pp.X, pp.Y0, O.Params(p=2.0), iterations=iters)
+        assert close(res[i], (o["R"], o["t"], o["s"]), synth.bbox_diag(pp.X), "full-size batch, smallest pairs vs oracle")
+    for i in (order[-1], order[len(order) // 2], order[len(order) // 3]):
+        pp = pairs[i]
+        with Gpu(pp.X, pp.Y0, p=2.0) as g:
+            single = g.run(iters)
+        assert close(res[i], single, synth.bbox_diag(pp.X), "full-size batch vs one call per pair")

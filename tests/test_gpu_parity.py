@@ -179,6 +179,26 @@ def test_forces_full_size_sampled_rows():
         force_check(g, case.X, case.Y0, aX, aY, O.sigma_auto(aX), 2.0, 1, rows, what=", 1M x 1M, 48 sampled rows")
 
 
+def test_scale_case_full_size_sampled_rows():
+    """The 35,000 x 30,800 case (5 ellipsoids, 90 deg, scale 0.8, 20% slab
+    removed, 10% outliers) at full size with the oracle's own descriptors
+    (k = 16 nearest, curvature, sigma), in the launch configuration the
+    benchmark's autotuner picks on GB300 (2 points per thread x 128 threads):
+    curvature of every point, then iteration-0 forces at sampled rows."""
+    sc = synth.scale_case()
+    rng = np.random.default_rng(35)
+    d = O.descriptors(sc.X, sc.Y0, O.Params(p=2.0))
+    with Gpu(sc.X, sc.Y0, p=2.0, tune={scgr.SCGR_TUNE_FORCE_P: 2, scgr.SCGR_TUNE_FORCE_TPB: 128}) as g:
+        plan = scgr.scgr_get_plan(g.ctx)
+        assert (plan["P"], plan["tpb"]) == (2, 128), plan
+        for which, a_ref in ((0, d["aX"]), (1, d["aY"])):
+            a_got = g.curv64(which)
+            check("curvature: max |da| / (|a| + 1e-6)", np.max(np.abs(a_got - a_ref) / (np.abs(a_ref) + 1e-6)), 1e-6)
+        check("sigma: relative error", abs(g.sigma() - d["sigma"]) / d["sigma"], 1e-9)
+        rows = np.sort(rng.choice(len(sc.Y0), size=96, replace=False))
+        force_check(g, sc.X, sc.Y0, d["aX"], d["aY"], d["sigma"], 2.0, 1, rows, what=", 35k x 30.8k, 96 sampled rows")
+
+
 def pose_check(res, ores, diag, what="pose vs oracle", rot_tol=0.5, t_tol=1e-3, s_tol=1e-5):
     R, t, s = res.as_numpy()
     check_pose(what, R, t, s, ores["R"], ores["t"], ores["s"], diag, rot_tol, t_tol, s_tol)
