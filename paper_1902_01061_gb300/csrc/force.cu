@@ -5,7 +5,8 @@
 //   w_ij = g(s_ij) d_ij^(p-1),   f_i = -sum_j w_ij (Y_i - X_j),
 //   W_i  = sum_j w_ij.
 // The kernel accumulates, per template point, sum_j w_ij and sum_j w_ij X_j;
-// f_i = aY (sum_j w X_j - Y_i sum_j w) is formed afterwards in float64.
+// the combine kernel forms f_i = aY (sum_j w X_j - Y_i sum_j w) afterwards
+// from an exact product and an exact two-sum.
 //
 // Per pair (float32): d^2 = |X'|^2 + |Y'|^2 - 2 X'.Y' (one add, three FMAs),
 // the similarity-and-aX factor 2^-(u^2 - L), u = a_hat_X - a_hat_Y (one sub,
@@ -22,11 +23,12 @@
 //
 // Layout of the work: grid.x covers template points (P per thread, TPB
 // threads), grid.y splits the reference range so that the grid has many
-// waves on 152 SMs.  Each tile's sums are accumulated in plain float32 (two
-// lanes per point) and then added to the running per-point sums with Kahan
-// compensation; each split writes its per-point partial (float4) and the
-// combine kernel adds the splits in a fixed order in float64, so results are
-// deterministic.
+// waves on 152 SMs.  Each staged tile's sums are accumulated in plain float32
+// (two lanes per point) and then added to the running per-point sums with
+// Kahan compensation (kept in registers, or in shared memory for the shape
+// that holds 4 points per thread); each split writes its per-point partial
+// (float4), and the combine kernel adds the splits per point in a fixed order
+// (Kahan) and the points in float64, so results are deterministic.
 #include <cmath>
 
 #include "common.cuh"
