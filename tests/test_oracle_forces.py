@@ -123,6 +123,7 @@ def test_force_is_minus_potential_gradient(p):
             Ym = Y.copy(); Ym[i, c] -= h
             fd = (O.potential(Yp, X, aY, aX, 0.1, p, 1) - O.potential(Ym, X, aY, aX, 0.1, p, 1)) / (2 * h)
             assert abs(fd + f[i, c]) <= 1e-6 * max(1.0, abs(f[i, c]))
+    np.testing.assert_array_equal(O.potential_grad(Y, X, aY, aX, 0.1, p, 1), -f)
 
 
 def test_pose_gradient_matches_finite_differences():

@@ -90,8 +90,21 @@ def _g_schedule_sign(t, G1, E):
     return 0.1 * G1 + 0.9 * G1 / (1.0 + math.exp(min(700.0, (t - E / 2.0))))
 
 
+def _rodrigues_column_form(omega):
+    return ORIG["rodrigues"](omega).T                 # column-vector matrix used in a row-vector product
+
+
+def _cloud_stats_unbiased(P):
+    P = np.asarray(P, dtype=np.float64)
+    mu = P.mean(axis=0)
+    D = P - mu
+    C = D.T @ D / (len(P) - 1)                        # 1/(n-1) instead of the 1/n of Sec. III-B
+    return mu, C, float(np.linalg.eigvalsh(C)[-1])
+
+
 ORIG = {name: getattr(M, name) for name in
-        ("_pair_terms", "forces_rows", "curvature", "kabsch", "knn", "scale_factor", "g_schedule")}
+        ("_pair_terms", "forces_rows", "curvature", "kabsch", "knn", "scale_factor", "g_schedule", "rodrigues",
+         "cloud_stats")}
 
 CASES = {
     "force sign": ("_pair_terms", _pair_terms_sign, [TF.test_two_point_hand_case]),
@@ -110,6 +123,9 @@ CASES = {
                                                                  TK.test_knn_key_is_rounded_per_operation]),
     "scale without square root": ("scale_factor", _scale_no_sqrt, [TP.test_scale_factor_and_polar]),
     "schedule sign": ("g_schedule", _g_schedule_sign, [TP.test_g_schedule_closed_form]),
+    "axis-angle rotation transposed": ("rodrigues", _rodrigues_column_form,
+                                       [TP.test_rodrigues_is_the_matrix_exponential_in_row_vector_form]),
+    "unbiased covariance": ("cloud_stats", _cloud_stats_unbiased, [TP.test_cloud_stats_closed_form]),
 }
 
 

@@ -101,3 +101,40 @@ def test_composed_pose_matches_literal_iteration():
     Ypose = res["s"] * case.Y0.astype(np.float64) @ res["R"] + res["t"]
     np.testing.assert_allclose(Ypose, res["Y"], atol=1e-10)
     np.testing.assert_allclose(res["R"] @ res["R"].T, np.eye(3), atol=1e-13)
+
+
+def test_rodrigues_is_the_matrix_exponential_in_row_vector_form():
+    """rodrigues(w) = exp([w]_x)^T (so that y = x @ R rotates x by |w| about
+    w, right-handed), against scipy's matrix exponential and a hand case;
+    near zero the series branch agrees with the closed form."""
+    from scipy.linalg import expm
+    rng = np.random.default_rng(3)
+    for w in [np.array([0.0, 0.0, math.pi / 2]), rng.normal(size=3), 1e-3 * rng.normal(size=3), 2.5 * rng.normal(size=3)]:
+        K = np.array([[0.0, -w[2], w[1]], [w[2], 0.0, -w[0]], [-w[1], w[0], 0.0]])
+        R = O.rodrigues(w)
+        np.testing.assert_allclose(R, expm(K).T, atol=1e-13)
+        np.testing.assert_allclose(R.T @ R, np.eye(3), atol=1e-13)
+        assert np.linalg.det(R) == pytest.approx(1.0, abs=1e-13)
+    # +90 degrees about z takes x to y in the row-vector convention
+    np.testing.assert_allclose(np.array([1.0, 0.0, 0.0]) @ O.rodrigues([0.0, 0.0, math.pi / 2]), [0.0, 1.0, 0.0],
+                               atol=1e-15)
+    w = np.array([3e-13, -1e-13, 2e-13])
+    K = np.array([[0.0, -w[2], w[1]], [w[2], 0.0, -w[0]], [-w[1], w[0], 0.0]])
+    np.testing.assert_allclose(O.rodrigues(w), (np.eye(3) + K).T, atol=1e-20)
+
+
+def test_cloud_stats_closed_form():
+    """Mean, 1/n covariance and largest eigenvalue (Sec. III-B) of the six
+    points centre +- a e_x, +- b e_y, +- c e_z: covariance diag(a^2, b^2, c^2)/3;
+    and numpy's biased covariance on a random cloud."""
+    a, b, c = 2.0, 0.5, 1.0
+    centre = np.array([0.3, -1.0, 4.0])
+    P = centre + np.array([[a, 0, 0], [-a, 0, 0], [0, b, 0], [0, -b, 0], [0, 0, c], [0, 0, -c]])
+    mu, C, lam = O.cloud_stats(P)
+    np.testing.assert_allclose(mu, centre, atol=1e-15)
+    np.testing.assert_allclose(C, np.diag([a * a, b * b, c * c]) / 3.0, atol=1e-15)
+    assert lam == pytest.approx(a * a / 3.0, rel=1e-14)
+    Q = np.random.default_rng(4).normal(size=(200, 3)) @ np.diag([1.0, 2.0, 0.5])
+    _, C2, lam2 = O.cloud_stats(Q)
+    np.testing.assert_allclose(C2, np.cov(Q.T, bias=True), atol=1e-14)
+    assert lam2 == pytest.approx(np.linalg.eigvalsh(np.cov(Q.T, bias=True))[-1], rel=1e-13)
