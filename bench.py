@@ -436,6 +436,69 @@ def bench_scale(args, scgr, torch, dev, steps, warmup):
             "ms_per_registration": sec * 1e3, "pair_interactions_per_s": n * m * 200 / sec, "autotuned": tuned}
 
 
+def bench_next(args, scgr, torch, dev, steps, warmup, Xd, Yd):
+    """The widened rows, each timed once set up: the odd-p fast path on the
+    1M x 1M workload (p = 1: pose-free force sums computed once per call;
+    p = 3: 14 pose-free moments), and on the 35,000-point case the radius
+    neighbourhood of Sec. IV, the pyramidal schedule and the change mask of
+    Sec. V after registration."""
+    from paper_1902_01061_gb300 import synth
+    out = {}
+    n, m = int(Xd.shape[0]), int(Yd.shape[0])
+    stream = torch.cuda.current_stream()
+    for p in (1.0, 3.0):
+        ctx = scgr.scgr_create(scgr.scgr_default_params(p=p, g_mode=1, k=16), stream)
+        try:
+            scgr.scgr_set_reference(ctx, Xd)
+            scgr.scgr_set_template(ctx, Yd)
+            scgr.scgr_compute_descriptors(ctx)
+            fast = _timed(lambda: (scgr.scgr_run(ctx, 50), scgr.scgr_get_result(ctx)), steps, 1, torch)
+            scgr.scgr_set_tuning(ctx, scgr.SCGR_TUNE_REUSE_POSE_FREE, 0)
+            per_it = _timed(lambda: (scgr.scgr_run(ctx, 2), scgr.scgr_get_result(ctx)), 1, 1, torch) / 2
+        finally:
+            scgr.scgr_destroy(ctx)
+        out[f"odd_p_fast_path_p{int(p)}"] = {
+            "workload": f"{n:,} x {m:,}, p = {p:g}, 50 iterations",
+            "ms_per_registration": fast * 1e3, "all_pairs_ms_per_iteration": per_it * 1e3,
+            "speedup_vs_all_pairs_every_iteration": 50 * per_it / fast,
+            "equivalent_pair_interactions_per_s": n * m * 50 / fast}
+    sc = synth.scale_case()
+    X = torch.from_numpy(sc.X).to(dev)
+    Y = torch.from_numpy(sc.Y0).to(dev)
+    ctx = scgr.scgr_create(scgr.scgr_default_params(p=2.0, neigh_mode=1, radius_scale=1.0), stream)
+    try:
+        scgr.scgr_set_reference(ctx, X)
+        scgr.scgr_set_template(ctx, Y)
+        rad = _timed(lambda: scgr.scgr_compute_descriptors(ctx), steps, 1, torch)
+    finally:
+        scgr.scgr_destroy(ctx)
+    out["radius_neighbourhood"] = {"workload": "35,000 + 30,800 points, radius sqrt(e) (scale 1.0), both clouds",
+                                   "ms_descriptors": rad * 1e3}
+    levels = [(70, 24, 1.0, 1.5), (70, 16, 1.0, 1.0), (60, 8, 1.0, 0.7)]
+    ctx = scgr.scgr_create(scgr.scgr_default_params(p=2.0, use_graph=1, E=200), stream)
+    try:
+        def pyramid():
+            scgr.scgr_set_reference(ctx, X)
+            scgr.scgr_set_template(ctx, Y)
+            scgr.scgr_compute_descriptors(ctx)
+            scgr.run_pyramid(ctx, levels)
+        pyr = _timed(pyramid, steps, 1, torch)
+        mask = torch.empty(len(sc.Y0), dtype=torch.uint8, device=dev)
+        diag = float(synth.bbox_diag(sc.X))
+        chg = _timed(lambda: scgr.scgr_change_mask(ctx, 0.01 * diag, mask), steps, 1, torch)
+        changed = int(mask.sum().item())
+    finally:
+        scgr.scgr_destroy(ctx)
+    out["pyramidal_schedule"] = {"workload": "35,000 x 30,800, levels (iterations, k, sigma scale) = "
+                                             "(70, 24, 1.5), (70, 16, 1.0), (60, 8, 0.7), CUDA graph per level",
+                                 "ms_per_registration": pyr * 1e3}
+    out["change_mask"] = {"workload": "30,800 moved template points against 35,000 reference points, "
+                                      "threshold 1% of the diagonal",
+                          "ms": chg * 1e3, "points_flagged": changed}
+    out["timing"] = "host wall clock around synchronised calls"
+    return out
+
+
 def run_reference(args, ws, rank):
     """The oracle arm: bounded samples of the same workload on the host cores."""
     if rank != 0:
@@ -495,6 +558,8 @@ def main():
     ap.add_argument("--batch-only", action="store_true",
                     help="run only the batched leg (no one-call-per-pair comparison) and print it")
     ap.add_argument("--batch-iters", type=int, default=100, help="iterations of the batched leg")
+    ap.add_argument("--next-only", action="store_true",
+                    help="only the leg of the widened rows (odd-p fast path, radius, pyramid, change mask)")
     ap.add_argument("--batch-plan", default=None, help="pin the batched force kernel 'P,CHUNK_TILES[,PERSISTENT]' (no autotuning)")
     ap.add_argument("--batch-eager", action="store_true", help="batched leg without the CUDA graph (for profilers)")
     ap.add_argument("--plan", default=None, help="pin the force kernel 'P,TPB[,OCC[,RSQRT]]' (no autotuning), e.g. 2,256,0,1")
@@ -524,6 +589,14 @@ def main():
             out = bench_diff(args, scgr, torch, torch.device("cuda", local), args.steps, args.warmup)
             print(json.dumps({"leg": "differentiation", "steps": args.steps, "warmup": args.warmup, **out}),
                   flush=True)
+        return 0
+    if args.next_only:
+        if rank == 0:
+            dev = torch.device("cuda", local)
+            pair = make_pair(args.workload)
+            out = bench_next(args, scgr, torch, dev, args.steps, args.warmup, torch.from_numpy(pair.X).to(dev),
+                             torch.from_numpy(pair.Y0).to(dev))
+            print(json.dumps({"leg": "next_rows", "steps": args.steps, **out}), flush=True)
         return 0
     wl = WORKLOADS[args.workload]
     pair = make_pair(args.workload)
@@ -627,11 +700,12 @@ def main():
         e2e = {"value": ws * pairs_per_step / e2e_s, "unit": "pair-interactions/s",
                "h2d_bytes_per_step": (n + m) * 12, "d2h_bytes_per_step": m * 12 + 8 * 13 + 8}
     scgr.scgr_destroy(ctx)
-    batch = diff = scale = None
+    batch = diff = scale = nxt = None
     if ws == 1 and not args.no_batch:
         batch = bench_batch(args, scgr, torch, dev, args.steps, args.warmup)
         diff = bench_diff(args, scgr, torch, dev, args.steps, args.warmup)
         scale = bench_scale(args, scgr, torch, dev, args.steps, args.warmup)
+        nxt = bench_next(args, scgr, torch, dev, args.steps, args.warmup, Xd, Yd)
 
     if rank != 0:
         if ws > 1:
@@ -668,6 +742,7 @@ def main():
         "batch": batch,
         "differentiation": diff,
         "scale_case": scale,
+        "next_rows": nxt,
     }
     line["peaks_measured"] = measured_peaks(scgr, num_sms, sm_mhz or sm_max_mhz)
     if ws == 1 and not args.no_cpu_baseline:
