@@ -186,8 +186,11 @@ SCGR_EXPORT scgr_status scgr_set_neighbourhood(scgr_ctx* ctx, int k, double radi
 
 /* Nearest reference point of q_dev [nq][3] (float32): index int32 [nq] and
  * float32 key (squared distance, the kNN key of R1) [nq]; either output may
- * be NULL.  Ties go to the lower index.  Enqueued.  STATE without a
- * reference. */
+ * be NULL.  Ties go to the lower index.  References of at least
+ * SCGR_TUNE_KNN_GRID_MIN points are searched through an exact uniform grid
+ * (same result as brute force; queries may lie outside the reference's box),
+ * which synchronises the stream once for the bounding box; smaller ones by
+ * brute force, enqueued.  STATE without a reference. */
 SCGR_EXPORT scgr_status scgr_nearest(scgr_ctx* ctx, const float* q_dev, int64_t nq, int32_t* idx_dev,
                                      float* key_dev);
 
@@ -195,8 +198,8 @@ SCGR_EXPORT scgr_status scgr_nearest(scgr_ctx* ctx, const float* q_dev, int64_t 
  * of the template that moved between captures stay unaligned).  For every
  * point of the moved template s Y0 R + t, mask_dev[i] = 1 (uint8) if its
  * nearest reference point is farther than `threshold`, else 0; dist_dev
- * (nullable, float32 [m]) receives that distance.  Enqueued.  STATE before
- * descriptors. */
+ * (nullable, float32 [m]) receives that distance.  The search is that of
+ * scgr_nearest.  STATE before descriptors. */
 SCGR_EXPORT scgr_status scgr_change_mask(scgr_ctx* ctx, double threshold, uint8_t* mask_dev, float* dist_dev);
 
 /* Forces at the current pose without updating it: per template point

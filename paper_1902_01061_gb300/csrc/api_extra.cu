@@ -19,8 +19,7 @@ scgr_status scgr_nearest(scgr_ctx* c, const float* q_dev, int64_t nq, int32_t* i
   c->err.clear();
   if (!c->have_X) return fail(c, SCGR_ERR_STATE, "set the reference first");
   if (nq < 0 || nq > (int64_t(1) << 30)) return fail(c, SCGR_ERR_INVALID_ARG, "bad query count");
-  SCGR_CK(c, launch_nearest(c->L(), (const float4*)c->X4.p, (int)c->n, q_dev, (int)nq, idx_dev, key_dev));
-  return SCGR_OK;
+  return nearest_reference(c, q_dev, (int)nq, idx_dev, key_dev);
 }
 
 scgr_status scgr_change_mask(scgr_ctx* c, double threshold, uint8_t* mask_dev, float* dist_dev) {
@@ -33,8 +32,8 @@ scgr_status scgr_change_mask(scgr_ctx* c, double threshold, uint8_t* mask_dev, f
   SCGR_CK(c, ensure(c->cd_moved, (size_t)m * 3 * sizeof(float)));
   SCGR_CK(c, ensure(c->cd_key, (size_t)m * sizeof(float)));
   SCGR_CK(c, launch_apply(c->L(), (const float4*)c->Y4.p, m, c->pose, (float*)c->cd_moved.p));
-  SCGR_CK(c, launch_nearest(c->L(), (const float4*)c->X4.p, (int)c->n, (const float*)c->cd_moved.p, m, nullptr,
-                            (float*)c->cd_key.p));
+  const scgr_status st = nearest_reference(c, (const float*)c->cd_moved.p, m, nullptr, (float*)c->cd_key.p);
+  if (st != SCGR_OK) return st;
   SCGR_CK(c, launch_threshold(c->L(), (const float*)c->cd_key.p, m, (float)(threshold * threshold), mask_dev,
                               dist_dev));
   return SCGR_OK;

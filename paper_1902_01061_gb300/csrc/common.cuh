@@ -244,6 +244,10 @@ cudaError_t launch_knn_grid(Launch L, const float4* P, int n, int k, const GridS
                             int32_t* out);
 cudaError_t launch_nearest(Launch L, const float4* P, int n, const float* q3, int nq, int32_t* idx_out,
                            float* key_out);
+cudaError_t launch_grid_build(Launch L, const float4* P, int n, const GridSpec& gs, int* cell_of, int* count,
+                              int* start, int* cursor, int* block_tot, float4* sorted, int* sorted_idx);
+cudaError_t launch_nearest_grid(Launch L, const float4* sorted, const int* sorted_idx, const int* start,
+                                const GridSpec& gs, const float* q3, int nq, int32_t* idx_out, float* key_out);
 cudaError_t launch_threshold(Launch L, const float* key, int nq, float thr2, uint8_t* mask, float* dist);
 cudaError_t launch_scale_double(Launch L, double* v, double f);
 cudaError_t launch_radius_curvature(Launch L, const float4* P, int n, const double* e_dev, double scale2,

@@ -119,6 +119,7 @@ scgr_status set_cloud(scgr_ctx* c, const float* xyz, int64_t n, bool host, bool 
 scgr_status force_launch(scgr_ctx* c);
 scgr_status collect_timing(scgr_ctx* c);
 scgr_status knn_cloud(scgr_ctx* c, const float4* P, int n, int32_t* out);
+scgr_status nearest_reference(scgr_ctx* c, const float* q3, int nq, int32_t* idx_out, float* key_out);
 scgr_status curvatures(scgr_ctx* c, int k, double radius_scale, double sigma_scale);
 scgr_status replan(scgr_ctx* c);
 scgr_status enqueue_iterations(scgr_ctx* c, int iters);

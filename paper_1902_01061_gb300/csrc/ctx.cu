@@ -149,14 +149,9 @@ scgr_status collect_timing(scgr_ctx* c) {
   return SCGR_OK;
 }
 
-// k nearest neighbours of one cloud: brute force below knn_grid_min points,
-// the exact grid search above (one host synchronisation for the box).
-scgr_status knn_cloud(scgr_ctx* c, const float4* P, int n, int32_t* out) {
-  const int k = c->prm.k;
-  if ((int64_t)n < c->knn_grid_min) {
-    SCGR_CK(c, launch_knn(c->L(), P, n, k, out));
-    return SCGR_OK;
-  }
+// Grid spec of a cloud and the workspace of its grid (one host
+// synchronisation for the bounding box).
+static scgr_status grid_setup(scgr_ctx* c, const float4* P, int n, GridSpec* gs_out) {
   SCGR_CK(c, ensure(c->gbb, sizeof(float) * (256 * 6 + 8)));
   float* part = (float*)c->gbb.p;
   SCGR_CK(c, launch_bbox(c->L(), P, n, part, part + 256 * 6));
@@ -172,8 +167,43 @@ scgr_status knn_cloud(scgr_ctx* c, const float4* P, int n, int32_t* out) {
   SCGR_CK(c, ensure(c->gblock, (size_t)((ncell + 1023) / 1024 + 1) * sizeof(int)));
   SCGR_CK(c, ensure(c->gsorted, (size_t)n * sizeof(float4)));
   SCGR_CK(c, ensure(c->gsidx, (size_t)n * sizeof(int)));
+  *gs_out = gs;
+  return SCGR_OK;
+}
+
+// k nearest neighbours of one cloud: brute force below knn_grid_min points,
+// the exact grid search above.
+scgr_status knn_cloud(scgr_ctx* c, const float4* P, int n, int32_t* out) {
+  const int k = c->prm.k;
+  if ((int64_t)n < c->knn_grid_min) {
+    SCGR_CK(c, launch_knn(c->L(), P, n, k, out));
+    return SCGR_OK;
+  }
+  GridSpec gs;
+  const scgr_status st = grid_setup(c, P, n, &gs);
+  if (st != SCGR_OK) return st;
   SCGR_CK(c, launch_knn_grid(c->L(), P, n, k, gs, (int*)c->gcell.p, (int*)c->gcount.p, (int*)c->gstart.p,
                              (int*)c->gcursor.p, (int*)c->gblock.p, (float4*)c->gsorted.p, (int*)c->gsidx.p, out));
+  return SCGR_OK;
+}
+
+// Nearest reference point of nq external queries (float32 [nq][3] on the
+// device): brute force below knn_grid_min reference points, else the exact
+// grid search over a grid of the reference (the same result).
+scgr_status nearest_reference(scgr_ctx* c, const float* q3, int nq, int32_t* idx_out, float* key_out) {
+  const float4* X4 = (const float4*)c->X4.p;
+  const int n = (int)c->n;
+  if ((int64_t)n < c->knn_grid_min) {
+    SCGR_CK(c, launch_nearest(c->L(), X4, n, q3, nq, idx_out, key_out));
+    return SCGR_OK;
+  }
+  GridSpec gs;
+  const scgr_status st = grid_setup(c, X4, n, &gs);
+  if (st != SCGR_OK) return st;
+  SCGR_CK(c, launch_grid_build(c->L(), X4, n, gs, (int*)c->gcell.p, (int*)c->gcount.p, (int*)c->gstart.p,
+                               (int*)c->gcursor.p, (int*)c->gblock.p, (float4*)c->gsorted.p, (int*)c->gsidx.p));
+  SCGR_CK(c, launch_nearest_grid(c->L(), (const float4*)c->gsorted.p, (const int*)c->gsidx.p,
+                                 (const int*)c->gstart.p, gs, q3, nq, idx_out, key_out));
   return SCGR_OK;
 }
 

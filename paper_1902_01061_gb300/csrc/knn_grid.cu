@@ -128,19 +128,19 @@ __device__ __forceinline__ bool lex_less(float ka, int ia, float kb, int ib) {
   return ka < kb || (ka == kb && ia < ib);
 }
 
+// The k (<= KC) first (key, index) neighbours of query q among the gridded
+// points: shells of cells around q's cell (clamped to the grid, so q may lie
+// outside the box), stopping once the k-th key is certified.  Every point
+// not yet scanned lies beyond a face of the scanned cube that has grid cells
+// behind it, and q is on the inner side of each such face, so its distance
+// to q is at least the distance dist_out from q to the nearest such face.
 template <int KC>
-__global__ void __launch_bounds__(GRID_TPB)
-    knn_grid_query_kernel(const float4* __restrict__ sorted, const int* __restrict__ sorted_idx,
-                          const int* __restrict__ start, int n, int k, GridSpec gs, int32_t* __restrict__ out) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= n) return;
-  const float4 q = sorted[t];  // queries in cell order: neighbouring threads share cells
-  const int qi = sorted_idx[t];
+__device__ __forceinline__ void grid_scan(const float4 q, const float4* __restrict__ sorted,
+                                          const int* __restrict__ sorted_idx, const int* __restrict__ start,
+                                          int k, const GridSpec& gs, float (&kd)[KC], int (&ki)[KC]) {
   const int cx = cell_coord(q.x, gs.o[0], gs.inv_h, gs.g[0]);
   const int cy = cell_coord(q.y, gs.o[1], gs.inv_h, gs.g[1]);
   const int cz = cell_coord(q.z, gs.o[2], gs.inv_h, gs.g[2]);
-  float kd[KC];
-  int ki[KC];
 #pragma unroll
   for (int m = 0; m < KC; ++m) {
     kd[m] = INFINITY;
@@ -207,9 +207,39 @@ __global__ void __launch_bounds__(GRID_TPB)
     const int kk = k < KC ? k : KC;
     if (ki[kk - 1] != INT_MAX && dout > 0.0 && (double)kd[kk - 1] < dout * dout * (1.0 - 1e-6)) break;
   }
+}
+
+// k nearest neighbours of every point of the gridded cloud itself.
+template <int KC>
+__global__ void __launch_bounds__(GRID_TPB)
+    knn_grid_query_kernel(const float4* __restrict__ sorted, const int* __restrict__ sorted_idx,
+                          const int* __restrict__ start, int n, int k, GridSpec gs, int32_t* __restrict__ out) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const float4 q = sorted[t];  // queries in cell order: neighbouring threads share cells
+  const int qi = sorted_idx[t];
+  float kd[KC];
+  int ki[KC];
+  grid_scan<KC>(q, sorted, sorted_idx, start, k, gs, kd, ki);
 #pragma unroll
   for (int m = 0; m < KC; ++m)
     if (m < k) out[(int64_t)qi * k + m] = ki[m];
+}
+
+// Nearest gridded point (first of the (key, index) order) of each of nq
+// external queries q3 [nq][3] (float32); key = the float32 squared distance.
+__global__ void __launch_bounds__(GRID_TPB)
+    nearest_grid_kernel(const float4* __restrict__ sorted, const int* __restrict__ sorted_idx,
+                        const int* __restrict__ start, GridSpec gs, const float* __restrict__ q3, int nq,
+                        int32_t* __restrict__ idx_out, float* __restrict__ key_out) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nq) return;
+  const float4 q = make_float4(q3[3 * (size_t)t], q3[3 * (size_t)t + 1], q3[3 * (size_t)t + 2], 0.f);
+  float kd[1];
+  int ki[1];
+  grid_scan<1>(q, sorted, sorted_idx, start, 1, gs, kd, ki);
+  if (idx_out) idx_out[t] = ki[0];
+  if (key_out) key_out[t] = kd[0];
 }
 
 // Grid spec from the bounding box: cell edge h = sqrt(8 A / n) with A the box
@@ -248,9 +278,10 @@ cudaError_t launch_bbox(Launch L, const float4* P, int n, float* part, float* ou
   return cudaGetLastError();
 }
 
-cudaError_t launch_knn_grid(Launch L, const float4* P, int n, int k, const GridSpec& gs, int* cell_of, int* count,
-                            int* start, int* cursor, int* block_tot, float4* sorted, int* sorted_idx,
-                            int32_t* out) {
+// Counting sort of the n points into the cells of gs: sorted / sorted_idx in
+// cell order, start[ncell + 1] the cell offsets.
+cudaError_t launch_grid_build(Launch L, const float4* P, int n, const GridSpec& gs, int* cell_of, int* count,
+                              int* start, int* cursor, int* block_tot, float4* sorted, int* sorted_idx) {
   const int64_t ncell = grid_cells(gs);
   cudaError_t e = cudaMemsetAsync(count, 0, (size_t)ncell * sizeof(int), L.stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(cursor, 0, (size_t)ncell * sizeof(int), L.stream);
@@ -262,11 +293,29 @@ cudaError_t launch_knn_grid(Launch L, const float4* P, int n, int k, const GridS
   scan_blocks_kernel<<<1, 32, 0, L.stream>>>(block_tot, nsb, start, (int)ncell);
   scan_add_kernel<<<(int)((ncell + tpb - 1) / tpb), tpb, 0, L.stream>>>(start, (int)ncell, block_tot);
   scatter_kernel<<<(n + tpb - 1) / tpb, tpb, 0, L.stream>>>(P, n, cell_of, start, cursor, sorted, sorted_idx);
+  if (L.counter) *L.counter += 5;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_knn_grid(Launch L, const float4* P, int n, int k, const GridSpec& gs, int* cell_of, int* count,
+                            int* start, int* cursor, int* block_tot, float4* sorted, int* sorted_idx,
+                            int32_t* out) {
+  cudaError_t e = launch_grid_build(L, P, n, gs, cell_of, count, start, cursor, block_tot, sorted, sorted_idx);
+  if (e != cudaSuccess) return e;
   const unsigned qb = (unsigned)((n + GRID_TPB - 1) / GRID_TPB);
   if (k <= 8) knn_grid_query_kernel<8><<<qb, GRID_TPB, 0, L.stream>>>(sorted, sorted_idx, start, n, k, gs, out);
   else if (k <= 16) knn_grid_query_kernel<16><<<qb, GRID_TPB, 0, L.stream>>>(sorted, sorted_idx, start, n, k, gs, out);
   else knn_grid_query_kernel<32><<<qb, GRID_TPB, 0, L.stream>>>(sorted, sorted_idx, start, n, k, gs, out);
-  if (L.counter) *L.counter += 6;
+  if (L.counter) *L.counter += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_nearest_grid(Launch L, const float4* sorted, const int* sorted_idx, const int* start,
+                                const GridSpec& gs, const float* q3, int nq, int32_t* idx_out, float* key_out) {
+  if (nq <= 0) return cudaSuccess;
+  nearest_grid_kernel<<<(nq + GRID_TPB - 1) / GRID_TPB, GRID_TPB, 0, L.stream>>>(sorted, sorted_idx, start, gs, q3,
+                                                                                nq, idx_out, key_out);
+  if (L.counter) *L.counter += 1;
   return cudaGetLastError();
 }
 

@@ -66,13 +66,21 @@ def test_set_neighbourhood_rejects_bad_values():
                 scgr.scgr_set_neighbourhood(g.ctx, *args)
 
 
-def test_nearest_bit_exact():
+@pytest.mark.parametrize("grid", [False, True])
+def test_nearest_bit_exact(grid):
+    """Brute force and (forced) exact grid search against the oracle, with
+    queries inside and far outside the reference's box, queries on reference
+    points, and duplicated reference points (ties to the lower index)."""
     import torch
     sc = synth.scale_case()
     X = sc.X[synth.subsample(sc.X, 3000, 71)]
+    X = np.concatenate([X, X[:50]])                  # exact duplicates: equal keys
     Q = sc.Y0[synth.subsample(sc.Y0, 1200, 72)]
+    far = (3.0 * Q[:100] + np.float32(2.5)).astype(np.float32)
+    Q = np.concatenate([Q, far, X[:40], X[3000:3010]]).astype(np.float32)
     idx_ref, key_ref = O.nearest(Q, X)
-    with Gpu(X, X) as g:
+    tune = {scgr.SCGR_TUNE_KNN_GRID_MIN: 0} if grid else {scgr.SCGR_TUNE_KNN_GRID_MIN: 1 << 30}
+    with Gpu(X, X, tune=tune) as g:
         idx = torch.empty(len(Q), dtype=torch.int32, device="cuda")
         key = torch.empty(len(Q), dtype=torch.float32, device="cuda")
         scgr.scgr_nearest(g.ctx, torch.from_numpy(Q).cuda(), idx, key)
@@ -80,7 +88,35 @@ def test_nearest_bit_exact():
         np.testing.assert_array_equal(key.cpu().numpy(), key_ref)
 
 
-def test_change_mask_at_identity_pose():
+def test_nearest_grid_at_full_size():
+    """The 1M-point reference of the benchmark workload (grid search by
+    default): 4,096 template points and 512 points outside the box, equal to
+    the brute-force kernel on every query and to the oracle on sampled ones."""
+    import torch
+    big = synth.large_case()
+    rng = np.random.default_rng(83)
+    Q = big.Y0[rng.choice(len(big.Y0), size=4096, replace=False)]
+    Q = np.concatenate([Q, (Q[:512] * 2.0 + np.float32(1.5)).astype(np.float32)])
+    Qd = torch.from_numpy(Q).cuda()
+    out = {}
+    for name, gmin in (("grid", 65536), ("brute", 1 << 30)):
+        with Gpu(big.X, big.Y0[:64], tune={scgr.SCGR_TUNE_KNN_GRID_MIN: gmin}) as g:
+            idx = torch.empty(len(Q), dtype=torch.int32, device="cuda")
+            key = torch.empty(len(Q), dtype=torch.float32, device="cuda")
+            scgr.scgr_nearest(g.ctx, Qd, idx, key)
+            out[name] = (idx.cpu().numpy(), key.cpu().numpy())
+    check("nearest: grid vs brute-force indices differing (1M reference)",
+          np.count_nonzero(out["grid"][0] != out["brute"][0]), 0)
+    np.testing.assert_array_equal(out["grid"][1], out["brute"][1])
+    sample = np.concatenate([np.arange(0, 4096, 97), np.arange(4096, 4608, 31)])
+    idx_ref, key_ref = O.nearest(Q[sample], big.X)
+    check("nearest: grid vs oracle indices differing (1M reference, sampled queries)",
+          np.count_nonzero(out["grid"][0][sample] != idx_ref), 0)
+    np.testing.assert_array_equal(out["grid"][1][sample], key_ref)
+
+
+@pytest.mark.parametrize("grid", [False, True])
+def test_change_mask_at_identity_pose(grid):
     """A template whose part moved between captures: the moved part is
     flagged.  At the identity pose the moved template is Y0 itself, so the
     oracle gets exactly the GPU's query points."""
@@ -92,7 +128,7 @@ def test_change_mask_at_identity_pose():
     Y0[:200] += np.float32(0.2)                      # a part that moved
     thr = 0.05
     mask_ref, dist_ref = O.change_mask(Y0, X, thr)
-    with Gpu(X, Y0) as g:
+    with Gpu(X, Y0, tune={scgr.SCGR_TUNE_KNN_GRID_MIN: 0 if grid else 1 << 30}) as g:
         mask = torch.empty(len(Y0), dtype=torch.uint8, device="cuda")
         dist = torch.empty(len(Y0), dtype=torch.float32, device="cuda")
         scgr.scgr_change_mask(g.ctx, thr, mask, dist)
