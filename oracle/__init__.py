@@ -25,13 +25,20 @@ Functions and their pins (the tests under ``tests/test_oracle_*.py``):
                        curvature when the radius neighbourhood is the whole
                        cloud.
 * ``register_pyramid`` - the pyramidal schedule of Sec. IV; pinned to
-                       ``register`` for a single level.
+                       ``register`` for a single level, for two equal levels
+                       (template and Eq. 12 position carried over), for a
+                       sigma scale (times the reference std), and to one
+                       method step with a second level's own descriptors.
 * ``nearest`` / ``change_mask`` - the change-detection post-pass; pinned to
                        the scalar brute force of the kNN pins (k = 1).
 * ``sigma_auto``     - R3; pinned to a closed form (two-valued population).
 * ``forces``         - Eq. 5 with Eq. 3, 10, 11; pinned to the two-point hand
                        case, the p=1 closed forms, Newton's third law,
                        rotation/translation equivariance and scaling.
+* ``force_row_magnitudes`` - per-row sums of term magnitudes of Eq. 5 (the
+                       condition number of each force sum); pinned to hand
+                       cases (one pull: kappa = 1; balanced pulls: f = 0) and
+                       to the Euclidean norm of an explicit term list.
 * ``potential`` / ``potential_grad`` - the potential whose negative gradient is
                        Eq. 5; pinned by central finite differences.
 * ``force_vjp``      - the force field's vector-Jacobian product; pinned by
@@ -59,6 +66,7 @@ from .scgr_oracle import (  # noqa: F401
     descriptors,
     forces,
     forces_rows,
+    force_row_magnitudes,
     potential,
     potential_grad,
     pose_potential_and_grad,

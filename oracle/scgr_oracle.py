@@ -230,6 +230,43 @@ def forces(Y, X, aY, aX, sigma, p, g_mode):
     return forces_rows(Y, X, aY, aX, sigma, p, g_mode, None)
 
 
+def force_row_magnitudes(Y, X, aY, aX, sigma, p, g_mode, rows=None, centre=None):
+    """Magnitudes of the terms of the Eq. 5 sum, for judging how well each
+    row's force is conditioned.  For template row i with pair weight
+    w_ij = g(s_ij) d_ij^(p-1) and r_ij = Y_i - X_j (the same terms as
+    `forces_rows`), returns per row, in float64, summed over j in order:
+
+      A_i = sum_j |w_ij r_ij|          (Euclidean norm of each term)
+      B_i = sum_j w_ij |X_j - centre|  (centre: 3-vector, default the origin)
+      W_i = sum_j w_ij
+
+    kappa_i = A_i / |f_i| is the condition number of the sum that gives f_i:
+    the factor by which relative errors of its terms can grow in the total.
+    B_i + |Y_i - centre| W_i bounds the size of the two sums sum_j w_ij X_j
+    and Y_i sum_j w_ij when f_i is formed as their difference in a frame
+    with that centre."""
+    Y = np.asarray(Y, dtype=np.float64)
+    X = np.asarray(X, dtype=np.float64)
+    aY = np.asarray(aY, dtype=np.float64)
+    aX = np.asarray(aX, dtype=np.float64)
+    c = np.zeros(3) if centre is None else np.asarray(centre, dtype=np.float64)
+    rows = np.arange(len(Y)) if rows is None else np.asarray(rows)
+    A = np.zeros(len(rows))
+    B = np.zeros(len(rows))
+    W = np.zeros(len(rows))
+    xdist = np.sqrt(np.sum((X - c) ** 2, axis=1))
+    chunk = max(1, (1 << 21) // max(len(X), 1))
+    for c0 in range(0, len(rows), chunk):
+        rr = rows[c0:c0 + chunk]
+        r, d, g = _pair_terms(Y[rr], X, aY[rr], aX, sigma, p, g_mode)
+        with np.errstate(invalid="ignore", divide="ignore"):
+            w = np.where(d > 0, g * d ** (p - 1.0), g if p == 1.0 else 0.0)   # R12
+        A[c0:c0 + len(rr)] = np.sum(w * d, axis=1)                          # |w r| = w d
+        B[c0:c0 + len(rr)] = w @ xdist
+        W[c0:c0 + len(rr)] = np.sum(w, axis=1)
+    return A, B, W
+
+
 def potential(Y, X, aY, aX, sigma, p, g_mode) -> float:
     """U = sum_i sum_j g(s_ij) d_ij^(p+1) / (p+1); its gradient with respect to
     Y_i is -f_i of Eq. 5 (descriptors held fixed)."""

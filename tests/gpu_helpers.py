@@ -4,7 +4,25 @@ check() asserts a measured error against its tolerance and, when the
 environment variable SCGR_PARITY_LOG names a file, appends the measurement
 to it (one JSON object per line: test id, quantity, value, tolerance), so
 that a GPU run states the error of every result against the FP64 oracle
-(tests/parity_report.py tabulates the log)."""
+(tests/parity_report.py tabulates the log).
+
+check_rows() adds the per-row view of a force check: a relative L2 over many
+rows can hide a single row whose sum cancels, so every checked row i must meet
+
+    |f_got,i - f_i| / |f_i| <= C_ROW * 2^-24 * kappa'_i,
+    kappa'_i = sum_j w_ij (|X_j - c| + |Y_i - c|) / |f_i|,
+
+with c the reference mean (the frame in which the kernel accumulates
+sum_j w_ij X_j and sum_j w_ij, whose difference is f_i).  kappa'_i is at least
+the condition number kappa_i = sum_j |w_ij r_ij| / |f_i| of the Eq. 5 sum (the
+triangle inequality), which is logged beside it.  The bound counts the
+rounding of each pair weight (ex2, sqrt, a few products: < 8 ulp), the
+float32 tile sums under Kahan compensation across tiles, and the squared
+distance evaluated as |X'|^2 + |Y'|^2 - 2 X'.Y', whose absolute error
+(about 2^-24 (|X'|^2 + |Y'|^2)) enters f_i only through w_ij r_ij and so
+stays within the same magnitude sums; C_ROW = 64 leaves room for all of them.
+W_i is a sum of positive terms (condition 1): its per-row relative error must
+stay below C_ROW * 2^-24."""
 import json
 import math
 import os
@@ -26,6 +44,44 @@ def rel_l2(a, b):
     a = np.asarray(a, np.float64)
     b = np.asarray(b, np.float64)
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+C_ROW = 64.0
+EPS32 = 2.0 ** -24
+
+
+def check_rows(what, got4, f_ref, W_ref, Y, X, aY, aX, sigma, p, g_mode, rows=None):
+    """Per-row force parity (see the module docstring).  got4: GPU rows
+    (fx, fy, fz, W) for template rows `rows` (all if None) of the template at
+    positions Y; f_ref, W_ref: the oracle's values for the same rows.
+    Returns (worst per-row relative error of f, worst kappa_i)."""
+    import oracle as O
+    got4 = np.asarray(got4, np.float64)
+    f_ref = np.asarray(f_ref, np.float64)
+    W_ref = np.asarray(W_ref, np.float64)
+    Y = np.asarray(Y, np.float64)
+    X = np.asarray(X, np.float64)
+    c = X.mean(axis=0)
+    rows_idx = np.arange(len(Y)) if rows is None else np.asarray(rows)
+    A, B, Wm = O.force_row_magnitudes(Y, X, aY, aX, sigma, p, g_mode, rows_idx, centre=c)
+    fn = np.linalg.norm(f_ref, axis=1)
+    live = fn > 0
+    err = np.linalg.norm(got4[:, :3] - f_ref, axis=1)
+    rel = err[live] / fn[live]
+    kappa = A[live] / fn[live]
+    bound = (B[live] + np.linalg.norm(Y[rows_idx][live] - c, axis=1) * Wm[live]) / fn[live]
+    ratio = rel / (EPS32 * bound)
+    i_worst = int(np.argmax(ratio)) if ratio.size else 0
+    check(f"{what}: per-row f error / (2^-24 kappa'_i), worst row", float(ratio.max()) if ratio.size else 0.0, C_ROW)
+    check(f"{what}: per-row relative error of f_i, worst row (its kappa_i = "
+          f"{float(kappa[i_worst]) if kappa.size else 0.0:.3g})", float(rel.max()) if rel.size else 0.0, float("inf"))
+    check(f"{what}: row condition kappa_i, largest", float(kappa.max()) if kappa.size else 0.0, float("inf"))
+    check(f"{what}: row condition kappa_i, median", float(np.median(kappa)) if kappa.size else 0.0, float("inf"))
+    wpos = W_ref > 0
+    relW = np.abs(got4[:, 3][wpos] - W_ref[wpos]) / W_ref[wpos]
+    check(f"{what}: per-row relative error of W_i / 2^-24, worst row", float(relW.max() / EPS32) if relW.size else 0.0,
+          C_ROW)
+    return (float(rel.max()) if rel.size else 0.0), (float(kappa.max()) if kappa.size else 0.0)
 
 
 def check(quantity, value, tol):

@@ -156,9 +156,9 @@ def test_full_size_batch_in_the_benchmark_configuration():
     """The benchmark's 512-pair batch (500-20,000 points per cloud, log-uniform;
     5.4 M points) at full size, in the launch configuration the benchmark's
     autotuner picks on GB300 (2 points per thread, 16-tile chunks, one CUDA
-    graph), for 20 iterations: the three smallest pairs against the FP64
-    oracle, and three other pairs (largest, median, one more) against
-    one-pair-per-call runs of the same library."""
+    graph), for 20 iterations: the three smallest pairs and the largest pair
+    against the FP64 oracle, and three pairs (largest, median, one more)
+    against one-pair-per-call runs of the same library."""
     pairs = synth.batch_case()
     iters = 20
     tuning = ((scgr.SCGR_TUNE_BATCH_P, 2), (scgr.SCGR_TUNE_BATCH_CHUNK_TILES, 16))
@@ -175,3 +175,17 @@ def test_full_size_batch_in_the_benchmark_configuration():
         with Gpu(pp.X, pp.Y0, p=2.0) as g:
             single = g.run(iters)
         assert close(res[i], single, synth.bbox_diag(pp.X), "full-size batch vs one call per pair")
+    # the largest pair against the FP64 oracle as well, its force rows spread
+    # over a spawned process pool (row blocks added in block order)
+    import multiprocessing as mp
+    import os
+    pp = pairs[order[-1]]
+    prm = O.Params(p=2.0)
+    d = O.descriptors(pp.X, pp.Y0, prm)
+    slim = {"aX": d["aX"], "aY": d["aY"], "sigma": d["sigma"]}
+    workers = max(1, min(16, os.cpu_count() or 1))
+    blocks = np.array_split(np.arange(len(pp.Y0)), workers)
+    with mp.get_context("spawn").Pool(workers) as pool:
+        o = O.register_from_partials(pp.X, pp.Y0, prm, iters, slim, blocks, map_partials=pool.map)
+    assert close(res[order[-1]], (o["R"], o["t"], o["s"]), synth.bbox_diag(pp.X),
+                 f"full-size batch, largest pair ({len(pp.X):,} x {len(pp.Y0):,}) vs oracle")

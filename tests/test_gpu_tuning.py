@@ -6,7 +6,7 @@ import pytest
 
 import oracle as O
 from paper_1902_01061_gb300 import autotune, scgr, synth
-from tests.gpu_helpers import Gpu, check, check_pose, rel_l2
+from tests.gpu_helpers import Gpu, check, check_pose, check_rows, rel_l2
 
 pytestmark = pytest.mark.gpu
 
@@ -40,6 +40,8 @@ def test_every_tile_shape_matches_oracle(P, tpb, splits, occ):
         f4 = g.forces()
     check(f"force f_i, tile shape P={P} tpb={tpb} splits={splits} occ={occ}: relative L2", rel_l2(f4[:, :3], f_ref), 1e-5)
     check(f"weight W_i, tile shape P={P} tpb={tpb} splits={splits} occ={occ}: relative L2", rel_l2(f4[:, 3], W_ref), 1e-5)
+    check_rows(f"force rows, tile shape P={P} tpb={tpb} splits={splits} occ={occ}", f4, f_ref, W_ref, Y0, X,
+               d["aY"], d["aX"], d["sigma"], 2.0, 1)
 
 
 @pytest.mark.parametrize("P,tpb", [(1, 128), (2, 256), (4, 256)])
@@ -65,6 +67,9 @@ def test_rsqrt_distance_form_matches_oracle(P, tpb):
     check("force f_i, rsqrt distance form: relative L2", rel_l2(f_rs[:, :3], f_ref), 1e-5)
     check("weight W_i, rsqrt distance form: relative L2", rel_l2(f_rs[:, 3], W_ref), 1e-5)
     check("rsqrt vs sqrt distance form: relative L2", rel_l2(f_rs, f_sq), 1e-5)
+    for what, f4 in (("rsqrt", f_rs), ("sqrt", f_sq)):
+        check_rows(f"force rows, {what} distance form (template holds copies of reference points)", f4, f_ref, W_ref,
+                   Y0, X, d["aY"], d["aX"], d["sigma"], 2.0, 1)
 
 
 def test_autotuner_picks_and_caches(tmp_path, monkeypatch):

@@ -11,6 +11,7 @@ from tests import test_oracle_curvature as TC
 from tests import test_oracle_forces as TF
 from tests import test_oracle_knn as TK
 from tests import test_oracle_pose as TP
+from tests import test_oracle_register as TR
 
 
 def _pair_terms_sign(Yi, X, aYi, aX, sigma, p, g_mode):
@@ -102,9 +103,40 @@ def _cloud_stats_unbiased(P):
     return mu, C, float(np.linalg.eigvalsh(C)[-1])
 
 
+def _pyramid_variant(position_reset=False, sigma_from_template=False, descriptors_on_moved=False):
+    """register_pyramid with one level-switch mistake planted (a copy of the
+    oracle's loop; the shared steps are the oracle's own functions)."""
+    from dataclasses import replace as dc_replace
+
+    def run(X, Y0, prm, levels):
+        X64 = np.asarray(X, dtype=np.float64)
+        Y = np.asarray(Y0, dtype=np.float64).copy()
+        total = sum(lv[0] for lv in levels)
+        E = prm.E if prm.E > 0 else total
+        _, _, eX = M.cloud_stats(X64)
+        s, R, t = 1.0, np.eye(3), np.zeros(3)
+        it = 0
+        for iters, k, rscale, sscale in levels:
+            lp = dc_replace(prm, k=k, radius_scale=rscale)
+            desc = M.descriptors(X, Y.astype(np.float32) if descriptors_on_moved else Y0, lp, sigma_scale=sscale)
+            if sigma_from_template:
+                desc["sigma"] = M.sigma_auto(desc["aY"]) * sscale
+            if position_reset:
+                it = 0
+            for _ in range(iters):
+                Y, info = M.step_once(Y, X64, desc, lp, it, E, eX)
+                c, Rinc, mu, dvec = info["c"], info["Rinc"], info["mu"], info["d"]
+                t = c * (t - mu) @ Rinc + mu + dvec
+                R = M.polar(R @ Rinc)
+                s = c * s
+                it += 1
+        return dict(R=R, t=t, s=s, Y=Y, iterations=it, E=E)
+    return run
+
+
 ORIG = {name: getattr(M, name) for name in
         ("_pair_terms", "forces_rows", "curvature", "kabsch", "knn", "scale_factor", "g_schedule", "rodrigues",
-         "cloud_stats")}
+         "cloud_stats", "register_pyramid")}
 
 CASES = {
     "force sign": ("_pair_terms", _pair_terms_sign, [TF.test_two_point_hand_case]),
@@ -126,6 +158,12 @@ CASES = {
     "axis-angle rotation transposed": ("rodrigues", _rodrigues_column_form,
                                        [TP.test_rodrigues_is_the_matrix_exponential_in_row_vector_form]),
     "unbiased covariance": ("cloud_stats", _cloud_stats_unbiased, [TP.test_cloud_stats_closed_form]),
+    "pyramid: Eq. 12 position reset per level": ("register_pyramid", _pyramid_variant(position_reset=True),
+                                                 [TR.test_pyramid_two_equal_levels_equal_one_long_level]),
+    "pyramid: sigma from the template curvatures": ("register_pyramid", _pyramid_variant(sigma_from_template=True),
+                                                    [TR.test_pyramid_sigma_scale_multiplies_reference_std]),
+    "pyramid: descriptors of the moved template": ("register_pyramid", _pyramid_variant(descriptors_on_moved=True),
+                                                   [TR.test_pyramid_second_level_uses_its_own_descriptors]),
 }
 
 
