@@ -198,7 +198,7 @@ def cpu_baseline(pair, p, g_mode, seconds=15.0):
     out = {"value": value, "unit": "pair-interactions/s", "cores": 1, "kind": "oracle",
            "sample": f"iteration-0 force pass (Eq. 5) of {nrows} template rows x {n} reference points "
                      f"in float64 numpy, single thread, {dt:.1f} s",
-           "cpu": _cpu_model(),
+           "cpu": _cpu_model(), "nproc": os.cpu_count() or 1,
            "extrapolated_s_per_iteration": n * m / value}
     try:
         allc = cpu_baseline_all_cores(pair, p, g_mode, dt / nrows)
@@ -209,15 +209,44 @@ def cpu_baseline(pair, p, g_mode, seconds=15.0):
     return out
 
 
+# Arm CPU part numbers (implementer 0x41) of the Neoverse cores that hosts
+# of this class carry; /proc/cpuinfo on Arm gives only the part number.
+ARM_PARTS = {"0xd0c": "Neoverse-N1", "0xd40": "Neoverse-V1", "0xd49": "Neoverse-N2", "0xd4f": "Neoverse-V2",
+             "0xd84": "Neoverse-V3", "0xd8e": "Neoverse-N3"}
+
+
 def _cpu_model():
+    """Host CPU model name, e.g. 'Neoverse-V2 (Arm part 0xd4f)' on an Arm host
+    or the 'model name' line on x86."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                name = line.split(":", 1)[1].strip()
+                if name and name != "-":
+                    return name
+    except (OSError, subprocess.SubprocessError):
+        pass
+    fields = {}
     try:
         for line in open("/proc/cpuinfo"):
-            if line.lower().startswith(("model name", "cpu part", "hardware")):
-                return line.split(":", 1)[1].strip()
+            if ":" in line:
+                k, v = line.split(":", 1)
+                fields.setdefault(k.strip().lower(), v.strip())
     except OSError:
         pass
+    if "model name" in fields:
+        return fields["model name"]
+    part = fields.get("cpu part")
+    if part:
+        name = ARM_PARTS.get(part.lower()) if fields.get("cpu implementer", "").lower() == "0x41" else None
+        return f"{name} (Arm part {part})" if name else f"Arm part {part}"
     import platform
     return platform.processor() or platform.machine()
+
+
+def _host_info():
+    return {"cpu": _cpu_model(), "nproc": os.cpu_count() or 1}
 
 
 _POOL_DATA = {}
@@ -261,6 +290,65 @@ def cpu_baseline_all_cores(pair, p, g_mode, per_row_s, seconds=10.0):
     return {"value": done * n / dt, "unit": "pair-interactions/s", "cores": cores, "kind": "oracle",
             "sample": f"iteration-0 force pass of {done} template rows x {n} reference points, float64 numpy, "
                       f"{cores} spawned processes over row blocks, {dt:.1f} s"}
+
+
+def oracle_runs():
+    """The FP64 oracle, as it stands, on the two configurations a host can
+    run end to end.  Config 1 (1,000 x 1,000, p = 2, 100 iterations): the
+    full registration (descriptors + iterations) on one thread, and with each
+    iteration's force rows spread over a spawned process pool of every core
+    (row blocks added in block order, `register_from_partials`).  Config 2
+    (35,000 x 30,800, p = 2, 200 iterations): the descriptor pass timed in
+    full, one whole iteration timed on every core, and one iteration's force
+    pass on one thread timed on a 1-in-64 row sample; the 200-iteration
+    totals are extrapolated from those (a full run takes hours on one
+    thread)."""
+    import multiprocessing as mp
+    import numpy as np
+    import oracle as O
+    from paper_1902_01061_gb300 import synth
+    cores = os.cpu_count() or 1
+    prm = O.Params(p=2.0)
+    out = {"kind": "oracle", "cpu": _cpu_model(), "nproc": cores}
+    t = synth.tiny()
+    t0 = time.perf_counter()
+    d = O.descriptors(t.X, t.Y0, prm)
+    O.register(t.X, t.Y0, prm, iterations=100, desc=d)
+    one = time.perf_counter() - t0
+    sc = synth.scale_case()
+    with mp.get_context("spawn").Pool(cores) as pool:
+        slim = {"aX": d["aX"], "aY": d["aY"], "sigma": d["sigma"]}
+        blocks = np.array_split(np.arange(len(t.Y0)), cores)
+        O.register_from_partials(t.X, t.Y0, prm, 1, slim, blocks, map_partials=pool.map)     # workers up
+        t0 = time.perf_counter()
+        d = O.descriptors(t.X, t.Y0, prm)
+        O.register_from_partials(t.X, t.Y0, prm, 100, {"aX": d["aX"], "aY": d["aY"], "sigma": d["sigma"]}, blocks,
+                                 map_partials=pool.map)
+        allc = time.perf_counter() - t0
+        out["config1_tiny"] = {
+            "workload": "1,000 x 1,000 points, p=2, k=16, 100 iterations (descriptors + iterations)",
+            "s_single_thread": one, "s_all_cores": allc, "cores": cores,
+            "pair_interactions_per_s_single_thread": 1000 * 1000 * 100 / one}
+        t0 = time.perf_counter()
+        d2 = O.descriptors(sc.X, sc.Y0, prm)
+        desc_s = time.perf_counter() - t0
+        slim2 = {"aX": d2["aX"], "aY": d2["aY"], "sigma": d2["sigma"]}
+        blocks2 = np.array_split(np.arange(len(sc.Y0)), cores)
+        t0 = time.perf_counter()
+        O.register_from_partials(sc.X, sc.Y0, prm, 1, slim2, blocks2, map_partials=pool.map)
+        it_all = time.perf_counter() - t0
+    rows = np.arange(0, len(sc.Y0), 64)
+    t0 = time.perf_counter()
+    O.forces_rows(sc.Y0, sc.X, d2["aY"], d2["aX"], d2["sigma"], 2.0, 1, rows)
+    it_one = (time.perf_counter() - t0) * len(sc.Y0) / len(rows)
+    n2, m2 = len(sc.X), len(sc.Y0)
+    out["config2_scale"] = {
+        "workload": f"{n2:,} x {m2:,} points, p=2, k=16, 200 iterations",
+        "descriptors_s": desc_s, "s_per_iteration_all_cores": it_all, "s_per_iteration_single_thread": it_one,
+        "extrapolated_s_all_cores": desc_s + 200 * it_all, "extrapolated_s_single_thread": desc_s + 200 * it_one,
+        "pair_interactions_per_s_all_cores": n2 * m2 / it_all, "cores": cores,
+        "sample": "descriptors in full; one full iteration on every core; one thread on a 1-in-64 row sample"}
+    return out
 
 
 def bench_batch(args, scgr, torch, dev, steps, warmup):
@@ -508,6 +596,129 @@ def bench_next(args, scgr, torch, dev, steps, warmup, Xd, Yd):
     return out
 
 
+def apply_plan(scgr, ctx, tuned):
+    """Pin the force plan the main leg's autotuner picked."""
+    if tuned and "P" in tuned:
+        scgr.scgr_set_tuning(ctx, scgr.SCGR_TUNE_FORCE_P, int(tuned["P"]))
+        scgr.scgr_set_tuning(ctx, scgr.SCGR_TUNE_FORCE_TPB, int(tuned["tpb"]))
+        scgr.scgr_set_tuning(ctx, scgr.SCGR_TUNE_FORCE_OCC, int(tuned.get("occ", 0)))
+        scgr.scgr_set_tuning(ctx, scgr.SCGR_TUNE_FORCE_RSQRT, int(tuned.get("rsqrt", 0)))
+
+
+def bench_g_equals_s(args, scgr, torch, dev, Xd, Yd, tuned, peak_basis):
+    """The g = s weighting of Sec. IV (every pair weighted by the similarity
+    alone, without the aX aY factor of Eq. 10) on the 1M x 1M workload, p = 2,
+    50 iterations: one whole registration (descriptors included) after a
+    short warm-up, with the force kernel timed by CUDA events on the
+    library's stream.  Per pair the counting convention drops the x aX flop:
+    21 flops."""
+    n, m = int(Xd.shape[0]), int(Yd.shape[0])
+    stream = torch.cuda.current_stream()
+    ctx = scgr.scgr_create(scgr.scgr_default_params(p=2.0, g_mode=0, k=16), stream)
+    try:
+        apply_plan(scgr, ctx, tuned)
+
+        def one(iters):
+            scgr.scgr_set_reference(ctx, Xd)
+            scgr.scgr_set_template(ctx, Yd)
+            scgr.scgr_compute_descriptors(ctx)
+            scgr.scgr_run(ctx, iters)
+            return scgr.scgr_get_result(ctx)
+
+        one(2)
+        torch.cuda.synchronize()
+        scgr.scgr_set_force_timing(ctx, True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        res = one(50)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        nforce, force_ms = scgr.scgr_get_force_timing(ctx)
+        scgr.scgr_set_force_timing(ctx, False)
+        plan = scgr.scgr_get_plan(ctx)
+    finally:
+        scgr.scgr_destroy(ctx)
+    reg_ms = e0.elapsed_time(e1)
+    avg = force_ms / max(nforce, 1)
+    achieved = 21 * n * m / (avg * 1e-3) / 1e12
+    peak, basis = peak_basis
+    return {"workload": f"{n:,} x {m:,}, g = s (Sec. IV), p = 2, k = 16, 50 iterations",
+            "ms_per_registration": reg_ms, "ms_per_iteration": reg_ms / 50,
+            "pair_interactions_per_s": n * m * 50 / (reg_ms * 1e-3), "plan": plan, "scale": res.s,
+            "roofline": {"bound": "alu", "kernel": "force_tile_kernel", "flops_per_pair": 21,
+                         "force_launch_ms": avg, "force_launches_timed": nforce, "achieved": achieved,
+                         "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "peak_basis": basis},
+            "timing": "CUDA events on the library stream around one registration; force launches by the library's "
+                      "own events"}
+
+
+def bench_radius_registration(scgr, torch, dev, steps):
+    """A whole registration with the radius neighbourhood of Sec. IV (radius
+    sqrt(e) of each cloud's covariance) on the 35,000 x 30,800 case: both
+    clouds' descriptors by the O(n^2) radius pass, then 200 iterations in a
+    CUDA graph."""
+    from paper_1902_01061_gb300 import synth
+    sc = synth.scale_case()
+    X = torch.from_numpy(sc.X).to(dev)
+    Y = torch.from_numpy(sc.Y0).to(dev)
+    ctx = scgr.scgr_create(scgr.scgr_default_params(p=2.0, neigh_mode=1, radius_scale=1.0, use_graph=1),
+                           torch.cuda.current_stream())
+    try:
+        def one():
+            scgr.scgr_set_reference(ctx, X)
+            scgr.scgr_set_template(ctx, Y)
+            scgr.scgr_compute_descriptors(ctx)
+            scgr.scgr_run(ctx, 200)
+            return scgr.scgr_get_result(ctx)
+        sec = _timed(one, max(1, min(steps, 3)), 1, torch)
+    finally:
+        scgr.scgr_destroy(ctx)
+    return {"workload": "35,000 x 30,800 points, radius neighbourhood sqrt(e) (scale 1.0), p=2, 200 iterations, "
+                        "CUDA graph", "ms_per_registration": sec * 1e3,
+            "timing": "host wall clock around synchronised calls"}
+
+
+def bench_tiny(scgr, torch, dev, steps):
+    """The 1,000 x 1,000 case (3-ellipsoid surface, 50 deg about x, p = 2,
+    100 iterations): the latency regime, where the per-iteration launches and
+    the float64 pose update dominate.  Whole registrations (descriptors +
+    100 iterations) and the iterations alone, with the loop replayed from a
+    CUDA graph and with eager launches."""
+    from paper_1902_01061_gb300 import synth
+    case = synth.tiny()
+    X = torch.from_numpy(case.X).to(dev)
+    Y = torch.from_numpy(case.Y0).to(dev)
+    out = {"workload": "1,000 x 1,000 points, 50 deg about x, p=2, k=16, 100 iterations"}
+    reps = max(5, min(steps, 20))
+    for use_graph in (1, 0):
+        ctx = scgr.scgr_create(scgr.scgr_default_params(p=2.0, use_graph=use_graph), torch.cuda.current_stream())
+        try:
+            def whole():
+                scgr.scgr_set_reference(ctx, X)
+                scgr.scgr_set_template(ctx, Y)
+                scgr.scgr_compute_descriptors(ctx)
+                scgr.scgr_run(ctx, 100)
+                scgr.scgr_get_result(ctx)
+            reg = _timed(whole, reps, 2, torch)
+
+            def iters_only():
+                scgr.scgr_set_state(ctx, state0)
+                scgr.scgr_run(ctx, 100)
+                scgr.scgr_get_result(ctx)
+            scgr.scgr_set_reference(ctx, X)
+            scgr.scgr_set_template(ctx, Y)
+            scgr.scgr_compute_descriptors(ctx)
+            state0 = scgr.scgr_get_state(ctx)
+            it = _timed(iters_only, reps, 2, torch)
+        finally:
+            scgr.scgr_destroy(ctx)
+        key = "graph" if use_graph else "eager"
+        out[key] = {"ms_per_registration": reg * 1e3, "ms_per_iteration": it * 1e3 / 100}
+    out["graph_speedup_per_iteration"] = out["eager"]["ms_per_iteration"] / out["graph"]["ms_per_iteration"]
+    out["timing"] = "host wall clock around synchronised calls, mean of repeated runs"
+    return out
+
+
 def run_reference(args, ws, rank):
     """The oracle arm: bounded samples of the same workload on the host cores."""
     if rank != 0:
@@ -569,6 +780,8 @@ def main():
     ap.add_argument("--batch-iters", type=int, default=100, help="iterations of the batched leg")
     ap.add_argument("--next-only", action="store_true",
                     help="only the leg of the widened rows (odd-p fast path, radius, pyramid, change mask)")
+    ap.add_argument("--oracle-only", action="store_true",
+                    help="only the oracle's timings on the host (sampled 1M x 1M force rows, configs 1 and 2)")
     ap.add_argument("--batch-plan", default=None, help="pin the batched force kernel 'P,CHUNK_TILES[,PERSISTENT]' (no autotuning)")
     ap.add_argument("--batch-eager", action="store_true", help="batched leg without the CUDA graph (for profilers)")
     ap.add_argument("--plan", default=None, help="pin the force kernel 'P,TPB[,OCC[,RSQRT]]' (no autotuning), e.g. 2,256,0,1")
@@ -576,6 +789,11 @@ def main():
     ws, rank, local = dist_env()
     if args.impl == "reference":
         return run_reference(args, ws, rank)
+    if args.oracle_only:
+        if rank == 0:
+            print(json.dumps({"leg": "oracle", "oracle_runs": oracle_runs(),
+                              "sampled": cpu_baseline(make_pair(args.workload), 2.0, 1)}), flush=True)
+        return 0
 
     import numpy as np
     import torch
@@ -603,8 +821,14 @@ def main():
         if rank == 0:
             dev = torch.device("cuda", local)
             pair = make_pair(args.workload)
-            out = bench_next(args, scgr, torch, dev, args.steps, args.warmup, torch.from_numpy(pair.X).to(dev),
-                             torch.from_numpy(pair.Y0).to(dev))
+            Xd, Yd = torch.from_numpy(pair.X).to(dev), torch.from_numpy(pair.Y0).to(dev)
+            out = bench_next(args, scgr, torch, dev, args.steps, args.warmup, Xd, Yd)
+            nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+            peak = (2 * FP32_LANES_PER_SM * nsm * 2070e6 / 1e12,
+                    f"2 x {FP32_LANES_PER_SM} FP32 lanes x {nsm} SMs x 2070 MHz (max clock)")
+            out["g_equals_s_full_size"] = bench_g_equals_s(args, scgr, torch, dev, Xd, Yd, None, peak)
+            out["radius_registration"] = bench_radius_registration(scgr, torch, dev, args.steps)
+            out["tiny_case"] = bench_tiny(scgr, torch, dev, args.steps)
             print(json.dumps({"leg": "next_rows", "steps": args.steps, **out}), flush=True)
         return 0
     wl = WORKLOADS[args.workload]
@@ -683,7 +907,7 @@ def main():
     force_avg_ms = force_ms / max(nforce, 1)
 
     # end to end through the host entry points (pinned host buffers)
-    e2e_steps = args.e2e_steps if args.e2e_steps is not None else args.steps
+    e2e_steps = args.e2e_steps if args.e2e_steps is not None else min(args.steps, 3)
     e2e = None
     if e2e_steps > 0:
         Xh = torch.from_numpy(pair.X).pin_memory().numpy()
@@ -709,28 +933,33 @@ def main():
         e2e = {"value": ws * pairs_per_step / e2e_s, "unit": "pair-interactions/s",
                "h2d_bytes_per_step": (n + m) * 12, "d2h_bytes_per_step": m * 12 + 8 * 13 + 8}
     scgr.scgr_destroy(ctx)
-    batch = diff = scale = nxt = None
+    sm_max_mhz = (clk or {}).get("sm_max_mhz") or 2070.0
+    sm_mhz = (clk or {}).get("sm_mhz")
+    peak_tflops = 2 * FP32_LANES_PER_SM * num_sms * sm_max_mhz * 1e6 / 1e12
+    peak_basis = f"2 x {FP32_LANES_PER_SM} FP32 lanes x {num_sms} SMs x {sm_max_mhz:.0f} MHz (max clock)"
+    batch = diff = scale = nxt = tiny = None
     if ws == 1 and not args.no_batch:
         batch = bench_batch(args, scgr, torch, dev, args.steps, args.warmup)
         diff = bench_diff(args, scgr, torch, dev, args.steps, args.warmup)
         scale = bench_scale(args, scgr, torch, dev, args.steps, args.warmup)
+        tiny = bench_tiny(scgr, torch, dev, args.steps)
         nxt = bench_next(args, scgr, torch, dev, args.steps, args.warmup, Xd, Yd)
+        nxt["g_equals_s_full_size"] = bench_g_equals_s(args, scgr, torch, dev, Xd, Yd, tuned,
+                                                       (peak_tflops, peak_basis))
+        nxt["radius_registration"] = bench_radius_registration(scgr, torch, dev, args.steps)
 
     if rank != 0:
         if ws > 1:
             dist.destroy_process_group()
         return 0
 
-    sm_max_mhz = (clk or {}).get("sm_max_mhz") or 2070.0
-    sm_mhz = (clk or {}).get("sm_mhz")
-    peak_tflops = 2 * FP32_LANES_PER_SM * num_sms * sm_max_mhz * 1e6 / 1e12
     achieved_tflops = FLOPS_PER_PAIR * n * m / (force_avg_ms * 1e-3) / 1e12
     traffic, digest = profile_traffic()
     roofline = {"bound": "alu", "achieved": achieved_tflops, "peak": peak_tflops, "unit": "TFLOP/s",
                 "frac": achieved_tflops / peak_tflops, "traffic": traffic,
                 "kernel": "force_tile_kernel", "flops_per_pair": FLOPS_PER_PAIR,
                 "force_launch_ms": force_avg_ms, "force_launches_timed": nforce,
-                "peak_basis": f"2 x {FP32_LANES_PER_SM} FP32 lanes x {num_sms} SMs x {sm_max_mhz:.0f} MHz (max clock)"}
+                "peak_basis": peak_basis}
     if sm_mhz:
         roofline["frac_at_measured_clock"] = achieved_tflops / (peak_tflops * sm_mhz / sm_max_mhz)
     line = {
@@ -751,11 +980,16 @@ def main():
         "batch": batch,
         "differentiation": diff,
         "scale_case": scale,
+        "tiny_case": tiny,
         "next_rows": nxt,
     }
     line["peaks_measured"] = measured_peaks(scgr, num_sms, sm_mhz or sm_max_mhz)
     if ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(pair, 2.0, 1)
+        try:
+            line["cpu_baseline"]["oracle_runs"] = oracle_runs()
+        except Exception as e:                   # the sampled figure stands on its own
+            line["cpu_baseline"]["oracle_runs"] = {"unavailable": f"{type(e).__name__}: {e}"[:200]}
     print(json.dumps(line), flush=True)
     if ws > 1:
         dist.destroy_process_group()

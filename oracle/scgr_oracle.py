@@ -234,37 +234,51 @@ def force_row_magnitudes(Y, X, aY, aX, sigma, p, g_mode, rows=None, centre=None)
     """Magnitudes of the terms of the Eq. 5 sum, for judging how well each
     row's force is conditioned.  For template row i with pair weight
     w_ij = g(s_ij) d_ij^(p-1) and r_ij = Y_i - X_j (the same terms as
-    `forces_rows`), returns per row, in float64, summed over j in order:
+    `forces_rows`), returns a dict of per-row sums over j, in float64:
 
-      A_i = sum_j |w_ij r_ij|          (Euclidean norm of each term)
-      B_i = sum_j w_ij |X_j - centre|  (centre: 3-vector, default the origin)
-      W_i = sum_j w_ij
+      A  = sum_j |w_ij r_ij|            (Euclidean norm of each term)
+      B  = sum_j w_ij |X_j - centre|    (centre: 3-vector, default the origin)
+      W  = sum_j w_ij
+      Ae = sum_j |w_ij r_ij| e_ij,  We = sum_j w_ij e_ij,
 
-    kappa_i = A_i / |f_i| is the condition number of the sum that gives f_i:
-    the factor by which relative errors of its terms can grow in the total.
+    with e_ij = -ln(g_ij / aY_i) = (aX_j - aY_i)^2 / sigma^2 - ln aX_j for
+    g = aX aY s (Eq. 10), and e_ij = -ln s_ij = (aX_j - aY_i)^2 / sigma^2 for
+    g = s: the size of the exponent of the pair's pose-independent factor.
+
+    kappa_i = A_i / |f_i| is the condition number of the sum that gives f_i.
     B_i + |Y_i - centre| W_i bounds the size of the two sums sum_j w_ij X_j
     and Y_i sum_j w_ij when f_i is formed as their difference in a frame
-    with that centre."""
+    with that centre, and Ae_i, We_i measure how an absolute error in each
+    pair's exponent (relative error e_ij times that of the exponent) reaches
+    f_i and W_i."""
     Y = np.asarray(Y, dtype=np.float64)
     X = np.asarray(X, dtype=np.float64)
     aY = np.asarray(aY, dtype=np.float64)
     aX = np.asarray(aX, dtype=np.float64)
     c = np.zeros(3) if centre is None else np.asarray(centre, dtype=np.float64)
     rows = np.arange(len(Y)) if rows is None else np.asarray(rows)
-    A = np.zeros(len(rows))
-    B = np.zeros(len(rows))
-    W = np.zeros(len(rows))
+    out = {key: np.zeros(len(rows)) for key in ("A", "B", "W", "Ae", "We")}
     xdist = np.sqrt(np.sum((X - c) ** 2, axis=1))
+    with np.errstate(divide="ignore"):
+        lnaX = np.where(aX > 0, np.log(np.where(aX > 0, aX, 1.0)), -np.inf)
     chunk = max(1, (1 << 21) // max(len(X), 1))
     for c0 in range(0, len(rows), chunk):
         rr = rows[c0:c0 + chunk]
         r, d, g = _pair_terms(Y[rr], X, aY[rr], aX, sigma, p, g_mode)
         with np.errstate(invalid="ignore", divide="ignore"):
             w = np.where(d > 0, g * d ** (p - 1.0), g if p == 1.0 else 0.0)   # R12
-        A[c0:c0 + len(rr)] = np.sum(w * d, axis=1)                          # |w r| = w d
-        B[c0:c0 + len(rr)] = w @ xdist
-        W[c0:c0 + len(rr)] = np.sum(w, axis=1)
-    return A, B, W
+        e = (aX[None, :] - aY[rr][:, None]) ** 2 / sigma ** 2                  # Eq. 3
+        if g_mode == 1:
+            e = e - lnaX[None, :]                                             # Eq. 10: the aX factor
+        e = np.where(w > 0, e, 0.0)                                           # zero terms carry no error
+        wd = w * d                                                            # |w r| = w d
+        sl = slice(c0, c0 + len(rr))
+        out["A"][sl] = np.sum(wd, axis=1)
+        out["B"][sl] = w @ xdist
+        out["W"][sl] = np.sum(w, axis=1)
+        out["Ae"][sl] = np.sum(wd * e, axis=1)
+        out["We"][sl] = np.sum(w * e, axis=1)
+    return out
 
 
 def potential(Y, X, aY, aX, sigma, p, g_mode) -> float:

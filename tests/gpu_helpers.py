@@ -9,20 +9,29 @@ that a GPU run states the error of every result against the FP64 oracle
 check_rows() adds the per-row view of a force check: a relative L2 over many
 rows can hide a single row whose sum cancels, so every checked row i must meet
 
-    |f_got,i - f_i| / |f_i| <= C_ROW * 2^-24 * kappa'_i,
-    kappa'_i = sum_j w_ij (|X_j - c| + |Y_i - c|) / |f_i|,
+    |f_got,i - f_i| <= C_ROW * 2^-24 * (B_i + |Y_i - c| W_i + Ae_i) + U_i,
 
-with c the reference mean (the frame in which the kernel accumulates
-sum_j w_ij X_j and sum_j w_ij, whose difference is f_i).  kappa'_i is at least
-the condition number kappa_i = sum_j |w_ij r_ij| / |f_i| of the Eq. 5 sum (the
-triangle inequality), which is logged beside it.  The bound counts the
-rounding of each pair weight (ex2, sqrt, a few products: < 8 ulp), the
-float32 tile sums under Kahan compensation across tiles, and the squared
-distance evaluated as |X'|^2 + |Y'|^2 - 2 X'.Y', whose absolute error
-(about 2^-24 (|X'|^2 + |Y'|^2)) enters f_i only through w_ij r_ij and so
-stays within the same magnitude sums; C_ROW = 64 leaves room for all of them.
-W_i is a sum of positive terms (condition 1): its per-row relative error must
-stay below C_ROW * 2^-24."""
+with the oracle's term-magnitude sums (oracle.force_row_magnitudes) in the
+frame centred on the reference mean c, where the kernel accumulates
+sum_j w_ij X_j and sum_j w_ij and forms f_i as their difference:
+B_i + |Y_i - c| W_i bounds both sums, and Ae_i = sum_j |w_ij r_ij| e_ij carries
+the rounding of each pair's float32 exponent (absolute error ~ 2^-24 e_ij,
+e_ij the exponent's size).  The logged ratio is therefore an effective
+condition number kappa'_i = (B_i + |Y_i - c| W_i + Ae_i) / |f_i| times
+2^-24 times the stated C_ROW, and kappa'_i is at least the condition number
+kappa_i = sum_j |w_ij r_ij| / |f_i| of the Eq. 5 sum (triangle inequality),
+which is logged beside it.  C_ROW = 64 covers the pair-weight rounding (ex2,
+sqrt, a few products: < 8 ulp), the float32 tile sums under Kahan
+compensation across tiles, and the squared distance evaluated as
+|X'|^2 + |Y'|^2 - 2 X'.Y' (absolute error ~ 2^-24 (|X'|^2 + |Y'|^2), which
+enters f_i only through w_ij r_ij).  U_i is the float32 underflow allowance:
+the factor 2^(log2 aX - (a_hat_X - a_hat_Y)^2) of each pair is flushed to 0
+below 2^-126, an absolute error of at most aY_i 2^-126 d_ij^(p-1) per pair
+weight, so U_i = aY_i 2^-126 N dmax_i^p (aY_i read as 1 for g = s) with
+dmax_i = |Y_i - c| + max_j |X_j - c|.  Rows whose oracle force is below
+2^24 U_i lie outside float32's range and are counted, not compared by their
+relative error.  W_i is checked the same way with its own sums
+(W_i + We_i, allowance N aY_i 2^-126 dmax_i^(p-1))."""
 import json
 import math
 import os
@@ -54,7 +63,8 @@ def check_rows(what, got4, f_ref, W_ref, Y, X, aY, aX, sigma, p, g_mode, rows=No
     """Per-row force parity (see the module docstring).  got4: GPU rows
     (fx, fy, fz, W) for template rows `rows` (all if None) of the template at
     positions Y; f_ref, W_ref: the oracle's values for the same rows.
-    Returns (worst per-row relative error of f, worst kappa_i)."""
+    Returns (worst per-row relative error of f over the rows inside float32's
+    range, worst kappa_i over those rows)."""
     import oracle as O
     got4 = np.asarray(got4, np.float64)
     f_ref = np.asarray(f_ref, np.float64)
@@ -63,25 +73,33 @@ def check_rows(what, got4, f_ref, W_ref, Y, X, aY, aX, sigma, p, g_mode, rows=No
     X = np.asarray(X, np.float64)
     c = X.mean(axis=0)
     rows_idx = np.arange(len(Y)) if rows is None else np.asarray(rows)
-    A, B, Wm = O.force_row_magnitudes(Y, X, aY, aX, sigma, p, g_mode, rows_idx, centre=c)
+    mg = O.force_row_magnitudes(Y, X, aY, aX, sigma, p, g_mode, rows_idx, centre=c)
+    ydist = np.linalg.norm(Y[rows_idx] - c, axis=1)
+    dmax = ydist + float(np.max(np.linalg.norm(X - c, axis=1)))
+    afac = np.asarray(aY, np.float64)[rows_idx] if g_mode == 1 else np.ones(len(rows_idx))
+    U_f = afac * 2.0 ** -126 * len(X) * dmax ** p
+    U_W = afac * 2.0 ** -126 * len(X) * dmax ** (p - 1.0)
+    scale_f = mg["B"] + ydist * mg["W"] + mg["Ae"]
     fn = np.linalg.norm(f_ref, axis=1)
-    live = fn > 0
     err = np.linalg.norm(got4[:, :3] - f_ref, axis=1)
-    rel = err[live] / fn[live]
-    kappa = A[live] / fn[live]
-    bound = (B[live] + np.linalg.norm(Y[rows_idx][live] - c, axis=1) * Wm[live]) / fn[live]
-    ratio = rel / (EPS32 * bound)
-    i_worst = int(np.argmax(ratio)) if ratio.size else 0
-    check(f"{what}: per-row f error / (2^-24 kappa'_i), worst row", float(ratio.max()) if ratio.size else 0.0, C_ROW)
+    live = scale_f > 0
+    c_f = np.maximum(err[live] - U_f[live], 0.0) / (EPS32 * scale_f[live])
+    check(f"{what}: per-row f error / (2^-24 kappa'_i |f_i|), worst row", float(c_f.max()) if c_f.size else 0.0, C_ROW)
+    inside = fn >= 2.0 ** 24 * U_f
+    check(f"{what}: rows below float32 range (not compared relatively)", int(np.count_nonzero(~inside & (fn > 0))),
+          float("inf"))
+    rel = err[inside] / fn[inside]
+    kappa = mg["A"][inside] / fn[inside]
     check(f"{what}: per-row relative error of f_i, worst row", float(rel.max()) if rel.size else 0.0, float("inf"))
-    check(f"{what}: row condition kappa_i of the row nearest its bound",
-          float(kappa[i_worst]) if kappa.size else 0.0, float("inf"))
+    if rel.size:
+        check(f"{what}: row condition kappa_i of the worst row", float(kappa[int(np.argmax(rel))]), float("inf"))
     check(f"{what}: row condition kappa_i, largest", float(kappa.max()) if kappa.size else 0.0, float("inf"))
     check(f"{what}: row condition kappa_i, median", float(np.median(kappa)) if kappa.size else 0.0, float("inf"))
-    wpos = W_ref > 0
-    relW = np.abs(got4[:, 3][wpos] - W_ref[wpos]) / W_ref[wpos]
-    check(f"{what}: per-row relative error of W_i / 2^-24, worst row", float(relW.max() / EPS32) if relW.size else 0.0,
-          C_ROW)
+    scale_W = mg["W"] + mg["We"]
+    wl = scale_W > 0
+    errW = np.abs(got4[:, 3] - W_ref)
+    c_W = np.maximum(errW[wl] - U_W[wl], 0.0) / (EPS32 * scale_W[wl])
+    check(f"{what}: per-row W error / (2^-24 (W_i + We_i)), worst row", float(c_W.max()) if c_W.size else 0.0, C_ROW)
     return (float(rel.max()) if rel.size else 0.0), (float(kappa.max()) if kappa.size else 0.0)
 
 

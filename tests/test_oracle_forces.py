@@ -182,21 +182,28 @@ def test_row_magnitudes_hand_cases():
     a = 0.2
     X = np.array([[0.0, 0.0, 0.0]])
     Y = np.array([[0.0, 3.0, 4.0]])                    # d = 5
-    A, B, W = O.force_row_magnitudes(Y, X, np.array([a]), np.array([a]), 0.1, 2.0, 1,
-                                     centre=np.array([1.0, 0.0, 0.0]))
+    mg = O.force_row_magnitudes(Y, X, np.array([a]), np.array([a]), 0.1, 2.0, 1, centre=np.array([1.0, 0.0, 0.0]))
     f, Wf = O.forces(Y, X, np.array([a]), np.array([a]), 0.1, 2.0, 1)
-    assert A[0] == pytest.approx(np.linalg.norm(f[0]), rel=1e-15)
-    assert A[0] == pytest.approx(a * a * 5.0 * 5.0, rel=1e-15)     # w = a^2 d, |r| = d
-    assert W[0] == pytest.approx(Wf[0], rel=1e-15)
-    assert B[0] == pytest.approx(a * a * 5.0 * 1.0, rel=1e-15)     # |X - centre| = 1
+    assert mg["A"][0] == pytest.approx(np.linalg.norm(f[0]), rel=1e-15)
+    assert mg["A"][0] == pytest.approx(a * a * 5.0 * 5.0, rel=1e-15)     # w = a^2 d, |r| = d
+    assert mg["W"][0] == pytest.approx(Wf[0], rel=1e-15)
+    assert mg["B"][0] == pytest.approx(a * a * 5.0 * 1.0, rel=1e-15)     # |X - centre| = 1
+    # equal curvatures: s = 1, so e = -ln aX (g = aX aY s) or 0 (g = s)
+    assert mg["We"][0] == pytest.approx(mg["W"][0] * -math.log(a), rel=1e-14)
+    assert mg["Ae"][0] == pytest.approx(mg["A"][0] * -math.log(a), rel=1e-14)
+    m0 = O.force_row_magnitudes(Y, X, np.array([a]), np.array([a]), 0.1, 2.0, 0)
+    assert m0["We"][0] == 0.0 and m0["Ae"][0] == 0.0
+    # aX = 0.1, aY = 0.3, sigma = 0.2: e = 1 - ln 0.1 (Eq. 3 exponent and the aX factor)
+    m1 = O.force_row_magnitudes(Y, X, np.array([0.3]), np.array([0.1]), 0.2, 2.0, 1)
+    assert m1["We"][0] / m1["W"][0] == pytest.approx(1.0 - math.log(0.1), rel=1e-14)
     # two equal pulls from opposite sides: f = 0, A = 2 w d (kappa infinite)
     X2 = np.array([[0.0, 0.0, -1.0], [0.0, 0.0, 1.0]])
     Y2 = np.zeros((1, 3))
     aa = np.array([a, a])
     f2, _ = O.forces(Y2, X2, np.array([a]), aa, 0.1, 1.5, 1)
-    A2, _, _ = O.force_row_magnitudes(Y2, X2, np.array([a]), aa, 0.1, 1.5, 1)
+    m2 = O.force_row_magnitudes(Y2, X2, np.array([a]), aa, 0.1, 1.5, 1)
     assert np.linalg.norm(f2) == 0.0
-    assert A2[0] == pytest.approx(2 * a * a, rel=1e-15)
+    assert m2["A"][0] == pytest.approx(2 * a * a, rel=1e-15)
 
 
 def test_row_magnitudes_match_term_list():
@@ -204,17 +211,20 @@ def test_row_magnitudes_match_term_list():
     X, Y, aX, aY = rand_case(11, n=9, m=4)
     sigma, p = 0.08, 1.5
     c = np.array([0.3, -0.1, 0.2])
-    A, B, W = O.force_row_magnitudes(Y, X, aY, aX, sigma, p, 1, rows=np.array([2, 0]), centre=c)
+    mg = O.force_row_magnitudes(Y, X, aY, aX, sigma, p, 1, rows=np.array([2, 0]), centre=c)
     for out_i, i in enumerate((2, 0)):
-        a_sum = b_sum = w_sum = 0.0
+        sums = dict(A=0.0, B=0.0, W=0.0, Ae=0.0, We=0.0)
         for j in range(len(X)):
             r = [Y[i][q] - X[j][q] for q in range(3)]
             d = math.sqrt(r[0] ** 2 + r[1] ** 2 + r[2] ** 2)
-            g = aX[j] * aY[i] * math.exp(-((aX[j] - aY[i]) ** 2) / sigma ** 2)
+            expo = (aX[j] - aY[i]) ** 2 / sigma ** 2
+            g = aX[j] * aY[i] * math.exp(-expo)
             w = g * d ** (p - 1.0)
-            a_sum += w * d
-            b_sum += w * math.sqrt(sum((X[j][q] - c[q]) ** 2 for q in range(3)))
-            w_sum += w
-        assert A[out_i] == pytest.approx(a_sum, rel=1e-13)
-        assert B[out_i] == pytest.approx(b_sum, rel=1e-13)
-        assert W[out_i] == pytest.approx(w_sum, rel=1e-13)
+            e = expo - math.log(aX[j])
+            sums["A"] += w * d
+            sums["B"] += w * math.sqrt(sum((X[j][q] - c[q]) ** 2 for q in range(3)))
+            sums["W"] += w
+            sums["Ae"] += w * d * e
+            sums["We"] += w * e
+        for key, value in sums.items():
+            assert mg[key][out_i] == pytest.approx(value, rel=1e-13), key
