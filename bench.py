@@ -477,7 +477,7 @@ def bench_diff(args, scgr, torch, dev, steps, warmup):
         if not args.no_autotune:
             from paper_1902_01061_gb300 import autotune
             tuned = autotune.tune_single(ctx, n, m, 2.0, reps=10)
-            tuned = {k: tuned[k] for k in ("P", "tpb", "occ", "rsqrt", "ms", "plan")}
+            tuned = {k: tuned[k] for k in ("P", "tpb", "occ", "rsqrt", "ex2poly", "ms", "plan")}
         pose = [0.1, -0.2, 0.3, 0.05, 0.0, -0.05, 1.02]
         gx = torch.empty((m, 3), dtype=torch.float32, device=dev)
         fwd = _timed(lambda: scgr.scgr_potential(ctx, pose, want_grad=False), steps, warmup, torch)
@@ -509,7 +509,7 @@ def bench_scale(args, scgr, torch, dev, steps, warmup):
             scgr.scgr_set_template(ctx, Y)
             scgr.scgr_compute_descriptors(ctx)
             tuned = autotune.tune_single(ctx, n, m, 2.0, reps=10)
-            tuned = {k: tuned[k] for k in ("P", "tpb", "occ", "rsqrt", "ms", "plan")}
+            tuned = {k: tuned[k] for k in ("P", "tpb", "occ", "rsqrt", "ex2poly", "ms", "plan")}
 
         def one():
             scgr.scgr_set_reference(ctx, X)
@@ -603,6 +603,7 @@ def apply_plan(scgr, ctx, tuned):
         scgr.scgr_set_tuning(ctx, scgr.SCGR_TUNE_FORCE_TPB, int(tuned["tpb"]))
         scgr.scgr_set_tuning(ctx, scgr.SCGR_TUNE_FORCE_OCC, int(tuned.get("occ", 0)))
         scgr.scgr_set_tuning(ctx, scgr.SCGR_TUNE_FORCE_RSQRT, int(tuned.get("rsqrt", 0)))
+        scgr.scgr_set_tuning(ctx, scgr.SCGR_TUNE_FORCE_EX2POLY, int(tuned.get("ex2poly", 0)))
 
 
 def bench_g_equals_s(args, scgr, torch, dev, Xd, Yd, tuned, peak_basis):
@@ -780,11 +781,15 @@ def main():
     ap.add_argument("--batch-iters", type=int, default=100, help="iterations of the batched leg")
     ap.add_argument("--next-only", action="store_true",
                     help="only the leg of the widened rows (odd-p fast path, radius, pyramid, change mask)")
+    ap.add_argument("--split", choices=["none", "rows", "replicas"], default=None,
+                    help="multi-GPU form: rows (default when WORLD_SIZE > 1) splits one registration by template rows "
+                         "over the ranks; replicas runs the whole workload on every rank; none (default on one GPU) "
+                         "is the single-context run")
     ap.add_argument("--oracle-only", action="store_true",
                     help="only the oracle's timings on the host (sampled 1M x 1M force rows, configs 1 and 2)")
     ap.add_argument("--batch-plan", default=None, help="pin the batched force kernel 'P,CHUNK_TILES[,PERSISTENT]' (no autotuning)")
     ap.add_argument("--batch-eager", action="store_true", help="batched leg without the CUDA graph (for profilers)")
-    ap.add_argument("--plan", default=None, help="pin the force kernel 'P,TPB[,OCC[,RSQRT]]' (no autotuning), e.g. 2,256,0,1")
+    ap.add_argument("--plan", default=None, help="pin the force kernel 'P,TPB[,OCC[,RSQRT[,EX2POLY]]]' (no autotuning), e.g. 4,128,2,0,1")
     args = ap.parse_args()
     ws, rank, local = dist_env()
     if args.impl == "reference":
@@ -840,33 +845,60 @@ def main():
     Yd = torch.from_numpy(pair.Y0).to(dev)
     moved = torch.empty((m, 3), dtype=torch.float32, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
-    params = scgr.scgr_default_params(p=2.0, g_mode=1, k=16)
+    split = args.split or ("rows" if ws > 1 else "none")
+    rows_mode = split == "rows"
+    from paper_1902_01061_gb300 import shard
+    row0, nrows = shard.row_partition(m, ws, rank) if rows_mode else (0, m)
+    # row sharding iterates stepwise, which needs the Eq. 12 horizon up front
+    params = scgr.scgr_default_params(p=2.0, g_mode=1, k=16, E=iters if rows_mode else 0)
     stream = torch.cuda.current_stream()
     ctx = scgr.scgr_create(params, stream)
     num_sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    part_buf = torch.empty(13, dtype=torch.float64, device=dev)
+    Xh = torch.from_numpy(pair.X).pin_memory().numpy()      # pinned host copies for the end-to-end leg
+    Yh = torch.from_numpy(pair.Y0).pin_memory().numpy()
+
+    def load_clouds(host=False):
+        if host:
+            scgr.scgr_set_reference_host(ctx, Xh)
+            scgr.scgr_set_template_host(ctx, Yh)
+        else:
+            scgr.scgr_set_reference(ctx, Xd)
+            scgr.scgr_set_template(ctx, Yd)
+        if rows_mode:
+            scgr.scgr_set_row_range(ctx, row0, nrows)
+        scgr.scgr_compute_descriptors(ctx)
+
+    def iterate():
+        if not rows_mode:
+            scgr.scgr_run(ctx, iters)
+            return
+        # this rank's template rows; the 13 partial sums all-gathered on the
+        # device (NCCL) and added in rank order by the library each iteration
+        for _ in range(iters):
+            scgr.scgr_step_partials_dev(ctx, part_buf)
+            scgr.scgr_step_apply_dev(ctx, shard.gather_parts(part_buf))
 
     tuned = None
     if args.plan:
         vals = [int(v) for v in args.plan.split(",")]
         P_, T_, O_ = vals[0], vals[1], (vals[2] if len(vals) > 2 else 0)
         R_ = vals[3] if len(vals) > 3 else 0
+        E_ = vals[4] if len(vals) > 4 else 0
         scgr.scgr_set_tuning(ctx, scgr.SCGR_TUNE_FORCE_P, P_)
         scgr.scgr_set_tuning(ctx, scgr.SCGR_TUNE_FORCE_TPB, T_)
         scgr.scgr_set_tuning(ctx, scgr.SCGR_TUNE_FORCE_OCC, O_)
         scgr.scgr_set_tuning(ctx, scgr.SCGR_TUNE_FORCE_RSQRT, R_)
-        tuned = {"P": P_, "tpb": T_, "occ": O_, "rsqrt": R_, "pinned": True}
+        scgr.scgr_set_tuning(ctx, scgr.SCGR_TUNE_FORCE_EX2POLY, E_)
+        tuned = {"P": P_, "tpb": T_, "occ": O_, "rsqrt": R_, "ex2poly": E_, "pinned": True}
     elif not args.no_autotune:
         from paper_1902_01061_gb300 import autotune
-        scgr.scgr_set_reference(ctx, Xd)
-        scgr.scgr_set_template(ctx, Yd)
-        scgr.scgr_compute_descriptors(ctx)
-        tuned = autotune.tune_single(ctx, n, m, 2.0, reps=2)
+        load_clouds()
+        tuned = autotune.tune_single(ctx, n, nrows, 2.0, reps=2)
 
     def step_device():
-        scgr.scgr_set_reference(ctx, Xd)
-        scgr.scgr_set_template(ctx, Yd)
-        scgr.scgr_compute_descriptors(ctx)
-        scgr.scgr_run(ctx, iters)
+        load_clouds()
+        iterate()
         scgr.scgr_get_moved(ctx, moved)
 
     for _ in range(args.warmup):
@@ -903,25 +935,24 @@ def main():
         t = torch.tensor([ms_per_step], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms_per_step = float(t.item())
-    value = ws * pairs_per_step / (ms_per_step * 1e-3)
+    # replicas: every rank registers the whole workload (weak scaling);
+    # rows: the ranks share one registration (strong scaling)
+    units = pairs_per_step if rows_mode else ws * pairs_per_step
+    value = units / (ms_per_step * 1e-3)
     force_avg_ms = force_ms / max(nforce, 1)
 
     # end to end through the host entry points (pinned host buffers)
     e2e_steps = args.e2e_steps if args.e2e_steps is not None else min(args.steps, 3)
     e2e = None
     if e2e_steps > 0:
-        Xh = torch.from_numpy(pair.X).pin_memory().numpy()
-        Yh = torch.from_numpy(pair.Y0).pin_memory().numpy()
         Mh = torch.empty((m, 3), dtype=torch.float32).pin_memory().numpy()
         times = []
         for _ in range(e2e_steps):
             flush.zero_()
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            scgr.scgr_set_reference_host(ctx, Xh)
-            scgr.scgr_set_template_host(ctx, Yh)
-            scgr.scgr_compute_descriptors(ctx)
-            scgr.scgr_run(ctx, iters)
+            load_clouds(host=True)
+            iterate()
             scgr.scgr_get_moved_host(ctx, Mh)
             scgr.scgr_get_result(ctx)
             times.append(time.perf_counter() - t0)
@@ -930,7 +961,7 @@ def main():
             t = torch.tensor([e2e_s], device=dev)
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             e2e_s = float(t.item())
-        e2e = {"value": ws * pairs_per_step / e2e_s, "unit": "pair-interactions/s",
+        e2e = {"value": units / e2e_s, "unit": "pair-interactions/s",
                "h2d_bytes_per_step": (n + m) * 12, "d2h_bytes_per_step": m * 12 + 8 * 13 + 8}
     scgr.scgr_destroy(ctx)
     sm_max_mhz = (clk or {}).get("sm_max_mhz") or 2070.0
@@ -953,7 +984,7 @@ def main():
             dist.destroy_process_group()
         return 0
 
-    achieved_tflops = FLOPS_PER_PAIR * n * m / (force_avg_ms * 1e-3) / 1e12
+    achieved_tflops = FLOPS_PER_PAIR * n * nrows / (force_avg_ms * 1e-3) / 1e12   # one launch: this rank's rows
     traffic, digest = profile_traffic()
     roofline = {"bound": "alu", "achieved": achieved_tflops, "peak": peak_tflops, "unit": "TFLOP/s",
                 "frac": achieved_tflops / peak_tflops, "traffic": traffic,
@@ -966,11 +997,12 @@ def main():
         "metric": metric_name(args.workload),
         "value": value, "unit": "pair-interactions/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "scaling": "strong" if rows_mode else "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "ms_per_iteration": ms_per_step / iters,
         "pct_fp32_peak": 100.0 * roofline["frac"],
         "config": dict(base_config(args.workload, n, m), autotuned=tuned, l2="flushed between steps (256 MB write)",
-                       parallelism=f"replicas x{ws}"),
+                       parallelism=(f"rows x{ws} (template rows split over the ranks, 13 float64 partial sums "
+                                    f"all-gathered on the device per iteration)" if rows_mode else f"replicas x{ws}")),
         "gpu_launches": launches,
         "wall_s_timed_region": wall,
         "pose": {"s": res.s, "iterations": res.iterations},

@@ -278,7 +278,10 @@ SCGR_EXPORT scgr_status scgr_get_force_timing(scgr_ctx* ctx, int64_t* launches, 
  * array's device address (cudaGetSymbolAddress, with that device current);
  * make that first call before any stream capture.  Every call shares the
  * array, so calls that overlap on the GPU (other streams, other host
- * threads) race and must be serialised by the caller. */
+ * threads) race and must be serialised by the caller.  The looked-up address
+ * is kept for the life of the process: after a cudaDeviceReset (which
+ * destroys the device's primary context, and the array with it) do not call
+ * this entry point again in that process. */
 SCGR_EXPORT scgr_status scgr_forces_static(const float* x_dev, int64_t n, const float* y_dev, int64_t m,
                                            const double* ax_dev, const double* ay_dev, double sigma,
                                            double p, int g_mode, float* f4_dev, void* cuda_stream);
@@ -319,6 +322,22 @@ SCGR_EXPORT scgr_status scgr_set_row_range(scgr_ctx* ctx, int64_t row0, int64_t 
 SCGR_EXPORT scgr_status scgr_step_partials(scgr_ctx* ctx, double out13[13]);
 SCGR_EXPORT scgr_status scgr_step_apply(scgr_ctx* ctx, const double tot13[13]);
 
+/* Stream-ordered forms of the same two halves, for an exchange that stays on
+ * the device (an NCCL all-gather enqueued on the context stream between
+ * them).  Neither copies to or from the host nor synchronises; device-side
+ * errors surface at the next synchronising call.
+ * scgr_step_partials_dev writes this rank's 13 float64 partial sums (F[3], W,
+ * T[3][3] row-major, as scgr_step_partials) to out13_dev (device, 13 doubles,
+ * 8-byte aligned, owned by the caller).
+ * scgr_step_apply_dev takes the ranks' partial sums gathered in rank order,
+ * parts_dev = [nparts][13] doubles on the device (1 <= nparts <= 65536), adds
+ * them in that order on the device and performs the pose update of
+ * Eq. 5.5 - Eq. 12 with the totals.  Ranks that pass identical parts hold
+ * identical poses.  STATE before descriptors or without params.E > 0;
+ * INVALID_ARG for NULL or a bad nparts. */
+SCGR_EXPORT scgr_status scgr_step_partials_dev(scgr_ctx* ctx, double* out13_dev);
+SCGR_EXPORT scgr_status scgr_step_apply_dev(scgr_ctx* ctx, const double* parts_dev, int nparts);
+
 /* Tuning knobs (set by the autotuner; defaults are sensible). */
 #define SCGR_TUNE_BATCH_CHUNK_TILES 1 /* reference tiles (256 points) per batched work item, default 16 */
 #define SCGR_TUNE_KNN_GRID_MIN 2      /* clouds of at least this many points use the exact grid kNN
@@ -346,6 +365,14 @@ SCGR_EXPORT scgr_status scgr_step_apply(scgr_ctx* ctx, const double tot13[13]);
                                          slot, each taking the next item (same order) from a queue head in
                                          device memory that is cleared before every launch.  Results are
                                          bit-identical: an item's sums do not depend on which block takes it */
+#define SCGR_TUNE_FORCE_EX2POLY 11   /* p = 2 with the shared-memory-sum shapes (variant 2): 0 (default) every
+                                         pair's similarity factor 2^-e from the special-function unit's ex2;
+                                         1 or 2: for that many template points per thread, one of the two
+                                         packed pair updates of each 4-point step evaluates it on the FP32
+                                         pipe instead (range reduction to [-1/2, 1/2] and a degree-5 minimax
+                                         polynomial, relative error < 2^-22; 2^-e below 2^-125.5 reads 0),
+                                         which moves a fraction value / (2 P) of the exponentials off the
+                                         special-function unit.  Results agree with 0 to rounding */
 #define SCGR_TUNE_REUSE_POSE_FREE 6   /* 1 (default): odd integer p skips the per-iteration all-pairs pass.
                                          p = 1: the pair weights do not depend on the pose, so scgr_run
                                          computes the force sums once per call and reuses them

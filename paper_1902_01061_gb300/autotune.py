@@ -82,32 +82,42 @@ def time_forces(ctx, m: int, reps: int = 3) -> float:
     return ms / max(n, 1)
 
 
-def _apply(ctx, P: int, tpb: int, occ: int, rsq: int = 0) -> None:
+def _apply(ctx, P: int, tpb: int, occ: int, rsq: int = 0, exo: int = 0) -> None:
     scgr.scgr_set_tuning(ctx, scgr.SCGR_TUNE_FORCE_P, P)
     scgr.scgr_set_tuning(ctx, scgr.SCGR_TUNE_FORCE_TPB, tpb)
     scgr.scgr_set_tuning(ctx, scgr.SCGR_TUNE_FORCE_OCC, occ)
     scgr.scgr_set_tuning(ctx, scgr.SCGR_TUNE_FORCE_RSQRT, rsq)
+    scgr.scgr_set_tuning(ctx, scgr.SCGR_TUNE_FORCE_EX2POLY, exo)
 
 
 def tune_single(ctx, n: int, m: int, p: float, candidates=None, reps: int = 3, store: bool = True) -> dict:
     """Time each (P, threads, occupancy variant) candidate on a context whose
     descriptors are computed (splits stay automatic); for p = 2 the two best
-    shapes are timed again with the rsqrt form of the distance factor.  Leave
-    the best in place and return it."""
+    shapes are timed again with the rsqrt form of the distance factor, and
+    the best shared-memory-sum shape with part of its exponentials on the
+    FP32 pipe (SCGR_TUNE_FORCE_EX2POLY 1 and 2).  Leave the best in place and
+    return it."""
     results = []
     for P, tpb, occ in candidates or SINGLE_CANDIDATES:
         _apply(ctx, P, tpb, occ, 0)
-        results.append((time_forces(ctx, m, reps), P, tpb, occ, 0, scgr.scgr_get_plan(ctx)))
+        results.append((time_forces(ctx, m, reps), P, tpb, occ, 0, 0, scgr.scgr_get_plan(ctx)))
     results.sort(key=lambda r: r[0])
     if float(p) == 2.0:
         for r in results[:2]:
             _apply(ctx, r[1], r[2], r[3], 1)
-            results.append((time_forces(ctx, m, reps), r[1], r[2], r[3], 1, scgr.scgr_get_plan(ctx)))
+            results.append((time_forces(ctx, m, reps), r[1], r[2], r[3], 1, 0, scgr.scgr_get_plan(ctx)))
+        ks = [r for r in results if r[3] == 2 and r[4] == 0 and r[5] == 0]
+        if ks:
+            r = min(ks, key=lambda x: x[0])
+            for exo in (1, 2):
+                _apply(ctx, r[1], r[2], r[3], 0, exo)
+                results.append((time_forces(ctx, m, reps), r[1], r[2], r[3], 0, exo, scgr.scgr_get_plan(ctx)))
         results.sort(key=lambda r: r[0])
-    best_ms, P, tpb, occ, rsq, plan = results[0]
-    _apply(ctx, P, tpb, occ, rsq)
-    best = {"P": P, "tpb": tpb, "occ": occ, "rsqrt": rsq, "ms": best_ms, "plan": plan,
-            "tried": [{"P": r[1], "tpb": r[2], "occ": r[3], "rsqrt": r[4], "ms": r[0]} for r in results],
+    best_ms, P, tpb, occ, rsq, exo, plan = results[0]
+    _apply(ctx, P, tpb, occ, rsq, exo)
+    best = {"P": P, "tpb": tpb, "occ": occ, "rsqrt": rsq, "ex2poly": exo, "ms": best_ms, "plan": plan,
+            "tried": [{"P": r[1], "tpb": r[2], "occ": r[3], "rsqrt": r[4], "ex2poly": r[5], "ms": r[0]}
+                      for r in results],
             "when": time.strftime("%Y-%m-%d %H:%M:%S")}
     if store:
         _store(single_key(gpu_name(), n, m, p), best)
@@ -158,7 +168,7 @@ def tune_batch(ctx, ref_off, ref_xyz, tmp_off, tmp_xyz, p: float, iterations: in
 def apply_cached_single(ctx, n: int, m: int, p: float) -> dict | None:
     hit = _load().get(single_key(gpu_name(), n, m, p))
     if hit:
-        _apply(ctx, hit["P"], hit["tpb"], hit.get("occ", 0), hit.get("rsqrt", 0))
+        _apply(ctx, hit["P"], hit["tpb"], hit.get("occ", 0), hit.get("rsqrt", 0), hit.get("ex2poly", 0))
     return hit
 
 

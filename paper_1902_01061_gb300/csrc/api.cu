@@ -94,6 +94,7 @@ void scgr_destroy(scgr_ctx* c) {
                     &c->bXr, &c->bXA, &c->bY0r, &c->bpartial, &c->bblockpart, &c->bpairs, &c->bitems,
                     &c->bcpair, &c->btabX, &c->btabY, &c->bxoff, &c->byoff, &c->bstats, &c->bposes, &c->bnext,
                     &c->gcell, &c->gcount, &c->gstart, &c->gcursor, &c->gblock, &c->gsorted, &c->gsidx, &c->gbb,
+                    &c->rgstart, &c->rgsorted, &c->rgsidx,
                     &c->cd_key, &c->cd_moved, &c->wstore, &c->wupart, &c->wpartial, &c->mpart, &c->mom};
   for (DevBuf* b : bufs) release(*b);
   if (c->pose) cudaFree(c->pose);
@@ -441,6 +442,11 @@ scgr_status scgr_set_tuning(scgr_ctx* c, int key, int value) {
   if (key == SCGR_TUNE_FORCE_RSQRT) {
     if (value < 0 || value > 2) return fail(c, SCGR_ERR_INVALID_ARG, "distance factor form must be 0, 1 or 2");
     c->ftune.rsq = value;
+    return c->have_desc ? replan(c) : SCGR_OK;
+  }
+  if (key == SCGR_TUNE_FORCE_EX2POLY) {
+    if (value < 0 || value > 2) return fail(c, SCGR_ERR_INVALID_ARG, "value must be 0, 1 or 2");
+    c->ftune.ex2poly = value;
     return c->have_desc ? replan(c) : SCGR_OK;
   }
   if (key == SCGR_TUNE_REUSE_POSE_FREE) {

@@ -102,4 +102,36 @@ scgr_status scgr_step_apply(scgr_ctx* c, const double tot13[13]) {
   return read_error_word(c);
 }
 
+// Stream-ordered forms of the two halves of a sharded iteration: nothing is
+// copied to or from the host and nothing waits, so the exchange between them
+// can be a collective enqueued on the same stream (an NCCL all-gather) and a
+// run of iterations never leaves the device.
+scgr_status scgr_step_partials_dev(scgr_ctx* c, double* out13_dev) {
+  NvtxRange nvtx_range("scgr_step_partials_dev");
+  if (!c || !out13_dev) return fail(c, SCGR_ERR_INVALID_ARG, "NULL argument");
+  c->err.clear();
+  if (!c->have_desc) return fail(c, SCGR_ERR_STATE, "compute descriptors first");
+  if (c->E_host <= 0) return fail(c, SCGR_ERR_STATE, "set params.E for stepwise iteration");
+  const int mloc = (int)(c->rows >= 0 ? c->rows : c->m);
+  scgr_status fs = force_launch(c);
+  if (fs != SCGR_OK) return fs;
+  SCGR_CK(c, launch_combine(c->L(), (const float4*)c->partial.p, c->fp.splits, (int)c->mpad, mloc,
+                            (const float4*)c->Y0r.p, (const double*)c->aY64.p + c->row0, c->prm.g_mode, c->pose,
+                            nullptr, (double*)c->blockpart.p));
+  SCGR_CK(c, launch_column_sum13(c->L(), (const double*)c->blockpart.p, combine_blocks(c->mpad), out13_dev));
+  return SCGR_OK;
+}
+
+scgr_status scgr_step_apply_dev(scgr_ctx* c, const double* parts_dev, int nparts) {
+  NvtxRange nvtx_range("scgr_step_apply_dev");
+  if (!c || !parts_dev) return fail(c, SCGR_ERR_INVALID_ARG, "NULL argument");
+  c->err.clear();
+  if (nparts < 1 || nparts > 65536) return fail(c, SCGR_ERR_INVALID_ARG, "nparts must be in [1, 65536]");
+  if (!c->have_desc) return fail(c, SCGR_ERR_STATE, "compute descriptors first");
+  if (c->E_host <= 0) return fail(c, SCGR_ERR_STATE, "set params.E for stepwise iteration");
+  SCGR_CK(c, launch_finalize(c->L(), parts_dev, nparts, c->pose, c->stats, step_params(c), c->errword));
+  c->iterations += 1;
+  return SCGR_OK;
+}
+
 }  // extern "C"

@@ -271,6 +271,9 @@ struct ForcePlan {
   int iblocks;    // grid.x
   int occ;        // 0: >= 2 resident blocks per SM; 1: more (3 for 256 threads and P <= 2, 4 for 128 threads);
                   // 2: running sums in shared memory, 2 record tiles per stage (P = 4 x 128, P = 2 x 256)
+  int ex2poly;    // p = 2, occ 2 only: number of template points per thread (0..2) whose second packed pair
+                  // update of each 4-point step evaluates 2^-e on the FP32 pipe instead of the special-function
+                  // unit (a fraction ex2poly / (2 P) of the pairs)
 };
 
 // Overrides of the force plan (0: automatic), set by the autotuner.
@@ -281,6 +284,7 @@ struct ForceTuning {
   int occ = -1;    // -1 automatic; 0 default; 1 the higher-occupancy variant (tighter register budget);
                    // 2 shared-memory sums
   int rsq = 0;     // p = 2 distance factor: 0 / 2 sqrt, 1 d^2 * rsqrt(d^2)
+  int ex2poly = 0; // see ForcePlan::ex2poly
 };
 
 ForcePlan plan_force(int64_t m, int64_t npad, double p, int num_sms, const ForceTuning& tune = ForceTuning());

@@ -40,6 +40,7 @@ using scgr::DevStats;
 using scgr::ForcePlan;
 using scgr::ForceTuning;
 using scgr::Launch;
+using scgr::GridSpec;
 
 struct scgr_ctx {
   scgr_params prm{};
@@ -83,6 +84,10 @@ struct scgr_ctx {
   int reuse_pose_free = 1;      // p = 1: one force pass per scgr_run (tunable)
   DevBuf gcell, gcount, gstart, gcursor, gblock, gsorted, gsidx, gbb, cd_key, cd_moved, wstore, wupart, wpartial,
       mpart, mom;
+  // the reference's grid for nearest-point queries, kept until the reference changes
+  DevBuf rgstart, rgsorted, rgsidx;
+  GridSpec rgspec{};
+  bool rgrid_ok = false;
   cudaGraph_t bgraph = nullptr;
   cudaGraphExec_t bgexec = nullptr;
 

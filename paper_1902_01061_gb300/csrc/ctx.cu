@@ -108,7 +108,7 @@ scgr_status set_cloud(scgr_ctx* c, const float* xyz, int64_t n, bool host, bool 
     src = (const float*)c->stage.p;
   }
   SCGR_CK(c, launch_pack(c->L(), src, n, (float4*)dst.p, c->errword));
-  if (ref) { c->n = n; c->have_X = true; }
+  if (ref) { c->n = n; c->have_X = true; c->rgrid_ok = false; }
   else { c->m = n; c->have_Y = true; }
   c->have_desc = false;
   return SCGR_OK;
@@ -189,7 +189,11 @@ scgr_status knn_cloud(scgr_ctx* c, const float4* P, int n, int32_t* out) {
 
 // Nearest reference point of nq external queries (float32 [nq][3] on the
 // device): brute force below knn_grid_min reference points, else the exact
-// grid search over a grid of the reference (the same result).
+// grid search over a grid of the reference (the same result).  The
+// reference's grid is built on the first query after scgr_set_reference and
+// kept in its own buffers (the descriptor pass reuses the shared grid
+// workspace for both clouds), so later queries skip the bounding-box
+// synchronisation and the counting sort.
 scgr_status nearest_reference(scgr_ctx* c, const float* q3, int nq, int32_t* idx_out, float* key_out) {
   const float4* X4 = (const float4*)c->X4.p;
   const int n = (int)c->n;
@@ -197,13 +201,21 @@ scgr_status nearest_reference(scgr_ctx* c, const float* q3, int nq, int32_t* idx
     SCGR_CK(c, launch_nearest(c->L(), X4, n, q3, nq, idx_out, key_out));
     return SCGR_OK;
   }
-  GridSpec gs;
-  const scgr_status st = grid_setup(c, X4, n, &gs);
-  if (st != SCGR_OK) return st;
-  SCGR_CK(c, launch_grid_build(c->L(), X4, n, gs, (int*)c->gcell.p, (int*)c->gcount.p, (int*)c->gstart.p,
-                               (int*)c->gcursor.p, (int*)c->gblock.p, (float4*)c->gsorted.p, (int*)c->gsidx.p));
-  SCGR_CK(c, launch_nearest_grid(c->L(), (const float4*)c->gsorted.p, (const int*)c->gsidx.p,
-                                 (const int*)c->gstart.p, gs, q3, nq, idx_out, key_out));
+  if (!c->rgrid_ok) {
+    GridSpec gs;
+    const scgr_status st = grid_setup(c, X4, n, &gs);
+    if (st != SCGR_OK) return st;
+    const int64_t ncell = grid_cells(gs);
+    SCGR_CK(c, ensure(c->rgstart, (size_t)(ncell + 1) * sizeof(int)));
+    SCGR_CK(c, ensure(c->rgsorted, (size_t)n * sizeof(float4)));
+    SCGR_CK(c, ensure(c->rgsidx, (size_t)n * sizeof(int)));
+    SCGR_CK(c, launch_grid_build(c->L(), X4, n, gs, (int*)c->gcell.p, (int*)c->gcount.p, (int*)c->rgstart.p,
+                                 (int*)c->gcursor.p, (int*)c->gblock.p, (float4*)c->rgsorted.p, (int*)c->rgsidx.p));
+    c->rgspec = gs;
+    c->rgrid_ok = true;
+  }
+  SCGR_CK(c, launch_nearest_grid(c->L(), (const float4*)c->rgsorted.p, (const int*)c->rgsidx.p,
+                                 (const int*)c->rgstart.p, c->rgspec, q3, nq, idx_out, key_out));
   return SCGR_OK;
 }
 

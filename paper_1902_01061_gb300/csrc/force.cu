@@ -32,6 +32,7 @@
 #include <cmath>
 
 #include "common.cuh"
+#include "ex2_poly.cuh"
 
 namespace scgr {
 
@@ -75,8 +76,39 @@ __device__ __forceinline__ void kahan_add(float& s, float& c, float x) {
 
 constexpr float RSQRT_CAP = 1e18f;
 
+// 2^-e for e >= 0 on the FP32 pipe, both lanes (Cody-Waite reduction):
+// e = n + g with n = round(e), g in [-1/2, 1/2]; 2^-g from the degree-5
+// minimax polynomial of ex2_poly.cuh (relative error < 2^-22 in float32),
+// and 2^-n added to the exponent field.  Adding 1.5 * 2^23 rounds e to an
+// integer held in the low mantissa bits: t = 1.5 * 2^23 - n, whose bit
+// pattern shifted left by 23 is -n << 23 for |n| < 256.  Results below
+// 2^-125.5 (e >= 125.5, including e = +inf) are 0, as the special-function
+// unit's flushing ex2 gives below 2^-126.
+constexpr float EX2_ROUND = 12582912.0f;  // 1.5 * 2^23
+constexpr float EX2_POLY_MAX = 125.5f;
+__device__ __forceinline__ u64 ex2_neg_poly2(u64 e) {
+  const u64 R2 = pk2(EX2_ROUND, EX2_ROUND);
+  const u64 t = sub2(R2, e);   // 1.5 * 2^23 - round(e)
+  const u64 nf = sub2(t, R2);  // -round(e), exact
+  const u64 g = add2(e, nf);   // e - round(e), exact
+  u64 q = fma2(pk2(EX2_POLY_C5, EX2_POLY_C5), g, pk2(EX2_POLY_C4, EX2_POLY_C4));
+  q = fma2(q, g, pk2(EX2_POLY_C3, EX2_POLY_C3));
+  q = fma2(q, g, pk2(EX2_POLY_C2, EX2_POLY_C2));
+  q = fma2(q, g, pk2(EX2_POLY_C1, EX2_POLY_C1));
+  q = fma2(q, g, pk2(EX2_POLY_C0, EX2_POLY_C0));
+  float t0, t1, q0, q1, e0, e1;
+  upk2(t, t0, t1);
+  upk2(q, q0, q1);
+  upk2(e, e0, e1);
+  const float r0 = __uint_as_float(__float_as_uint(q0) + (__float_as_uint(t0) << 23));
+  const float r1 = __uint_as_float(__float_as_uint(q1) + (__float_as_uint(t1) << 23));
+  return pk2(e0 < EX2_POLY_MAX ? r0 : 0.f, e1 < EX2_POLY_MAX ? r1 : 0.f);
+}
+
 // One packed pair update: reference points (j, j+1) against one template point.
-template <int PM>
+// POLY (p = 2 only): the factor 2^-ep on the FP32 pipe instead of the
+// special-function unit.
+template <int PM, bool POLY = false>
 __device__ __forceinline__ void pair2(u64 xv, u64 yv, u64 zv, u64 nv, u64 av, u64 lv, u64 mx, u64 my,
                                       u64 mz, u64 ny, u64 ah, u64 nq, u64& W, u64& Sx, u64& Sy, u64& Sz) {
   u64 d2 = add2(nv, ny);
@@ -92,9 +124,14 @@ __device__ __forceinline__ void pair2(u64 xv, u64 yv, u64 zv, u64 nv, u64 av, u6
     w = pk2(ex2_neg(e0), ex2_neg(e1));
   } else if (PM == 2) {
     float e0, e1, q0, q1;
-    upk2(ep, e0, e1);
     upk2(d2, q0, q1);
-    w = mul2(pk2(ex2_neg(e0), ex2_neg(e1)), pk2(sqrt_approx(fabsf(q0)), sqrt_approx(fabsf(q1))));
+    const u64 dd = pk2(sqrt_approx(fabsf(q0)), sqrt_approx(fabsf(q1)));
+    if (POLY) {
+      w = mul2(ex2_neg_poly2(ep), dd);
+    } else {
+      upk2(ep, e0, e1);
+      w = mul2(pk2(ex2_neg(e0), ex2_neg(e1)), dd);
+    }
   } else if (PM == 3) {
     float e0, e1;
     upk2(ep, e0, e1);
@@ -180,7 +217,7 @@ struct RunningSums {
 // one float4 partial per template point to outbase[0 .. P*TPB).  SUB record
 // tiles of TJ points are staged together (sT holds SUB*TJ points per row);
 // a stage past t1 is filled with zero-weight entries (-L = +inf).
-template <int P, int PM, int TPB, int TJ, bool KS, int SUB>
+template <int P, int PM, int TPB, int TJ, bool KS, int SUB, int EXO = 0>
 __device__ __forceinline__ void force_block(float (&sT)[6][TJ * SUB], float* sk, const float* __restrict__ Xr,
                                             const float* __restrict__ XA, int t0, int t1,
                                             const float4* __restrict__ Y0r, int ibase, const DevPose* ps,
@@ -252,8 +289,13 @@ __device__ __forceinline__ void force_block(float (&sT)[6][TJ * SUB], float* sk,
       for (int q = 0; q < P; ++q)
         pair2<PM>(X.x, Yv.x, Z.x, N.x, Av.x, Lv.x, mx[q], my[q], mz[q], ny[q], ah[q], nq, aW[q], ax[q], ay[q], az[q]);
 #pragma unroll
-      for (int q = 0; q < P; ++q)
-        pair2<PM>(X.y, Yv.y, Z.y, N.y, Av.y, Lv.y, mx[q], my[q], mz[q], ny[q], ah[q], nq, aW[q], ax[q], ay[q], az[q]);
+      for (int q = 0; q < P; ++q) {
+        if (q < EXO)  // resolved at compile time once the loop is unrolled
+          pair2<PM, true>(X.y, Yv.y, Z.y, N.y, Av.y, Lv.y, mx[q], my[q], mz[q], ny[q], ah[q], nq, aW[q], ax[q], ay[q],
+                          az[q]);
+        else
+          pair2<PM>(X.y, Yv.y, Z.y, N.y, Av.y, Lv.y, mx[q], my[q], mz[q], ny[q], ah[q], nq, aW[q], ax[q], ay[q], az[q]);
+      }
     }
 #pragma unroll
     for (int q = 0; q < P; ++q) run.add(q, aW[q], ax[q], ay[q], az[q]);
@@ -286,7 +328,7 @@ __device__ __forceinline__ void batch_item(const int4 it, const BatchPair* __res
 // chunk} of a batch of independent problems (items[], pairs[], one pose per
 // pair); tiles_per_split is then the chunk length in tiles.
 // KS, SUB: running sums in shared memory, record tiles staged SUB at a time.
-template <int P, int PM, int TPB, int TJ, int MINB, bool BATCH, bool KS = false, int SUB = 1>
+template <int P, int PM, int TPB, int TJ, int MINB, bool BATCH, bool KS = false, int SUB = 1, int EXO = 0>
 __global__ void __launch_bounds__(TPB, MINB)
     force_tile_kernel(const float* __restrict__ Xr, const float* __restrict__ XA, int ntiles,
                       int tiles_per_split, const float4* __restrict__ Y0r, int mpad,
@@ -306,7 +348,7 @@ __global__ void __launch_bounds__(TPB, MINB)
     ps = pose;
     outbase = partial + (size_t)blockIdx.y * mpad + ibase;
   }
-  force_block<P, PM, TPB, TJ, KS, SUB>(sT, sK, Xr, XA, t0, t1, Y0r, ibase, ps, qexp, outbase);
+  force_block<P, PM, TPB, TJ, KS, SUB, EXO>(sT, sK, Xr, XA, t0, t1, Y0r, ibase, ps, qexp, outbase);
 }
 
 // Persistent form of the batched pass: a grid of resident blocks takes work
@@ -374,6 +416,7 @@ ForcePlan plan_force(int64_t m, int64_t npad, double p, int num_sms, const Force
     fp.occ = ((fp.P == 4 && fp.tpb == 128) || (fp.P == 2 && fp.tpb == 256)) ? 2 : 0;
   else
     fp.occ = 0;
+  fp.ex2poly = (fp.pmode == 2 && fp.occ == 2) ? (tune.ex2poly < fp.P ? tune.ex2poly : fp.P) : 0;
   const int64_t per_block = (int64_t)fp.tpb * fp.P;
   fp.iblocks = (int)((m + per_block - 1) / per_block);
   const int ntiles = (int)(npad / FORCE_TJ);
@@ -412,12 +455,12 @@ int64_t force_mpad(int64_t m, const ForcePlan& fp) {
   return (mp + 255) / 256 * 256;
 }
 
-template <int P, int PM, int TPB, int MINB, bool KS, int SUB>
+template <int P, int PM, int TPB, int MINB, bool KS, int SUB, int EXO>
 static void launch_force_t(cudaStream_t st, const ForcePlan& fp, const float4* Xr,
                            const float2* XA, int ntiles, const float4* Y0r, int mpad,
                            const DevPose* pose, float qexp, float4* partial) {
   dim3 grid(fp.iblocks, fp.splits);
-  force_tile_kernel<P, PM, TPB, FORCE_TJ, MINB, false, KS, SUB><<<grid, TPB, 0, st>>>(
+  force_tile_kernel<P, PM, TPB, FORCE_TJ, MINB, false, KS, SUB, EXO><<<grid, TPB, 0, st>>>(
       reinterpret_cast<const float*>(Xr), reinterpret_cast<const float*>(XA), ntiles,
       fp.tiles_per_split, Y0r, mpad, pose, qexp, partial, nullptr, nullptr);
 }
@@ -430,8 +473,16 @@ template <class F>
 static int with_shape(const ForcePlan& fp, const F& f) {
   const bool hi = fp.occ == 1;
   if (fp.occ == 2) {
-    if (fp.P == 4 && fp.tpb == 128) return f.template operator()<4, 128, 3, true, 2>();
-    if (fp.P == 2 && fp.tpb == 256) return f.template operator()<2, 256, 2, true, 2>();
+    if (fp.P == 4 && fp.tpb == 128) {
+      if (fp.ex2poly == 1) return f.template operator()<4, 128, 3, true, 2, 1>();
+      if (fp.ex2poly == 2) return f.template operator()<4, 128, 3, true, 2, 2>();
+      return f.template operator()<4, 128, 3, true, 2>();
+    }
+    if (fp.P == 2 && fp.tpb == 256) {
+      if (fp.ex2poly == 1) return f.template operator()<2, 256, 2, true, 2, 1>();
+      if (fp.ex2poly == 2) return f.template operator()<2, 256, 2, true, 2, 2>();
+      return f.template operator()<2, 256, 2, true, 2>();
+    }
   }
   if (fp.tpb == 256) {
     if (fp.P == 4) return f.template operator()<4, 256, 2, false, 1>();
@@ -455,9 +506,11 @@ struct LaunchShape {
   const DevPose* pose;
   float qexp;
   float4* partial;
-  template <int P, int TPB, int MINB, bool KS, int SUB>
+  template <int P, int TPB, int MINB, bool KS, int SUB, int EXO = 0>
   int operator()() const {
-    launch_force_t<P, PM, TPB, MINB, KS, SUB>(st, fp, Xr, XA, ntiles, Y0r, mpad, pose, qexp, partial);
+    // the FP32-pipe exponential exists for p = 2 (sqrt form) only
+    constexpr int E = PM == 2 ? EXO : 0;
+    launch_force_t<P, PM, TPB, MINB, KS, SUB, E>(st, fp, Xr, XA, ntiles, Y0r, mpad, pose, qexp, partial);
     return 0;
   }
 };
@@ -471,11 +524,12 @@ static void launch_force_pm(cudaStream_t st, const ForcePlan& fp, const float4* 
 
 template <int PM>
 struct OccShape {
-  template <int P, int TPB, int MINB, bool KS, int SUB>
+  template <int P, int TPB, int MINB, bool KS, int SUB, int EXO = 0>
   int operator()() const {
+    constexpr int E = PM == 2 ? EXO : 0;
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, force_tile_kernel<P, PM, TPB, FORCE_TJ, MINB, false, KS, SUB>,
-                                                      TPB, 0) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &nb, force_tile_kernel<P, PM, TPB, FORCE_TJ, MINB, false, KS, SUB, E>, TPB, 0) != cudaSuccess) {
       cudaGetLastError();
       return 2;
     }
@@ -861,13 +915,16 @@ __global__ void __launch_bounds__(CMB_TPB, 8)
       float f[3];
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
-        // D = (Sh - Sc) - y (Wh - Wc): y Wh = p + pe exactly, Sh - p = dh + dl exactly
-        const float p = y[a] * Wh;
-        const float pe = fmaf(y[a], Wh, -p);
-        const float dh = Sh[a] - p;
-        const float bv = dh - Sh[a];
-        const float dl = (Sh[a] - (dh - bv)) + (-p - bv);
-        const float D = dh + ((dl - pe) + fmaf(y[a], Wc, -Sc[a]));
+        // D = (Sh - Sc) - y (Wh - Wc): y Wh = p + pe exactly, Sh - p = dh + dl
+        // exactly.  Each step is an explicitly rounded operation, so the
+        // compiler cannot contract y Wh into the subtraction (the error-free
+        // transformations need p and dh rounded on their own).
+        const float p = __fmul_rn(y[a], Wh);
+        const float pe = __fmaf_rn(y[a], Wh, -p);
+        const float dh = __fsub_rn(Sh[a], p);
+        const float bv = __fsub_rn(dh, Sh[a]);
+        const float dl = __fadd_rn(__fsub_rn(Sh[a], __fsub_rn(dh, bv)), __fsub_rn(-p, bv));
+        const float D = __fadd_rn(dh, __fadd_rn(__fsub_rn(dl, pe), __fmaf_rn(y[a], Wc, -Sc[a])));
         f[a] = ay * D;
       }
       const float Wi = ay * (Wh - Wc);

@@ -32,6 +32,7 @@ EXPORTED = (
     "scgr_potential", "scgr_batch_run", "scgr_set_tuning", "scgr_set_row_range", "scgr_step_partials",
     "scgr_step_apply", "scgr_get_plan", "scgr_microbench", "scgr_set_neighbourhood", "scgr_nearest",
     "scgr_change_mask", "scgr_force_vjp", "scgr_potential_stored", "scgr_debug_fail_allocations",
+    "scgr_step_partials_dev", "scgr_step_apply_dev",
 )
 SCGR_TUNE_BATCH_CHUNK_TILES = 1
 SCGR_TUNE_KNN_GRID_MIN = 2
@@ -43,6 +44,7 @@ SCGR_TUNE_FORCE_OCC = 7
 SCGR_TUNE_BATCH_P = 8
 SCGR_TUNE_BATCH_PERSISTENT = 10
 SCGR_TUNE_FORCE_RSQRT = 9
+SCGR_TUNE_FORCE_EX2POLY = 11
 
 
 class scgr_params(Structure):
@@ -123,6 +125,8 @@ def load():
         "scgr_set_row_range": (S, [ctx, c_int64, c_int64]),
         "scgr_step_partials": (S, [ctx, POINTER(c_double)]),
         "scgr_step_apply": (S, [ctx, POINTER(c_double)]),
+        "scgr_step_partials_dev": (S, [ctx, c_void_p]),
+        "scgr_step_apply_dev": (S, [ctx, c_void_p, c_int]),
         "scgr_potential": (S, [ctx, POINTER(c_double), POINTER(c_double), POINTER(c_double), c_void_p]),
         "scgr_forces_static": (S, [c_void_p, c_int64, c_void_p, c_int64, c_void_p, c_void_p, c_double,
                                    c_double, c_int, c_void_p, c_void_p]),
@@ -329,6 +333,22 @@ def scgr_step_partials(ctx) -> np.ndarray:
 def scgr_step_apply(ctx, totals) -> None:
     t = (c_double * 13)(*[float(v) for v in np.asarray(totals, dtype=np.float64).reshape(13)])
     _check(load().scgr_step_apply(ctx, t), ctx)
+
+
+def scgr_step_partials_dev(ctx, out13) -> None:
+    """Enqueue this rank's 13 float64 partial sums into the CUDA tensor out13
+    (13 doubles, contiguous)."""
+    if out13.numel() != 13:
+        raise ValueError("out13 must hold 13 doubles")
+    _check(load().scgr_step_partials_dev(ctx, _dev_ptr(out13.reshape(-1), "float64")), ctx)
+
+
+def scgr_step_apply_dev(ctx, parts) -> None:
+    """Enqueue the pose update from the ranks' partial sums gathered in rank
+    order: a CUDA float64 tensor of shape [nparts, 13] (or 13 * nparts)."""
+    if parts.numel() % 13 != 0 or parts.numel() == 0:
+        raise ValueError("parts must hold nparts x 13 doubles")
+    _check(load().scgr_step_apply_dev(ctx, _dev_ptr(parts.reshape(-1), "float64"), parts.numel() // 13), ctx)
 
 
 def scgr_microbench(kind: int, stream=None):

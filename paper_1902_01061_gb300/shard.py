@@ -9,6 +9,14 @@ update (Eq. 5.5 - Eq. 12).  This is the method's only exchange: 13 doubles
 per iteration.  The per-rank compute is a backend object with
 ``step_partials() -> ndarray[13]`` and ``step_apply(totals)``; the CUDA
 backend (``CudaRowShard``) runs both in the scgr library.
+
+``StreamShardedRegistration`` keeps the whole iteration on the device: the
+backend writes its partial sums into a 13-double tensor
+(``partials_into``), the ranks all-gather those tensors into a [world, 13]
+tensor in rank order (NCCL on the GPU: enqueued on the same stream, no host
+round trip), and the backend adds the rows in rank order and updates the pose
+from the totals (``apply_parts``; on the GPU both halves are single
+stream-ordered library calls).
 """
 from __future__ import annotations
 
@@ -42,6 +50,40 @@ def reduce_partials(local13, group=None):
     return total
 
 
+def gather_parts(local13, group=None):
+    """All-gather the ranks' 13-vectors (tensors on the backend's device) into
+    a [world, 13] tensor whose row r is rank r's (one process: [1, 13])."""
+    import torch
+    import torch.distributed as dist
+    v = local13.reshape(13)
+    if not (dist.is_available() and dist.is_initialized()):
+        return v.reshape(1, 13)
+    world = dist.get_world_size(group)
+    if dist.get_backend(group) == "nccl":
+        out = torch.empty((world, 13), dtype=v.dtype, device=v.device)
+        dist.all_gather_into_tensor(out, v, group=group)
+        return out
+    parts = [torch.empty_like(v) for _ in range(world)]
+    dist.all_gather(parts, v, group=group)
+    return torch.stack(parts)
+
+
+class StreamShardedRegistration:
+    """Iterations of one row-sharded registration with the exchange kept on
+    the backend's device: partials into a 13-double tensor, all-gather in
+    rank order, rank-ordered totals and pose update by the backend."""
+
+    def __init__(self, backend, group=None):
+        self.backend = backend
+        self.group = group
+        self.buf = backend.new_partials_buffer()
+
+    def run(self, iterations: int):
+        for _ in range(iterations):
+            self.backend.partials_into(self.buf)
+            self.backend.apply_parts(gather_parts(self.buf, self.group))
+
+
 class ShardedRegistration:
     """Runs iterations of one registration whose template rows are split
     over the ranks of `group` (default: the default process group)."""
@@ -63,7 +105,7 @@ class CudaRowShard:
     def __init__(self, X, Y0, row0: int, rows: int, params=None, stream=None):
         from . import scgr
         self.scgr = scgr
-        self.ctx = scgr.scgr_create(params, stream)
+        self.ctx = scgr.scgr_create(params, stream)     # None: torch's current stream
         scgr.scgr_set_reference(self.ctx, X)
         scgr.scgr_set_template(self.ctx, Y0)
         scgr.scgr_set_row_range(self.ctx, row0, rows)
@@ -74,6 +116,16 @@ class CudaRowShard:
 
     def step_apply(self, totals):
         self.scgr.scgr_step_apply(self.ctx, totals)
+
+    def new_partials_buffer(self):
+        import torch
+        return torch.empty(13, dtype=torch.float64, device="cuda")
+
+    def partials_into(self, buf):
+        self.scgr.scgr_step_partials_dev(self.ctx, buf)
+
+    def apply_parts(self, parts):
+        self.scgr.scgr_step_apply_dev(self.ctx, parts)
 
     def result(self):
         return self.scgr.scgr_get_result(self.ctx)

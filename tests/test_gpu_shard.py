@@ -42,6 +42,38 @@ def test_two_row_shards_match_unsharded_run():
     check_pose("two row shards vs unsharded", Ra, ta, sa, Rr, tr, sr, diag)
 
 
+def test_stream_ordered_row_shards_match_unsharded_run():
+    """The stream-ordered form: each shard enqueues its 13 partial sums into a
+    device tensor, the tensors are gathered in rank order on the device (the
+    all-gather of a multi-GPU run), and each shard adds them and updates its
+    pose on the device; no host round trip per iteration.  Both shards hold
+    identical poses, equal to the unsharded run within the pose tolerance."""
+    case = synth.mild(n=1500)
+    iters = 12
+    X = torch.from_numpy(case.X).cuda()
+    Y0 = torch.from_numpy(case.Y0).cuda()
+    params = scgr.scgr_default_params(E=iters)
+    shards = [shard.CudaRowShard(X, Y0, *shard.row_partition(len(case.Y0), 2, r), params=params) for r in range(2)]
+    try:
+        bufs = [s.new_partials_buffer() for s in shards]
+        for _ in range(iters):
+            for s, b in zip(shards, bufs):
+                s.partials_into(b)
+            parts = torch.stack(bufs)                   # rank order
+            for s in shards:
+                s.apply_parts(parts)
+        a, b = (s.result() for s in shards)
+    finally:
+        for s in shards:
+            s.close()
+    assert list(a.R) == list(b.R) and list(a.t) == list(b.t) and a.s == b.s and a.iterations == iters
+    with Gpu(case.X, case.Y0, E=iters) as g:
+        ref = g.run(iters)
+    Ra, ta, sa = a.as_numpy()
+    Rr, tr, sr = ref.as_numpy()
+    check_pose("two stream-ordered row shards vs unsharded", Ra, ta, sa, Rr, tr, sr, synth.bbox_diag(case.X))
+
+
 def test_row_range_guards():
     case = synth.mild(n=300)
     ctx = scgr.scgr_create(scgr.scgr_default_params())
@@ -57,6 +89,13 @@ def test_row_range_guards():
         assert e.value.status == 2
         with pytest.raises(scgr.ScgrError) as e:
             scgr.scgr_step_partials(ctx)                       # needs params.E > 0
+        assert e.value.status == 2
+        buf = torch.zeros(13, dtype=torch.float64, device="cuda")
+        with pytest.raises(scgr.ScgrError) as e:
+            scgr.scgr_step_partials_dev(ctx, buf)
+        assert e.value.status == 2
+        with pytest.raises(scgr.ScgrError) as e:
+            scgr.scgr_step_apply_dev(ctx, buf)
         assert e.value.status == 2
     finally:
         scgr.scgr_destroy(ctx)

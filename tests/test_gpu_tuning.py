@@ -72,6 +72,38 @@ def test_rsqrt_distance_form_matches_oracle(P, tpb):
                    Y0, X, d["aY"], d["aX"], d["sigma"], 2.0, 1)
 
 
+@pytest.mark.parametrize("P,tpb,exo", [(4, 128, 1), (4, 128, 2), (2, 256, 1), (2, 256, 2)])
+def test_fp32_pipe_exponential_matches_oracle(P, tpb, exo):
+    """p = 2 with part of the similarity exponentials evaluated on the FP32
+    pipe (SCGR_TUNE_FORCE_EX2POLY) in the shared-memory-sum shapes: the same
+    parity bar, per row as well.  The template holds exact copies of
+    reference points (d = 0 pairs) and the padding of the last tiles has
+    infinite exponents, which must give weight 0."""
+    sc = synth.scale_case()
+    X = sc.X[synth.subsample(sc.X, 2600, 65)]
+    Y0 = np.concatenate([sc.Y0[synth.subsample(sc.Y0, 1500, 66)], X[:300]])
+    d = O.descriptors(X, Y0, O.Params(p=2.0))
+    f_ref, W_ref = O.forces(Y0, X, d["aY"], d["aX"], d["sigma"], 2.0, 1)
+    with Gpu(X, Y0, p=2.0) as g:
+        scgr.scgr_set_tuning(g.ctx, scgr.SCGR_TUNE_FORCE_P, P)
+        scgr.scgr_set_tuning(g.ctx, scgr.SCGR_TUNE_FORCE_TPB, tpb)
+        scgr.scgr_set_tuning(g.ctx, scgr.SCGR_TUNE_FORCE_OCC, 2)
+        scgr.scgr_set_tuning(g.ctx, scgr.SCGR_TUNE_FORCE_EX2POLY, exo)
+        plan = scgr.scgr_get_plan(g.ctx)
+        assert (plan["P"], plan["tpb"], plan["occ"]) == (P, tpb, 2)
+        f_poly = g.forces()
+        scgr.scgr_set_tuning(g.ctx, scgr.SCGR_TUNE_FORCE_EX2POLY, 0)
+        f_mufu = g.forces()
+        with pytest.raises(scgr.ScgrError):
+            scgr.scgr_set_tuning(g.ctx, scgr.SCGR_TUNE_FORCE_EX2POLY, 3)
+    assert np.isfinite(f_poly).all()
+    what = f"FP32-pipe exponential, P={P} tpb={tpb}, {exo} of {2 * P} pair updates per step"
+    check(f"force f_i, {what}: relative L2", rel_l2(f_poly[:, :3], f_ref), 1e-5)
+    check(f"weight W_i, {what}: relative L2", rel_l2(f_poly[:, 3], W_ref), 1e-5)
+    check(f"{what} vs special-function ex2: relative L2", rel_l2(f_poly, f_mufu), 1e-5)
+    check_rows(f"force rows, {what}", f_poly, f_ref, W_ref, Y0, X, d["aY"], d["aX"], d["sigma"], 2.0, 1)
+
+
 def test_autotuner_picks_and_caches(tmp_path, monkeypatch):
     monkeypatch.setenv("SCGR_TUNE_CACHE", str(tmp_path / "tune.json"))
     case = synth.mild(n=3000)

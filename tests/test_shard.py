@@ -31,6 +31,21 @@ class OracleRowShard:
         self.Y, _ = O.update_from_totals(self.Y, totals, self.prm, self.it, self.E, self.eX)
         self.it += 1
 
+    # the stream-ordered shape of the backend interface, on CPU tensors
+    def new_partials_buffer(self):
+        import torch
+        return torch.zeros(13, dtype=torch.float64)
+
+    def partials_into(self, buf):
+        import torch
+        buf.copy_(torch.from_numpy(self.step_partials()))
+
+    def apply_parts(self, parts):
+        total = np.zeros(13)
+        for row in parts.numpy():                  # rank order
+            total = total + row
+        self.step_apply(total)
+
 
 def test_update_from_totals_equals_step_once():
     case = synth.mild(n=250)
@@ -63,7 +78,7 @@ def _free_port():
         return s.getsockname()[1]
 
 
-def _worker(rank, world, port, iters, q):
+def _worker(rank, world, port, iters, q, stream_form=False):
     import torch.distributed as dist
     os.environ["MASTER_ADDR"] = "127.0.0.1"
     os.environ["MASTER_PORT"] = str(port)
@@ -73,18 +88,25 @@ def _worker(rank, world, port, iters, q):
         prm = O.Params(E=iters)
         row0, rows = shard.row_partition(len(case.Y0), world, rank)
         be = OracleRowShard(case.X, case.Y0, prm, row0, rows, iters)
-        shard.ShardedRegistration(be).run(iters)
+        if stream_form:
+            shard.StreamShardedRegistration(be).run(iters)
+        else:
+            shard.ShardedRegistration(be).run(iters)
         q.put((rank, be.Y))
     finally:
         dist.destroy_process_group()
 
 
-def test_two_gloo_ranks_match_single_rank():
+@pytest.mark.parametrize("stream_form", [False, True])
+def test_two_gloo_ranks_match_single_rank(stream_form):
+    """Host-side exchange (totals added by the shard module) and the
+    stream-ordered form (tensors all-gathered in rank order, totals added by
+    the backend) give the same registration on both ranks."""
     iters = 5
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
     port = _free_port()
-    procs = [ctx.Process(target=_worker, args=(r, 2, port, iters, q)) for r in range(2)]
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, iters, q, stream_form)) for r in range(2)]
     for p in procs:
         p.start()
     out = dict(q.get(timeout=300) for _ in procs)
