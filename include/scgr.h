@@ -347,7 +347,10 @@ SCGR_EXPORT scgr_status scgr_step_apply_dev(scgr_ctx* ctx, const double* parts_d
 #define SCGR_TUNE_FORCE_SPLITS 5      /* force kernel reference splits: 0 auto (wave-filling), >= 1 */
 #define SCGR_TUNE_BATCH_P 8           /* template points per thread in the batched force kernel: 1 (default)
                                          or 2 (128 threads per block), or 4 (64 threads per block, running
-                                         sums in shared memory) */
+                                         sums in shared memory); 0 mixed: per pair, 4 points x 128 threads
+                                         (512-point template blocks, running sums in shared memory) where
+                                         that padding costs less than the shape gains, else 2 x 128, both
+                                         in one launch (the persistent form is not used with 0) */
 #define SCGR_TUNE_FORCE_OCC 7         /* force kernel variant: 0 registers only, 2 resident blocks per SM;
                                          1 a tighter register budget and more resident blocks per SM (3 at
                                          256 threads, 4 at 128); 2 the per-point running sums in shared

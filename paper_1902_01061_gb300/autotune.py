@@ -19,7 +19,7 @@ from . import scgr
 SINGLE_CANDIDATES = [(P, tpb, occ) for P in (1, 2, 4) for tpb in (128, 256) for occ in (0, 1)
                      if not (P == 4 and tpb == 256 and occ == 1)] + [(4, 128, 2), (2, 256, 2)]
 BATCH_CHUNKS = (8, 16, 32)
-BATCH_P = (1, 2, 4)
+BATCH_P = (0, 1, 2, 4)
 
 
 def cache_path() -> str:
@@ -148,7 +148,8 @@ def tune_batch(ctx, ref_off, ref_xyz, tmp_off, tmp_xyz, p: float, iterations: in
     results = [timed(ct, P, 0, 0) for P in BATCH_P for ct in BATCH_CHUNKS]
     results.sort()
     _, ct, P, _, _ = results[0]
-    results.append(timed(ct, P, 0, 1))
+    if P != 0:                                     # the mixed form has no persistent variant
+        results.append(timed(ct, P, 0, 1))
     if float(p) == 2.0:
         results.append(timed(ct, P, 1, 0))
     results.sort()

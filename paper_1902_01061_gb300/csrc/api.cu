@@ -461,8 +461,8 @@ scgr_status scgr_set_tuning(scgr_ctx* c, int key, int value) {
     return SCGR_OK;
   }
   if (key == SCGR_TUNE_BATCH_P) {
-    if (value != 1 && value != 2 && value != 4)
-      return fail(c, SCGR_ERR_INVALID_ARG, "batch points per thread must be 1, 2 or 4");
+    if (value != 0 && value != 1 && value != 2 && value != 4)
+      return fail(c, SCGR_ERR_INVALID_ARG, "batch points per thread must be 0 (mixed), 1, 2 or 4");
     c->batch_P = value;
     return SCGR_OK;
   }

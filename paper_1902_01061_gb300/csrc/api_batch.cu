@@ -34,7 +34,8 @@ scgr_status scgr_batch_run(scgr_ctx* c, int npairs, const int64_t* ref_off, cons
 
   // ---- host plan: per-pair geometry, work items (longest first), tables
   const int CT = c->batch_chunk_tiles;
-  const int FB = batch_block_threads(c->batch_P) * c->batch_P;  // template points per batched force block
+  const bool mixed = c->batch_P == 0;  // per-pair shape: 4 x 128 (512-point blocks) or 2 x 128 (256)
+  const int FB0 = mixed ? 256 : batch_block_threads(c->batch_P) * c->batch_P;  // template points per force block
   std::vector<BatchPair> pairs(npairs);
   std::vector<int4> items;
   std::vector<int> cpair;
@@ -48,6 +49,8 @@ scgr_status scgr_batch_run(scgr_ctx* c, int npairs, const int64_t* ref_off, cons
     bp.y0 = tmp_off[p];
     bp.m = tmp_off[p + 1] - tmp_off[p];
     bp.ntiles = (int)((bp.n + FORCE_TJ - 1) / FORCE_TJ);
+    bp.shape4 = mixed && batch_pair_shape4(bp.m) ? 1 : 0;
+    const int FB = bp.shape4 ? 512 : FB0;
     bp.xtile0 = xt;
     xt += bp.ntiles;
     const int64_t round = FB > 256 ? FB : 256;  // whole force blocks and combine blocks
@@ -137,7 +140,7 @@ scgr_status scgr_batch_run(scgr_ctx* c, int npairs, const int64_t* ref_off, cons
   StepParams sp = step_params(c);
   const int pmode = (c->prm.p == 1.0) ? 1 : (c->prm.p == 2.0) ? (c->ftune.rsq == 1 ? 4 : 2) : (c->prm.p == 3.0) ? 3 : 0;
   int pgrid = 0;  // persistent form: one resident block per slot (queried before any capture)
-  if (c->batch_persistent) SCGR_CK(c, force_batch_slots(pmode, c->batch_P, &pgrid));
+  if (c->batch_persistent && !mixed) SCGR_CK(c, force_batch_slots(pmode, c->batch_P, &pgrid));
   auto enqueue = [&](Launch LL) -> scgr_status {
     for (int t = 0; t < iterations; ++t) {
       SCGR_CK(c, launch_force_batch(LL, pmode, c->batch_P, (int)items.size(), (const int4*)c->bitems.p, dpairs,

@@ -204,6 +204,8 @@ struct BatchPair {
   int ntiles;        // reference tiles of FORCE_TJ points
   int chunks;        // reference chunks (one partial per chunk and template point)
   int cblk0, ncblk;  // combine blocks [cblk0, cblk0 + ncblk) of 256 template slots
+  int shape4;        // mixed batched pass: 1 if this pair's force items take 4 template points x 128 threads
+                     // (512-point blocks, running sums in shared memory), 0 for 2 points x 128 threads
 };
 
 // Uniform grid of the exact grid kNN: origin, cell edge, cells per axis.
@@ -316,6 +318,7 @@ cudaError_t launch_force_batch(Launch L, int pmode, int P, int nitems, const int
 cudaError_t force_batch_slots(int pmode, int P, int* slots);
 // Threads per block of the batched force kernel with P template points per thread.
 int batch_block_threads(int P);
+bool batch_pair_shape4(int64_t m);
 cudaError_t launch_combine_batch(Launch L, int nblocks, const int* cpair, const BatchPair* pairs,
                                  const float4* partial, const float4* Y0r, const double* aY64, int g_mode,
                                  const DevPose* poses, double* blockpart);

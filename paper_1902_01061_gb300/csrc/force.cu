@@ -381,6 +381,37 @@ __global__ void __launch_bounds__(TPB, MINB)
   }
 }
 
+// Mixed batched pass: each work item takes the shape its pair was planned
+// with (BatchPair::shape4) - 4 template points x 128 threads with the running
+// sums in shared memory and 512-point stages, the fastest shape per pair
+// (the one large templates use), for pairs whose templates fill 512-point
+// blocks well, and 2 points x 128 threads for the others, whose templates
+// would otherwise be padded to a multiple of 512.  One launch for both
+// shapes, so the longest-first item order fills the last wave with the
+// shortest items of either kind.  The 2-point shape uses the first half of
+// the record stage as its 256-point tile.
+template <int PM>
+__global__ void __launch_bounds__(128, 3)
+    force_batch_mixed_kernel(const float* __restrict__ Xr, const float* __restrict__ XA, int tiles_per_split,
+                             const float4* __restrict__ Y0r, const DevPose* __restrict__ pose, float qexp,
+                             float4* __restrict__ partial, const int4* __restrict__ items,
+                             const BatchPair* __restrict__ pairs) {
+  __shared__ __align__(16) float sT[6][FORCE_TJ * 2];
+  __shared__ float sK[8 * 4 * 128];
+  const int4 it = items[blockIdx.x];
+  int ibase, t0, t1;
+  const DevPose* ps;
+  float4* outbase;
+  if (pairs[it.x].shape4) {
+    batch_item<4, 128>(it, pairs, tiles_per_split, pose, partial, ibase, t0, t1, ps, outbase);
+    force_block<4, PM, 128, FORCE_TJ, true, 2>(sT, sK, Xr, XA, t0, t1, Y0r, ibase, ps, qexp, outbase);
+  } else {
+    batch_item<2, 128>(it, pairs, tiles_per_split, pose, partial, ibase, t0, t1, ps, outbase);
+    float(&s1)[6][FORCE_TJ] = *reinterpret_cast<float(*)[6][FORCE_TJ]>(&sT[0][0]);
+    force_block<2, PM, 128, FORCE_TJ, false, 1>(s1, sK, Xr, XA, t0, t1, Y0r, ibase, ps, qexp, outbase);
+  }
+}
+
 // ---- planning --------------------------------------------------------------
 
 static int force_blocks_per_sm(const ForcePlan& fp);
@@ -581,27 +612,44 @@ struct BatchShape {
 
 int batch_block_threads(int P) { return P == 4 ? BatchShape<4>::TPB : BatchShape<1>::TPB; }
 
+// Shape of pair template of m points in the mixed batched pass: the 4-point
+// shape (512-point blocks) unless its padding costs more than its speed
+// (measured per pair on GB300: 9.0 against 8.5 pairs per clock per SM for
+// the 2-point shape with 256-point blocks).
+bool batch_pair_shape4(int64_t m) {
+  const int64_t pad4 = (m + 511) / 512 * 512;
+  const int64_t pad2 = (m + 255) / 256 * 256;
+  return (double)pad4 * 8.5 <= (double)pad2 * 9.0;
+}
+
 template <int P, int PM>
 static void launch_force_batch_p(cudaStream_t st, int nitems, const int4* items, const BatchPair* pairs,
                                  const float4* Xr, const float2* XA, const float4* Y0r, const DevPose* poses,
                                  float qexp, float4* partial, int chunk_tiles, int grid, int* next) {
-  using B = BatchShape<P>;
   const float* xr = reinterpret_cast<const float*>(Xr);
   const float* xa = reinterpret_cast<const float*>(XA);
-  if (grid <= 0)
-    force_tile_kernel<P, PM, B::TPB, FORCE_TJ, B::MINB, true, B::KS, B::SUB><<<nitems, B::TPB, 0, st>>>(
-        xr, xa, 0, chunk_tiles, Y0r, 0, poses, qexp, partial, items, pairs);
-  else
-    force_batch_persistent_kernel<P, PM, B::TPB, FORCE_TJ, B::MINB, B::KS, B::SUB>
-        <<<grid < nitems ? grid : nitems, B::TPB, 0, st>>>(xr, xa, chunk_tiles, Y0r, poses, qexp, partial, items,
-                                                          nitems, pairs, next);
+  if constexpr (P == 0) {
+    force_batch_mixed_kernel<PM><<<nitems, 128, 0, st>>>(xr, xa, chunk_tiles, Y0r, poses, qexp, partial, items,
+                                                         pairs);
+  } else {
+    using B = BatchShape<P>;
+    if (grid <= 0)
+      force_tile_kernel<P, PM, B::TPB, FORCE_TJ, B::MINB, true, B::KS, B::SUB><<<nitems, B::TPB, 0, st>>>(
+          xr, xa, 0, chunk_tiles, Y0r, 0, poses, qexp, partial, items, pairs);
+    else
+      force_batch_persistent_kernel<P, PM, B::TPB, FORCE_TJ, B::MINB, B::KS, B::SUB>
+          <<<grid < nitems ? grid : nitems, B::TPB, 0, st>>>(xr, xa, chunk_tiles, Y0r, poses, qexp, partial, items,
+                                                            nitems, pairs, next);
+  }
 }
 
 template <int PM>
 static void launch_force_batch_pm(cudaStream_t st, int P, int nitems, const int4* items, const BatchPair* pairs,
                                   const float4* Xr, const float2* XA, const float4* Y0r, const DevPose* poses,
                                   float qexp, float4* partial, int chunk_tiles, int grid, int* next) {
-  if (P == 4)
+  if (P == 0)
+    launch_force_batch_p<0, PM>(st, nitems, items, pairs, Xr, XA, Y0r, poses, qexp, partial, chunk_tiles, 0, next);
+  else if (P == 4)
     launch_force_batch_p<4, PM>(st, nitems, items, pairs, Xr, XA, Y0r, poses, qexp, partial, chunk_tiles, grid, next);
   else if (P == 2)
     launch_force_batch_p<2, PM>(st, nitems, items, pairs, Xr, XA, Y0r, poses, qexp, partial, chunk_tiles, grid, next);

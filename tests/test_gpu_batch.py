@@ -118,7 +118,7 @@ def test_persistent_batch_kernel_is_bit_identical(P, chunk, use_graph):
         assert list(ra.R) == list(rb.R) and list(ra.t) == list(rb.t) and ra.s == rb.s
 
 
-@pytest.mark.parametrize("P", [2, 4])
+@pytest.mark.parametrize("P", [0, 2, 4])
 def test_batch_chunk_tuning_keeps_results_close(P):
     pairs = make_pairs([3000, 700], seed=17)
     a, _ = run_batch(pairs, 10, p=2.0)
@@ -137,6 +137,29 @@ def test_batch_chunk_tuning_keeps_results_close(P):
         scgr.scgr_destroy(ctx)
     for (X, _), ra, rb in zip(pairs, a, b):
         assert close(ra, rb, synth.bbox_diag(X), f"batched, chunk 3 / P {P} / rsqrt vs defaults")
+
+
+@pytest.mark.parametrize("use_graph", [0, 1])
+def test_mixed_shape_batch_matches_single_pair_runs(use_graph):
+    """The mixed batched pass (SCGR_TUNE_BATCH_P = 0): pairs whose templates
+    fill 512-point blocks take 4 points x 128 threads with shared-memory sums,
+    the others 2 points x 128 threads, in one launch.  Sizes on both sides of
+    the choice (600 and 2,100 points take the 2-point shape, 2,000, 4,096 and
+    5,200 the 4-point one), and a 16-point pair; every pair against a
+    one-pair-per-call run of the same library, and replay against eager."""
+    pairs = make_pairs([600, 2000, 5200, 4096, 2100, 16, 1300], seed=37)
+    iters = 15
+    res, la = run_batch(pairs, iters, tuning=((scgr.SCGR_TUNE_BATCH_P, 0),), p=2.0, use_graph=use_graph)
+    for (X, Y), r in zip(pairs, res):
+        with Gpu(X, Y, p=2.0) as g:
+            single = g.run(iters)
+        assert r.iterations == iters
+        assert close(r, single, synth.bbox_diag(X), "mixed-shape batch vs one call per pair")
+    if use_graph:
+        eager, lb = run_batch(pairs, iters, tuning=((scgr.SCGR_TUNE_BATCH_P, 0),), p=2.0, use_graph=0)
+        assert la == lb
+        for ra, rb in zip(res, eager):
+            assert list(ra.R) == list(rb.R) and list(ra.t) == list(rb.t) and ra.s == rb.s
 
 
 def test_batch_rejects_bad_offsets():
