@@ -376,6 +376,11 @@ SCGR_EXPORT scgr_status scgr_step_apply_dev(scgr_ctx* ctx, const double* parts_d
                                          polynomial, relative error < 2^-22; 2^-e below 2^-125.5 reads 0),
                                          which moves a fraction value / (2 P) of the exponentials off the
                                          special-function unit.  Results agree with 0 to rounding */
+#define SCGR_TUNE_NEAREST_LEVELS 12  /* nearest-point search over a gridded reference (scgr_nearest,
+                                         scgr_change_mask): 2 (default) fine cells around the query, then
+                                         coarse cells of 4 x 4 x 4 fine cells that skip empty ones and ones
+                                         beyond the best distance so far; 1 fine shells only.  The result
+                                         is the same */
 #define SCGR_TUNE_REUSE_POSE_FREE 6   /* 1 (default): odd integer p skips the per-iteration all-pairs pass.
                                          p = 1: the pair weights do not depend on the pose, so scgr_run
                                          computes the force sums once per call and reuses them

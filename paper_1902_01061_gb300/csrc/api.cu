@@ -94,7 +94,7 @@ void scgr_destroy(scgr_ctx* c) {
                     &c->bXr, &c->bXA, &c->bY0r, &c->bpartial, &c->bblockpart, &c->bpairs, &c->bitems,
                     &c->bcpair, &c->btabX, &c->btabY, &c->bxoff, &c->byoff, &c->bstats, &c->bposes, &c->bnext,
                     &c->gcell, &c->gcount, &c->gstart, &c->gcursor, &c->gblock, &c->gsorted, &c->gsidx, &c->gbb,
-                    &c->rgstart, &c->rgsorted, &c->rgsidx,
+                    &c->rgstart, &c->rgsorted, &c->rgsidx, &c->rcgstart, &c->rcgsorted, &c->rcgsidx,
                     &c->cd_key, &c->cd_moved, &c->wstore, &c->wupart, &c->wpartial, &c->mpart, &c->mom};
   for (DevBuf* b : bufs) release(*b);
   if (c->pose) cudaFree(c->pose);
@@ -448,6 +448,11 @@ scgr_status scgr_set_tuning(scgr_ctx* c, int key, int value) {
     if (value < 0 || value > 2) return fail(c, SCGR_ERR_INVALID_ARG, "value must be 0, 1 or 2");
     c->ftune.ex2poly = value;
     return c->have_desc ? replan(c) : SCGR_OK;
+  }
+  if (key == SCGR_TUNE_NEAREST_LEVELS) {
+    if (value != 1 && value != 2) return fail(c, SCGR_ERR_INVALID_ARG, "value must be 1 or 2");
+    c->nearest_levels = value;
+    return SCGR_OK;
   }
   if (key == SCGR_TUNE_REUSE_POSE_FREE) {
     if (value != 0 && value != 1) return fail(c, SCGR_ERR_INVALID_ARG, "value must be 0 or 1");

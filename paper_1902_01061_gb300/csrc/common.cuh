@@ -248,6 +248,12 @@ cudaError_t launch_nearest(Launch L, const float4* P, int n, const float* q3, in
                            float* key_out);
 cudaError_t launch_grid_build(Launch L, const float4* P, int n, const GridSpec& gs, int* cell_of, int* count,
                               int* start, int* cursor, int* block_tot, float4* sorted, int* sorted_idx);
+constexpr int NEAREST_COARSE = 4;  // fine cells per coarse cell side in the two-level nearest search
+GridSpec coarse_grid_spec(const GridSpec& gs);
+cudaError_t launch_nearest_grid2(Launch L, const float4* sorted, const int* sorted_idx, const int* start,
+                                 const GridSpec& gs, const float4* csorted, const int* csorted_idx,
+                                 const int* cstart, const GridSpec& gc, const float* q3, int nq, int32_t* idx_out,
+                                 float* key_out);
 cudaError_t launch_nearest_grid(Launch L, const float4* sorted, const int* sorted_idx, const int* start,
                                 const GridSpec& gs, const float* q3, int nq, int32_t* idx_out, float* key_out);
 cudaError_t launch_threshold(Launch L, const float* key, int nq, float thr2, uint8_t* mask, float* dist);

@@ -85,9 +85,10 @@ struct scgr_ctx {
   DevBuf gcell, gcount, gstart, gcursor, gblock, gsorted, gsidx, gbb, cd_key, cd_moved, wstore, wupart, wpartial,
       mpart, mom;
   // the reference's grid for nearest-point queries, kept until the reference changes
-  DevBuf rgstart, rgsorted, rgsidx;
-  GridSpec rgspec{};
+  DevBuf rgstart, rgsorted, rgsidx, rcgstart, rcgsorted, rcgsidx;  // fine and coarse levels
+  GridSpec rgspec{}, rcgspec{};
   bool rgrid_ok = false;
+  int nearest_levels = 2;       // 2: two-level nearest search (default), 1: fine shells only (tunable)
   cudaGraph_t bgraph = nullptr;
   cudaGraphExec_t bgexec = nullptr;
 

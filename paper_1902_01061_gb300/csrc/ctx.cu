@@ -189,11 +189,12 @@ scgr_status knn_cloud(scgr_ctx* c, const float4* P, int n, int32_t* out) {
 
 // Nearest reference point of nq external queries (float32 [nq][3] on the
 // device): brute force below knn_grid_min reference points, else the exact
-// grid search over a grid of the reference (the same result).  The
-// reference's grid is built on the first query after scgr_set_reference and
-// kept in its own buffers (the descriptor pass reuses the shared grid
-// workspace for both clouds), so later queries skip the bounding-box
-// synchronisation and the counting sort.
+// two-level grid search over the reference (the same result): fine cells
+// around the query, then coarse cells that skip empty space.  The
+// reference's two grids are built on the first query after
+// scgr_set_reference and kept in their own buffers (the descriptor pass
+// reuses the shared grid workspace for both clouds), so later queries skip
+// the bounding-box synchronisation and the counting sorts.
 scgr_status nearest_reference(scgr_ctx* c, const float* q3, int nq, int32_t* idx_out, float* key_out) {
   const float4* X4 = (const float4*)c->X4.p;
   const int n = (int)c->n;
@@ -211,11 +212,27 @@ scgr_status nearest_reference(scgr_ctx* c, const float* q3, int nq, int32_t* idx
     SCGR_CK(c, ensure(c->rgsidx, (size_t)n * sizeof(int)));
     SCGR_CK(c, launch_grid_build(c->L(), X4, n, gs, (int*)c->gcell.p, (int*)c->gcount.p, (int*)c->rgstart.p,
                                  (int*)c->gcursor.p, (int*)c->gblock.p, (float4*)c->rgsorted.p, (int*)c->rgsidx.p));
+    // the coarse level: the same counting sort with cells NEAREST_COARSE times larger
+    // (it fits the fine level's count/cursor/block scratch)
+    const GridSpec gc = coarse_grid_spec(gs);
+    SCGR_CK(c, ensure(c->rcgstart, (size_t)(grid_cells(gc) + 1) * sizeof(int)));
+    SCGR_CK(c, ensure(c->rcgsorted, (size_t)n * sizeof(float4)));
+    SCGR_CK(c, ensure(c->rcgsidx, (size_t)n * sizeof(int)));
+    SCGR_CK(c, launch_grid_build(c->L(), X4, n, gc, (int*)c->gcell.p, (int*)c->gcount.p, (int*)c->rcgstart.p,
+                                 (int*)c->gcursor.p, (int*)c->gblock.p, (float4*)c->rcgsorted.p, (int*)c->rcgsidx.p));
     c->rgspec = gs;
+    c->rcgspec = gc;
     c->rgrid_ok = true;
   }
-  SCGR_CK(c, launch_nearest_grid(c->L(), (const float4*)c->rgsorted.p, (const int*)c->rgsidx.p,
-                                 (const int*)c->rgstart.p, c->rgspec, q3, nq, idx_out, key_out));
+  if (c->nearest_levels == 1) {
+    SCGR_CK(c, launch_nearest_grid(c->L(), (const float4*)c->rgsorted.p, (const int*)c->rgsidx.p,
+                                   (const int*)c->rgstart.p, c->rgspec, q3, nq, idx_out, key_out));
+  } else {
+    SCGR_CK(c, launch_nearest_grid2(c->L(), (const float4*)c->rgsorted.p, (const int*)c->rgsidx.p,
+                                    (const int*)c->rgstart.p, c->rgspec, (const float4*)c->rcgsorted.p,
+                                    (const int*)c->rcgsidx.p, (const int*)c->rcgstart.p, c->rcgspec, q3, nq, idx_out,
+                                    key_out));
+  }
   return SCGR_OK;
 }
 

@@ -453,9 +453,12 @@ ForcePlan plan_force(int64_t m, int64_t npad, double p, int num_sms, const Force
   const int ntiles = (int)(npad / FORCE_TJ);
   const int64_t slots = (int64_t)num_sms * force_blocks_per_sm(fp);
   // at least 8 waves when the reference range allows it, at most 64 splits,
-  // and at least 4 tiles per split
+  // and at least 4 tiles per split - unless even that leaves the grid short
+  // of one wave (small problems, where a block's sequential walk over its
+  // tiles is the launch's latency): then down to one tile per split
   int64_t S_lo = (8 * slots + fp.iblocks - 1) / fp.iblocks;
   int64_t S_hi = ntiles / 4 > 0 ? ntiles / 4 : 1;
+  if ((int64_t)fp.iblocks * S_hi < slots) S_hi = ntiles;
   if (S_hi > 64) S_hi = 64;
   if (S_lo > S_hi) S_lo = S_hi;
   if (S_lo < 1) S_lo = 1;

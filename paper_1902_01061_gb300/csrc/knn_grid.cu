@@ -242,6 +242,127 @@ __global__ void __launch_bounds__(GRID_TPB)
   if (key_out) key_out[t] = kd[0];
 }
 
+// Nearest gridded point (k = 1, first of the (key, index) order) over the
+// shells 0..smax of cells around q's cell in grid g.  With `prune`, a
+// non-empty cell is skipped when every point of its box is farther than the
+// best key so far (its squared box distance, less a 1e-6 margin for the
+// rounding of the float32 key, exceeds that key, so no point in it can even
+// tie).  Re-scanning a point already seen leaves the best unchanged.
+// Returns true once the best is certified by the stop rule of grid_scan (or
+// the whole grid has been scanned).
+__device__ __forceinline__ bool nearest_shells(const float4 q, const float4* __restrict__ sorted,
+                                               const int* __restrict__ sorted_idx, const int* __restrict__ start,
+                                               const GridSpec& g, int smax, bool prune, float& bk, int& bi) {
+  const int cc[3] = {cell_coord(q.x, g.o[0], g.inv_h, g.g[0]), cell_coord(q.y, g.o[1], g.inv_h, g.g[1]),
+                     cell_coord(q.z, g.o[2], g.inv_h, g.g[2])};
+  const float qq[3] = {q.x, q.y, q.z};
+  const int sgrid = max(g.g[0], max(g.g[1], g.g[2]));
+  const int slast = smax < sgrid ? smax : sgrid;
+  for (int s = 0; s <= slast; ++s) {
+    for (int dz = -s; dz <= s; ++dz) {
+      const int z = cc[2] + dz;
+      if (z < 0 || z >= g.g[2]) continue;
+      for (int dy = -s; dy <= s; ++dy) {
+        const int y = cc[1] + dy;
+        if (y < 0 || y >= g.g[1]) continue;
+        const bool face = (dz == -s || dz == s || dy == -s || dy == s);
+        const int step = face ? 1 : (s > 0 ? 2 * s : 1);
+        for (int dx = -s; dx <= s; dx += step) {
+          const int x = cc[0] + dx;
+          if (x < 0 || x >= g.g[0]) continue;
+          const int cell = (z * g.g[1] + y) * g.g[0] + x;
+          const int b = start[cell], e = start[cell + 1];
+          if (b == e) continue;
+          if (prune && bi != INT_MAX) {
+            const int xyz[3] = {x, y, z};
+            double d2 = 0.0;
+            for (int a = 0; a < 3; ++a) {
+              const double lo = g.o[a] + (double)xyz[a] * g.h;
+              const double hi = lo + g.h;
+              const double v = (double)qq[a];
+              const double d = v < lo ? lo - v : (v > hi ? v - hi : 0.0);
+              d2 += d * d;
+            }
+            if (d2 * (1.0 - 1e-6) > (double)bk) continue;
+          }
+          for (int j = b; j < e; ++j) {
+            const float4 c = sorted[j];
+            const float ex = __fsub_rn(q.x, c.x);
+            const float ey = __fsub_rn(q.y, c.y);
+            const float ez = __fsub_rn(q.z, c.z);
+            const float key = __fadd_rn(__fadd_rn(__fmul_rn(ex, ex), __fmul_rn(ey, ey)), __fmul_rn(ez, ez));
+            const int idx = sorted_idx[j];
+            if (lex_less(key, idx, bk, bi)) {
+              bk = key;
+              bi = idx;
+            }
+          }
+        }
+      }
+    }
+    double dout = INFINITY;
+    bool all = true;
+    for (int a = 0; a < 3; ++a) {
+      if (cc[a] - s > 0) {
+        dout = fmin(dout, (double)qq[a] - (g.o[a] + (double)(cc[a] - s) * g.h));
+        all = false;
+      }
+      if (cc[a] + s < g.g[a] - 1) {
+        dout = fmin(dout, (g.o[a] + (double)(cc[a] + s + 1) * g.h) - (double)qq[a]);
+        all = false;
+      }
+    }
+    if (all) return true;
+    if (bi != INT_MAX && dout > 0.0 && (double)bk < dout * dout * (1.0 - 1e-6)) return true;
+  }
+  return false;
+}
+
+// Two-level exact nearest search: the query's own cell and its neighbours
+// in the fine grid (enough for a query on the surface), then, if that does
+// not certify the nearest point, shells of the coarse grid (cells of
+// NEAREST_COARSE fine cells a side, points sorted by coarse cell) that skip
+// empty coarse cells and coarse cells beyond the best key.  A query far off
+// the surface then visits a few hundred coarse cells instead of the
+// (1.7 D / h)^3 fine cells a fine shell scan needs to certify distance D.
+// The result is the (key, index)-first point, as the one-level search gives.
+__global__ void __launch_bounds__(GRID_TPB)
+    nearest_grid2_kernel(const float4* __restrict__ sorted, const int* __restrict__ sorted_idx,
+                         const int* __restrict__ start, GridSpec gs, const float4* __restrict__ csorted,
+                         const int* __restrict__ csorted_idx, const int* __restrict__ cstart, GridSpec gc,
+                         const float* __restrict__ q3, int nq, int32_t* __restrict__ idx_out,
+                         float* __restrict__ key_out) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nq) return;
+  const float4 q = make_float4(q3[3 * (size_t)t], q3[3 * (size_t)t + 1], q3[3 * (size_t)t + 2], 0.f);
+  float bk = INFINITY;
+  int bi = INT_MAX;
+  if (!nearest_shells(q, sorted, sorted_idx, start, gs, 1, false, bk, bi))
+    nearest_shells(q, csorted, csorted_idx, cstart, gc, INT_MAX, true, bk, bi);
+  if (idx_out) idx_out[t] = bi;
+  if (key_out) key_out[t] = bk;
+}
+
+// The coarse grid over the same origin: cells of NEAREST_COARSE fine cells a side.
+GridSpec coarse_grid_spec(const GridSpec& gs) {
+  GridSpec gc = gs;
+  gc.h = gs.h * NEAREST_COARSE;
+  gc.inv_h = 1.0 / gc.h;
+  for (int a = 0; a < 3; ++a) gc.g[a] = (gs.g[a] + NEAREST_COARSE - 1) / NEAREST_COARSE;
+  return gc;
+}
+
+cudaError_t launch_nearest_grid2(Launch L, const float4* sorted, const int* sorted_idx, const int* start,
+                                 const GridSpec& gs, const float4* csorted, const int* csorted_idx,
+                                 const int* cstart, const GridSpec& gc, const float* q3, int nq, int32_t* idx_out,
+                                 float* key_out) {
+  if (nq <= 0) return cudaSuccess;
+  nearest_grid2_kernel<<<(nq + GRID_TPB - 1) / GRID_TPB, GRID_TPB, 0, L.stream>>>(
+      sorted, sorted_idx, start, gs, csorted, csorted_idx, cstart, gc, q3, nq, idx_out, key_out);
+  if (L.counter) *L.counter += 1;
+  return cudaGetLastError();
+}
+
 // Grid spec from the bounding box: cell edge h = sqrt(8 A / n) with A the box
 // surface area (about 8 points per occupied cell on a surface sample), at most
 // 8 n cells, at least one cell per axis.

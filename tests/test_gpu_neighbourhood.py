@@ -115,6 +115,35 @@ def test_nearest_grid_at_full_size():
     np.testing.assert_array_equal(out["grid"][1][sample], key_ref)
 
 
+def test_nearest_two_level_search_off_surface_queries():
+    """The two-level search (fine cells, then coarse cells skipping empty
+    space) and the fine-shell search give the same (key, index)-first point
+    as the brute force for queries spread through the 1M reference's box,
+    most of them off the surface, plus queries on reference points and far
+    outside the box; the second query pass reuses the cached grids."""
+    import torch
+    big = synth.large_case()
+    rng = np.random.default_rng(91)
+    lo, hi = big.X.min(axis=0), big.X.max(axis=0)
+    Q = np.concatenate([rng.uniform(lo, hi, size=(3000, 3)).astype(np.float32),
+                        big.X[rng.choice(len(big.X), size=500, replace=False)],
+                        (hi + np.float32(1.0) + rng.uniform(0, 2, size=(200, 3))).astype(np.float32)])
+    Qd = torch.from_numpy(Q).cuda()
+    out = {}
+    for name, gmin, levels in (("two-level", 65536, 2), ("fine", 65536, 1), ("brute", 1 << 30, 2)):
+        with Gpu(big.X, big.Y0[:64], tune={scgr.SCGR_TUNE_KNN_GRID_MIN: gmin,
+                                           scgr.SCGR_TUNE_NEAREST_LEVELS: levels}) as g:
+            idx = torch.empty(len(Q), dtype=torch.int32, device="cuda")
+            key = torch.empty(len(Q), dtype=torch.float32, device="cuda")
+            for _ in range(2):
+                scgr.scgr_nearest(g.ctx, Qd, idx, key)
+            out[name] = (idx.cpu().numpy(), key.cpu().numpy())
+    for name in ("two-level", "fine"):
+        check(f"nearest: {name} grid search vs brute force, indices differing (1M reference, off-surface queries)",
+              np.count_nonzero(out[name][0] != out["brute"][0]), 0)
+        np.testing.assert_array_equal(out[name][1], out["brute"][1])
+
+
 @pytest.mark.parametrize("grid", [False, True])
 def test_change_mask_at_identity_pose(grid):
     """A template whose part moved between captures: the moved part is
