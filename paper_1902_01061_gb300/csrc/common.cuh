@@ -306,6 +306,10 @@ cudaError_t launch_combine(Launch L, const float4* partial, int S, int mpad, int
                            const float4* Y0r, const double* aY64, int g_mode,
                            const DevPose* pose, float4* f4out, double* blockpart);
 cudaError_t launch_pose_init(Launch L, DevPose* pose, const DevStats* stats, int E);
+constexpr int FUSED_MAX_SLOTS = 2048;  // templates up to this many padded slots: combine_finalize_kernel
+cudaError_t launch_combine_finalize(Launch L, const float4* partial, int S, int mpad, int m, const float4* Y0r,
+                                    const double* aY64, int g_mode, DevPose* pose, const DevStats* stats,
+                                    StepParams sp, int* err);
 cudaError_t launch_finalize(Launch L, const double* blockpart, int nblocks, DevPose* pose,
                             const DevStats* stats, StepParams sp, int* err);
 cudaError_t launch_apply(Launch L, const float4* Y4, int m, const DevPose* pose, float* out);

@@ -33,6 +33,7 @@
 
 #include "common.cuh"
 #include "ex2_poly.cuh"
+#include "pointsum.cuh"
 
 namespace scgr {
 
@@ -56,22 +57,6 @@ __device__ __forceinline__ float sqrt_approx(float x) {
   float y;
   asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
   return y;
-}
-
-// Template point in the frame centred on the reference mean: Y' = Y0 A + b.
-// The force and combine kernels both call this, so they see identical bits.
-__device__ __forceinline__ void template_point(const float4 y0, const float* A, const float* b,
-                                               float& yx, float& yy, float& yz) {
-  yx = fmaf(y0.z, A[6], fmaf(y0.y, A[3], fmaf(y0.x, A[0], b[0])));
-  yy = fmaf(y0.z, A[7], fmaf(y0.y, A[4], fmaf(y0.x, A[1], b[1])));
-  yz = fmaf(y0.z, A[8], fmaf(y0.y, A[5], fmaf(y0.x, A[2], b[2])));
-}
-
-__device__ __forceinline__ void kahan_add(float& s, float& c, float x) {
-  const float y = x - c;
-  const float t = s + y;
-  c = (t - s) - y;
-  s = t;
 }
 
 constexpr float RSQRT_CAP = 1e18f;
@@ -864,26 +849,6 @@ cudaError_t launch_combine_moments(Launch L, const double* mom, int m, int mpad,
 constexpr int CMB_TPB = 64;
 constexpr int CMB_PPT = 4;  // points per thread: CMB_TPB * CMB_PPT = 256 slots per block
 
-// Reduce 16 doubles over a warp by recursive halving: lane L ends with the
-// warp total of quantity 8 b4 + 4 b3 + 2 b2 + b1 (b_k = bit k of L), 16
-// additions per lane instead of 80 for a butterfly per quantity.
-__device__ __forceinline__ void warp_reduce16(double (&v)[16]) {
-  const int lane = threadIdx.x & 31;
-#pragma unroll
-  for (int lvl = 0; lvl < 4; ++lvl) {
-    const int off = 16 >> lvl;
-    const int half = 8 >> lvl;
-    const bool upper = (lane & off) != 0;
-#pragma unroll
-    for (int q = 0; q < half; ++q) {
-      const double send = upper ? v[q] : v[q + half];
-      const double keep = upper ? v[q + half] : v[q];
-      v[q] = keep + __shfl_xor_sync(0xffffffffu, send, off);
-    }
-  }
-  v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
-}
-
 // BATCH = true: block b belongs to pair cpair[b]; its 256 template slots are
 // that pair's slots (b - cblk0) * 256 + threadIdx.x + 64 k, k < 4.
 template <bool BATCH>
@@ -921,77 +886,14 @@ __global__ void __launch_bounds__(CMB_TPB, 8)
     abase = aY64;
     ps = pose;
   }
-  float A[9], b[3], ch[3], cl[3];
-#pragma unroll
-  for (int q = 0; q < 9; ++q) A[q] = ps->A[q];
-#pragma unroll
-  for (int q = 0; q < 3; ++q) {
-    b[q] = ps->b[q];
-    const double yb = ps->ybs[q];  // template mean (centred frame) as a float pair
-    ch[q] = (float)yb;
-    cl[q] = (float)(yb - (double)ch[q]);
-  }
+  const PointFrame fr(ps);
   float acc[13];
 #pragma unroll
   for (int q = 0; q < 13; ++q) acc[q] = 0.f;
 #pragma unroll
   for (int k = 0; k < CMB_PPT; ++k) {
     const int i = i0 + k * CMB_TPB + threadIdx.x;
-    if (i < mm) {
-      float Wh = 0.f, Wc = 0.f, Sh[3] = {0.f, 0.f, 0.f}, Sc[3] = {0.f, 0.f, 0.f};
-      // splits in order; four loads issued together
-      int s = 0;
-      for (; s + 4 <= SS; s += 4) {
-        float4 pp[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) pp[u] = pbase[(size_t)(s + u) * pstride + i];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          kahan_add(Wh, Wc, pp[u].x);
-          kahan_add(Sh[0], Sc[0], pp[u].y);
-          kahan_add(Sh[1], Sc[1], pp[u].z);
-          kahan_add(Sh[2], Sc[2], pp[u].w);
-        }
-      }
-      for (; s < SS; ++s) {
-        const float4 pp = pbase[(size_t)s * pstride + i];
-        kahan_add(Wh, Wc, pp.x);
-        kahan_add(Sh[0], Sc[0], pp.y);
-        kahan_add(Sh[1], Sc[1], pp.z);
-        kahan_add(Sh[2], Sc[2], pp.w);
-      }
-      float y[3];
-      template_point(ybase[i], A, b, y[0], y[1], y[2]);
-      const float ay = g_mode == 1 ? (float)abase[i] : 1.f;
-      float f[3];
-#pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        // D = (Sh - Sc) - y (Wh - Wc): y Wh = p + pe exactly, Sh - p = dh + dl
-        // exactly.  Each step is an explicitly rounded operation, so the
-        // compiler cannot contract y Wh into the subtraction (the error-free
-        // transformations need p and dh rounded on their own).
-        const float p = __fmul_rn(y[a], Wh);
-        const float pe = __fmaf_rn(y[a], Wh, -p);
-        const float dh = __fsub_rn(Sh[a], p);
-        const float bv = __fsub_rn(dh, Sh[a]);
-        const float dl = __fadd_rn(__fsub_rn(Sh[a], __fsub_rn(dh, bv)), __fsub_rn(-p, bv));
-        const float D = __fadd_rn(dh, __fadd_rn(__fsub_rn(dl, pe), __fmaf_rn(y[a], Wc, -Sc[a])));
-        f[a] = ay * D;
-      }
-      const float Wi = ay * (Wh - Wc);
-      float c[3];
-#pragma unroll
-      for (int q = 0; q < 3; ++q) c[q] = (y[q] - ch[q]) - cl[q];
-      acc[0] += f[0];
-      acc[1] += f[1];
-      acc[2] += f[2];
-      acc[3] += Wi;
-#pragma unroll
-      for (int a = 0; a < 3; ++a)
-#pragma unroll
-        for (int bb = 0; bb < 3; ++bb) acc[4 + 3 * a + bb] = fmaf(f[a], c[bb], acc[4 + 3 * a + bb]);
-      if (f4out) f4out[i] = make_float4(f[0], f[1], f[2], Wi);
-    }
+    if (i < mm) point_force(pbase, pstride, SS, i, ybase[i], g_mode == 1 ? (float)abase[i] : 1.f, fr, acc, f4out);
   }
   double v[16];
 #pragma unroll
@@ -999,8 +901,7 @@ __global__ void __launch_bounds__(CMB_TPB, 8)
   v[13] = v[14] = v[15] = 0.0;
   warp_reduce16(v);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int qid = ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 + ((lane >> 1) & 1);
-  if ((lane & 1) == 0) sh[warp][qid] = v[0];
+  if ((lane & 1) == 0) sh[warp][warp_reduce16_slot(lane)] = v[0];
   __syncthreads();
   if (threadIdx.x < 13) {
     double t = sh[0][threadIdx.x];

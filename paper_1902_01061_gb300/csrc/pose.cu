@@ -7,6 +7,7 @@
 #include <cmath>
 
 #include "common.cuh"
+#include "pointsum.cuh"
 
 namespace scgr {
 
@@ -331,21 +332,18 @@ __device__ bool reorth_warp(double R, Lane3 L, double& out) {
   return true;
 }
 
-__device__ void finalize_body(const double* __restrict__ blockpart, int nblocks, DevPose* ps,
-                              const DevStats* __restrict__ st, StepParams sp, int* err,
-                              double (*sh)[RED_THREADS]) {
-  double v[13];
-#pragma unroll
-  for (int q = 0; q < 13; ++q) v[q] = 0.0;
-  for (int bidx = threadIdx.x; bidx < nblocks; bidx += RED_THREADS) {
-#pragma unroll
-    for (int q = 0; q < 13; ++q) v[q] += blockpart[(size_t)bidx * 13 + q];
-  }
-  block_sum<13>(v, sh);
-  __syncthreads();  // every thread has read the totals: sh is scratch from here on
-  if (threadIdx.x >= 32) return;
+// Rows up to which warp 0 adds the per-block partials by itself: lane q
+// (q < 13) adds column q over the rows in order, and the totals are shared
+// by shuffles.  A warp-wide float64 instruction occupies the scheduler's
+// float64 unit for tens of cycles on GB300, so for a few rows this is far
+// cheaper than the block-wide tree (about 150 such instructions).
+constexpr int FINALIZE_WARP_ROWS = 64;
 
-  // Warp 0 forms the update; lane (r, c) owns entry (r, c) of each 3x3.
+// Warp 0 forms the update from the 13 totals v (the same in every lane of
+// warp 0; F[3], W, T[3][3]); lane (r, c) owns entry (r, c) of each 3x3.
+// sh is scratch (at least 64 doubles).
+__device__ void finalize_update(const double (&v)[13], DevPose* ps, const DevStats* __restrict__ st,
+                                StepParams sp, int* err, double (*sh)[RED_THREADS]) {
   const Lane3 L = lane3();
   const int lane = threadIdx.x;
   const double W = v[3];
@@ -458,6 +456,80 @@ __device__ void finalize_body(const double* __restrict__ blockpart, int nblocks,
     ps->s = sn;
     ps->it = it + 1;
   }
+}
+
+// Totals of nblocks rows of 13 partials (fixed order), then the update.
+__device__ void finalize_body(const double* __restrict__ blockpart, int nblocks, DevPose* ps,
+                              const DevStats* __restrict__ st, StepParams sp, int* err,
+                              double (*sh)[RED_THREADS]) {
+  double v[13];
+  if (nblocks <= FINALIZE_WARP_ROWS) {
+    if (threadIdx.x >= 32) return;
+    const int lane = threadIdx.x;
+    double col = 0.0;
+    if (lane < 13)
+      for (int b = 0; b < nblocks; ++b) col += blockpart[(size_t)b * 13 + lane];
+#pragma unroll
+    for (int q = 0; q < 13; ++q) v[q] = __shfl_sync(WFULL, col, q);
+  } else {
+#pragma unroll
+    for (int q = 0; q < 13; ++q) v[q] = 0.0;
+    for (int bidx = threadIdx.x; bidx < nblocks; bidx += RED_THREADS) {
+#pragma unroll
+      for (int q = 0; q < 13; ++q) v[q] += blockpart[(size_t)bidx * 13 + q];
+    }
+    block_sum<13>(v, sh);
+    __syncthreads();  // every thread has read the totals: sh is scratch from here on
+    if (threadIdx.x >= 32) return;
+  }
+  finalize_update(v, ps, st, sp, err, sh);
+}
+
+// Combine and finalize in one block, for templates of at most
+// FUSED_MAX_SLOTS padded slots (the latency regime of small problems): each
+// thread forms the force of its slots from their split partials
+// (point_force, as the combine kernel), the 13 sums are reduced per warp
+// (float64) and across the warps in order by warp 0, and warp 0 updates the
+// pose.  One launch per iteration instead of two, and no per-block partials.
+__global__ void __launch_bounds__(RED_THREADS)
+    combine_finalize_kernel(const float4* __restrict__ partial, int S, int mpad, int m,
+                            const float4* __restrict__ Y0r, const double* __restrict__ aY64, int g_mode,
+                            DevPose* ps, const DevStats* __restrict__ st, StepParams sp, int* err) {
+  __shared__ double sh[13][RED_THREADS];
+  float acc[13];
+#pragma unroll
+  for (int q = 0; q < 13; ++q) acc[q] = 0.f;
+  {
+    const PointFrame fr(ps);
+    for (int i = threadIdx.x; i < m; i += RED_THREADS)
+      point_force(partial, (size_t)mpad, S, i, Y0r[i], g_mode == 1 ? (float)aY64[i] : 1.f, fr, acc, nullptr);
+  }
+  double w[16];
+#pragma unroll
+  for (int q = 0; q < 13; ++q) w[q] = (double)acc[q];
+  w[13] = w[14] = w[15] = 0.0;
+  warp_reduce16(w);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if ((lane & 1) == 0) sh[warp_reduce16_slot(lane)][warp] = w[0];
+  __syncthreads();  // all of ps and sh read/written: warp 0 updates the pose from here
+  if (warp != 0) return;
+  double col = 0.0;
+  if (lane < 13)
+    for (int k = 0; k < RED_THREADS / 32; ++k) col += sh[lane][k];
+  __syncwarp();
+  double v[13];
+#pragma unroll
+  for (int q = 0; q < 13; ++q) v[q] = __shfl_sync(WFULL, col, q);
+  finalize_update(v, ps, st, sp, err, sh);
+}
+
+cudaError_t launch_combine_finalize(Launch L, const float4* partial, int S, int mpad, int m, const float4* Y0r,
+                                    const double* aY64, int g_mode, DevPose* pose, const DevStats* stats,
+                                    StepParams sp, int* err) {
+  combine_finalize_kernel<<<1, RED_THREADS, 0, L.stream>>>(partial, S, mpad, m, Y0r, aY64, g_mode, pose, stats, sp,
+                                                           err);
+  if (L.counter) ++*L.counter;
+  return cudaGetLastError();
 }
 
 __global__ void __launch_bounds__(RED_THREADS)
