@@ -703,49 +703,88 @@ cudaError_t force_batch_slots(int pmode, int P, int* slots) {
 //   sum w   = |Y|^2 M0 - 2 Y.M1 + m2,
 //   sum w X = |Y|^2 M1 - 2 M2 Y + m3,
 // with M0 = sum g, M1 = sum g X', M2 = sum g X' X'^T, m2 = sum g |X'|^2,
-// m3 = sum g |X'|^2 X'.  One pass computes them (float32 per tile, float64
-// across tiles), after which an iteration is O(M).
+// m3 = sum g |X'|^2 X'.  One pass computes them (packed float32 per tile,
+// Kahan-compensated float32 across tiles), after which an iteration is O(M).
 constexpr int MOM_TPB = 256;
 constexpr int NMOM = 14;  // M0, M1[3], M2[6] (xx xy xz yy yz zz), m2, m3[3]
 
+// One packed moment update: reference points (j, j+1) against one template
+// point (ah = its a_hat in both lanes): g = 2^-(u^2 - L) (the pair factor of
+// the force kernel), then g, g X', g X' X'^T, g |X'|^2, g |X'|^2 X' added to
+// the 14 packed accumulators m[].
+__device__ __forceinline__ void moment2(u64 xv, u64 yv, u64 zv, u64 nv, u64 av, u64 lv, u64 ah, u64 (&m)[NMOM]) {
+  const u64 u = sub2(av, ah);
+  float e0, e1;
+  upk2(fma2(u, u, lv), e0, e1);
+  const u64 g = pk2(ex2_neg(e0), ex2_neg(e1));
+  const u64 gx = mul2(g, xv), gy = mul2(g, yv), gz = mul2(g, zv), gn = mul2(g, nv);
+  m[0] = add2(m[0], g);
+  m[1] = add2(m[1], gx);
+  m[2] = add2(m[2], gy);
+  m[3] = add2(m[3], gz);
+  m[4] = fma2(gx, xv, m[4]);
+  m[5] = fma2(gx, yv, m[5]);
+  m[6] = fma2(gx, zv, m[6]);
+  m[7] = fma2(gy, yv, m[7]);
+  m[8] = fma2(gy, zv, m[8]);
+  m[9] = fma2(gz, zv, m[9]);
+  m[10] = add2(m[10], gn);
+  m[11] = fma2(gn, xv, m[11]);
+  m[12] = fma2(gn, yv, m[12]);
+  m[13] = fma2(gn, zv, m[13]);
+}
+
+// Per template point, the 14 moments over reference tiles [t0, t1) of one
+// split: each tile's sums in packed float32 (two reference points per
+// instruction, 128-bit shared-memory broadcasts of four points), added to
+// float32 running sums with Kahan compensation; the split's result is
+// written as doubles.  Padding records have -L = +inf, so g = 0.
 __global__ void __launch_bounds__(MOM_TPB)
     moments_kernel(const float* __restrict__ Xr, const float* __restrict__ XA, int ntiles, int tiles_per_split,
                    const float4* __restrict__ Y0r, int mpad, double* __restrict__ mpart) {
-  __shared__ float sT[6][FORCE_TJ];
+  __shared__ __align__(16) float sT[6][FORCE_TJ];
   const int i = blockIdx.x * MOM_TPB + threadIdx.x;
   const int split = blockIdx.y;
-  const float ah = Y0r[i].w;
-  double acc[NMOM];
+  const float a = Y0r[i].w;
+  const u64 ah = pk2(a, a);
+  float hs[NMOM], cs[NMOM];
 #pragma unroll
-  for (int q = 0; q < NMOM; ++q) acc[q] = 0.0;
+  for (int q = 0; q < NMOM; ++q) hs[q] = cs[q] = 0.f;
   const int t0 = split * tiles_per_split;
   const int t1 = min(ntiles, t0 + tiles_per_split);
+  constexpr int Q4 = FORCE_TJ / 4;
   for (int t = t0; t < t1; ++t) {
     __syncthreads();
-    for (int u = threadIdx.x; u < 4 * FORCE_TJ; u += MOM_TPB) (&sT[0][0])[u] = Xr[(size_t)t * 4 * FORCE_TJ + u];
-    for (int u = threadIdx.x; u < 2 * FORCE_TJ; u += MOM_TPB) (&sT[4][0])[u] = XA[(size_t)t * 2 * FORCE_TJ + u];
+    const float4* g4 = reinterpret_cast<const float4*>(Xr + (size_t)t * 4 * FORCE_TJ);
+    const float4* a4 = reinterpret_cast<const float4*>(XA + (size_t)t * 2 * FORCE_TJ);
+    for (int u = threadIdx.x; u < 4 * Q4; u += MOM_TPB) *reinterpret_cast<float4*>(&sT[u / Q4][4 * (u % Q4)]) = g4[u];
+    for (int u = threadIdx.x; u < 2 * Q4; u += MOM_TPB)
+      *reinterpret_cast<float4*>(&sT[4 + u / Q4][4 * (u % Q4)]) = a4[u];
     __syncthreads();
-    float m[NMOM];
+    u64 m[NMOM];
 #pragma unroll
-    for (int q = 0; q < NMOM; ++q) m[q] = 0.f;
-    for (int j = 0; j < FORCE_TJ; ++j) {
-      const float x = sT[0][j], y = sT[1][j], z = sT[2][j], nx = sT[3][j];
-      const float uu = sT[4][j] - ah;
-      const float g = exp2f(-fmaf(uu, uu, sT[5][j]));
-      const float gx = g * x, gy = g * y, gz = g * z, gn = g * nx;
-      m[0] += g;
-      m[1] += gx; m[2] += gy; m[3] += gz;
-      m[4] = fmaf(gx, x, m[4]); m[5] = fmaf(gx, y, m[5]); m[6] = fmaf(gx, z, m[6]);
-      m[7] = fmaf(gy, y, m[7]); m[8] = fmaf(gy, z, m[8]); m[9] = fmaf(gz, z, m[9]);
-      m[10] += gn;
-      m[11] = fmaf(gn, x, m[11]); m[12] = fmaf(gn, y, m[12]); m[13] = fmaf(gn, z, m[13]);
+    for (int q = 0; q < NMOM; ++q) m[q] = 0ull;
+#pragma unroll 2
+    for (int jq = 0; jq < FORCE_TJ; jq += 4) {
+      const ulonglong2 X = *reinterpret_cast<const ulonglong2*>(&sT[0][jq]);
+      const ulonglong2 Yv = *reinterpret_cast<const ulonglong2*>(&sT[1][jq]);
+      const ulonglong2 Z = *reinterpret_cast<const ulonglong2*>(&sT[2][jq]);
+      const ulonglong2 N = *reinterpret_cast<const ulonglong2*>(&sT[3][jq]);
+      const ulonglong2 Av = *reinterpret_cast<const ulonglong2*>(&sT[4][jq]);
+      const ulonglong2 Lv = *reinterpret_cast<const ulonglong2*>(&sT[5][jq]);
+      moment2(X.x, Yv.x, Z.x, N.x, Av.x, Lv.x, ah, m);
+      moment2(X.y, Yv.y, Z.y, N.y, Av.y, Lv.y, ah, m);
     }
 #pragma unroll
-    for (int q = 0; q < NMOM; ++q) acc[q] += m[q];
+    for (int q = 0; q < NMOM; ++q) {
+      float l0, l1;
+      upk2(m[q], l0, l1);
+      kahan_add(hs[q], cs[q], l0 + l1);
+    }
   }
   double* out = mpart + ((size_t)split * mpad + i) * NMOM;
 #pragma unroll
-  for (int q = 0; q < NMOM; ++q) out[q] = acc[q];
+  for (int q = 0; q < NMOM; ++q) out[q] = (double)hs[q] - (double)cs[q];
 }
 
 // Per-point moments: the splits added in order.

@@ -510,7 +510,12 @@ __global__ void __launch_bounds__(RED_THREADS)
   w[13] = w[14] = w[15] = 0.0;
   warp_reduce16(w);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  if ((lane & 1) == 0) sh[warp_reduce16_slot(lane)][warp] = w[0];
+  // even lanes hold quantities 0..15 after the reduction; 13..15 are padding
+  // and have no row in sh
+  if ((lane & 1) == 0) {
+    const int q = warp_reduce16_slot(lane);
+    if (q < 13) sh[q][warp] = w[0];
+  }
   __syncthreads();  // all of ps and sh read/written: warp 0 updates the pose from here
   if (warp != 0) return;
   double col = 0.0;
