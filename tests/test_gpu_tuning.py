@@ -143,18 +143,20 @@ def test_p3_moment_path_matches_all_pairs_and_oracle():
     case = synth.mild(n=1500)
     iters = 25
     with Gpu(case.X, case.Y0, p=3.0) as g:
+        scgr.scgr_set_force_timing(g.ctx, True)
         a = g.run(iters)
-        na = scgr.scgr_launch_count(g.ctx)
+        na = scgr.scgr_get_force_timing(g.ctx)[0]
     with Gpu(case.X, case.Y0, p=3.0) as g:
         scgr.scgr_set_tuning(g.ctx, scgr.SCGR_TUNE_REUSE_POSE_FREE, 0)
+        scgr.scgr_set_force_timing(g.ctx, True)
         b = g.run(iters)
-        nb = scgr.scgr_launch_count(g.ctx)
+        nb = scgr.scgr_get_force_timing(g.ctx)[0]
     o = O.register(case.X, case.Y0, O.Params(p=3.0), iterations=iters)
     diag = synth.bbox_diag(case.X)
     for what, r in (("pose, p = 3 moment path", a), ("pose, p = 3 all-pairs path", b)):
         R, t, s = r.as_numpy()
         check_pose(what, R, t, s, o["R"], o["t"], o["s"], diag)
-    assert nb - na == iters - 2          # 2 moment launches replace 25 force launches
+    assert (na, nb) == (0, iters)        # one moments pass replaces the 25 all-pairs force launches
 
 
 def test_small_problem_splits_reference_down_to_single_tiles():
