@@ -198,7 +198,8 @@ scgr_status scgr_run(scgr_ctx* c, int iters) {
         e = cudaStreamEndCapture(c->cap_stream, &g);
       }
       c->stream = user;
-      c->launches = before;  // counted at replay
+      c->graph_launches = c->launches - before;  // kernel launches in the graph, counted at each replay
+      c->launches = before;
       if (st != SCGR_OK) { if (g) cudaGraphDestroy(g); return st; }
       if (e != cudaSuccess) return cuda_fail(c, e, "graph capture");
       c->graph = g;
@@ -211,8 +212,7 @@ scgr_status scgr_run(scgr_ctx* c, int iters) {
     SCGR_CK(c, cudaGraphLaunch(c->gexec, c->cap_stream));
     SCGR_CK(c, cudaEventRecord(c->join_out, c->cap_stream));
     SCGR_CK(c, cudaStreamWaitEvent(c->stream, c->join_out, 0));
-    const bool pf = c->fp.pmode == 1 && c->reuse_pose_free, mo = c->fp.pmode == 3 && c->reuse_pose_free;
-    c->launches += pf ? 2 * (int64_t)iters + 1 : (mo ? 2 * (int64_t)iters + 2 : 3 * (int64_t)iters);
+    c->launches += c->graph_launches;
   } else {
     scgr_status st = enqueue_iterations(c, iters);
     if (st != SCGR_OK) return st;

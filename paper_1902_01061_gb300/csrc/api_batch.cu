@@ -176,6 +176,7 @@ scgr_status scgr_batch_run(scgr_ctx* c, int npairs, const int64_t* ref_off, cons
         stq = enqueue(Launch{c->cap_stream, &c->launches});
         e = cudaStreamEndCapture(c->cap_stream, &g);
       }
+      const int64_t in_graph = c->launches - before;  // kernel launches of the graph, counted at its replay
       c->launches = before;
       if (stq != SCGR_OK) { if (g) cudaGraphDestroy(g); return stq; }
       if (e != cudaSuccess) return cuda_fail(c, e, "batch graph capture");
@@ -184,7 +185,7 @@ scgr_status scgr_batch_run(scgr_ctx* c, int npairs, const int64_t* ref_off, cons
       SCGR_CK(c, cudaGraphLaunch(c->bgexec, c->cap_stream));
       SCGR_CK(c, cudaEventRecord(c->join_out, c->cap_stream));
       SCGR_CK(c, cudaStreamWaitEvent(c->stream, c->join_out, 0));
-      c->launches += 3 * (int64_t)iterations;
+      c->launches += in_graph;
     } else {
       scgr_status stq = enqueue(L);
       if (stq != SCGR_OK) return stq;

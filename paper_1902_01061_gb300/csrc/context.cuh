@@ -69,6 +69,7 @@ struct scgr_ctx {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t gexec = nullptr;
   int graph_iters = -1;
+  int64_t graph_launches = 0;  // kernel launches one replay of the graph makes
   bool capturing = false;
   cudaStream_t cap_stream = nullptr;  // capture / replay stream (never the legacy stream)
   cudaEvent_t join_in = nullptr, join_out = nullptr;
