@@ -74,6 +74,26 @@ def test_stream_ordered_row_shards_match_unsharded_run():
     check_pose("two stream-ordered row shards vs unsharded", Ra, ta, sa, Rr, tr, sr, synth.bbox_diag(case.X))
 
 
+def test_stream_ordered_entry_points_reject_bad_arguments():
+    case = synth.mild(n=300)
+    ctx = scgr.scgr_create(scgr.scgr_default_params(E=4))
+    try:
+        scgr.scgr_set_reference(ctx, torch.from_numpy(case.X).cuda())
+        scgr.scgr_set_template(ctx, torch.from_numpy(case.Y0).cuda())
+        scgr.scgr_compute_descriptors(ctx)
+        lib = scgr.load()
+        assert lib.scgr_step_partials_dev(ctx, None) == 1                  # NULL output
+        parts = torch.zeros((1, 13), dtype=torch.float64, device="cuda")
+        assert lib.scgr_step_apply_dev(ctx, parts.data_ptr(), 0) == 1      # no parts
+        assert lib.scgr_step_apply_dev(ctx, None, 1) == 1                  # NULL parts
+        buf = torch.zeros(13, dtype=torch.float64, device="cuda")
+        scgr.scgr_step_partials_dev(ctx, buf)                              # then a good step
+        scgr.scgr_step_apply_dev(ctx, buf)
+        assert scgr.scgr_get_result(ctx).iterations == 1
+    finally:
+        scgr.scgr_destroy(ctx)
+
+
 def test_row_range_guards():
     case = synth.mild(n=300)
     ctx = scgr.scgr_create(scgr.scgr_default_params())
