@@ -1020,6 +1020,15 @@ def main():
         "next_rows": nxt,
     }
     line["peaks_measured"] = measured_peaks(scgr, num_sms, sm_mhz or sm_max_mhz)
+    # the co-bound of the p = 2 force kernel: one ex2 and one sqrt per pair on
+    # the special-function unit, at the rates just measured
+    pk = line["peaks_measured"]
+    sfu = 1.0 / (1.0 / pk["mufu_ex2"]["per_clk_per_sm"] + 1.0 / pk["mufu_sqrt"]["per_clk_per_sm"])
+    clk_mhz = sm_mhz or sm_max_mhz
+    got = n * nrows / (force_avg_ms * 1e-3) / (num_sms * clk_mhz * 1e6)
+    roofline["pairs_per_clk_per_sm"] = got
+    roofline["sfu_bound_pairs_per_clk_per_sm"] = sfu
+    roofline["frac_of_sfu_bound"] = got / sfu
     if ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(pair, 2.0, 1)
         try:
