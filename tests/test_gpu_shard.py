@@ -119,3 +119,69 @@ def test_row_range_guards():
         assert e.value.status == 2
     finally:
         scgr.scgr_destroy(ctx)
+
+
+def _nccl_worker(port, iters, q):
+    """One NCCL rank (world size 1) on the GPU: the row-split registration
+    with the exchange through NCCL collectives - the stream-ordered form's
+    all_gather_into_tensor and the host form's all_gather."""
+    import os
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    from paper_1902_01061_gb300 import scgr, shard, synth
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    torch.cuda.set_device(0)
+    dist.init_process_group("nccl", rank=0, world_size=1)
+    try:
+        case = synth.mild(n=1500)
+        X = torch.from_numpy(case.X).cuda()
+        Y0 = torch.from_numpy(case.Y0).cuda()
+        params = scgr.scgr_default_params(E=iters)
+        out = []
+        for form in ("stream", "host"):
+            be = shard.CudaRowShard(X, Y0, 0, len(case.Y0), params=params)
+            try:
+                if form == "stream":
+                    shard.StreamShardedRegistration(be).run(iters)
+                else:
+                    shard.ShardedRegistration(be).run(iters)
+                r = be.result()
+                out.append((np.array(r.R[:]), np.array(r.t[:]), r.s, r.iterations))
+            finally:
+                be.close()
+        q.put(("ok", out))
+    except Exception as e:                      # reported to the parent test
+        q.put(("error", repr(e)))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_nccl_exchange_single_rank():
+    """The NCCL branches of the shard exchange (device all-gather into a
+    [world, 13] tensor, and the host form's all-gather of 13-vectors) run
+    on the GPU in a one-rank NCCL process group (a child process, so the
+    group does not outlive the test); both give the unsharded pose."""
+    import socket
+    import torch.multiprocessing as mp
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    iters = 10
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    p = ctx.Process(target=_nccl_worker, args=(port, iters, q))
+    p.start()
+    status, out = q.get(timeout=600)
+    p.join(timeout=120)
+    assert status == "ok", out
+    assert p.exitcode == 0
+    case = synth.mild(n=1500)
+    with Gpu(case.X, case.Y0, E=iters) as g:
+        ref = g.run(iters)
+    Rr, tr, sr = ref.as_numpy()
+    for (R, t, s, it), form in zip(out, ("stream-ordered", "host")):
+        assert it == iters
+        check_pose(f"one NCCL rank, {form} exchange vs unsharded", R.reshape(3, 3), t, s, Rr, tr, sr,
+                   synth.bbox_diag(case.X))
