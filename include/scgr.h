@@ -294,8 +294,9 @@ SCGR_EXPORT scgr_status scgr_forces_static(const float* x_dev, int64_t n, const 
  * Descriptors for all clouds run in one launch per stage; each iteration is
  * three launches for all pairs (force work items sorted longest first, one
  * block per item or a persistent grid taking items from a queue, see
- * SCGR_TUNE_BATCH_PERSISTENT; a per-pair fixed-order combine; one float64
- * finalize block per pair); with
+ * SCGR_TUNE_BATCH_PERSISTENT, with one kernel shape for all pairs or a shape
+ * per pair, see SCGR_TUNE_BATCH_P; a per-pair fixed-order combine; one
+ * float64 finalize block per pair); with
  * params.use_graph the iteration loop is captured in a CUDA graph and
  * replayed.  results_host[p] receives pair p's pose (as scgr_get_result).
  * The single-registration state of the context is not touched.
