@@ -789,6 +789,9 @@ def main():
                     help="multi-GPU form: rows (default when WORLD_SIZE > 1) splits one registration by template rows "
                          "over the ranks; replicas runs the whole workload on every rank; none (default on one GPU) "
                          "is the single-context run")
+    ap.add_argument("--p", type=float, default=2.0,
+                    help="distance exponent of the main leg (default 2, the benchmark workload; 1 and 3 run the "
+                         "odd-p fast paths, for profiling them)")
     ap.add_argument("--oracle-only", action="store_true",
                     help="only the oracle's timings on the host (sampled 1M x 1M force rows, configs 1 and 2)")
     ap.add_argument("--batch-plan", default=None, help="pin the batched force kernel 'P,CHUNK_TILES[,PERSISTENT]' (no autotuning)")
@@ -854,7 +857,7 @@ def main():
     from paper_1902_01061_gb300 import shard
     row0, nrows = shard.row_partition(m, ws, rank) if rows_mode else (0, m)
     # row sharding iterates stepwise, which needs the Eq. 12 horizon up front
-    params = scgr.scgr_default_params(p=2.0, g_mode=1, k=16, E=iters if rows_mode else 0)
+    params = scgr.scgr_default_params(p=args.p, g_mode=1, k=16, E=iters if rows_mode else 0)
     stream = torch.cuda.current_stream()
     ctx = scgr.scgr_create(params, stream)
     num_sms = torch.cuda.get_device_properties(dev).multi_processor_count
@@ -898,7 +901,7 @@ def main():
     elif not args.no_autotune:
         from paper_1902_01061_gb300 import autotune
         load_clouds()
-        tuned = autotune.tune_single(ctx, n, nrows, 2.0, reps=2)
+        tuned = autotune.tune_single(ctx, n, nrows, args.p, reps=2)
 
     def step_device():
         load_clouds()
@@ -1004,7 +1007,8 @@ def main():
         "scaling": "strong" if rows_mode else "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "ms_per_iteration": ms_per_step / iters,
         "pct_fp32_peak": 100.0 * roofline["frac"],
-        "config": dict(base_config(args.workload, n, m), autotuned=tuned, l2="flushed between steps (256 MB write)",
+        "config": dict(base_config(args.workload, n, m), p=args.p, autotuned=tuned,
+                       l2="flushed between steps (256 MB write)",
                        parallelism=(f"rows x{ws} (template rows split over the ranks, 13 float64 partial sums "
                                     f"all-gathered on the device per iteration)" if rows_mode else f"replicas x{ws}")),
         "gpu_launches": launches,
