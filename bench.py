@@ -991,22 +991,28 @@ def main():
             dist.destroy_process_group()
         return 0
 
-    achieved_tflops = FLOPS_PER_PAIR * n * nrows / (force_avg_ms * 1e-3) / 1e12   # one launch: this rank's rows
     traffic, digest = profile_traffic()
-    roofline = {"bound": "alu", "achieved": achieved_tflops, "peak": peak_tflops, "unit": "TFLOP/s",
-                "frac": achieved_tflops / peak_tflops, "traffic": traffic,
-                "kernel": "force_tile_kernel", "flops_per_pair": FLOPS_PER_PAIR,
-                "force_launch_ms": force_avg_ms, "force_launches_timed": nforce,
-                "peak_basis": peak_basis}
-    if sm_mhz:
-        roofline["frac_at_measured_clock"] = achieved_tflops / (peak_tflops * sm_mhz / sm_max_mhz)
+    if nforce > 0:
+        achieved_tflops = FLOPS_PER_PAIR * n * nrows / (force_avg_ms * 1e-3) / 1e12   # one launch: this rank's rows
+        roofline = {"bound": "alu", "achieved": achieved_tflops, "peak": peak_tflops, "unit": "TFLOP/s",
+                    "frac": achieved_tflops / peak_tflops, "traffic": traffic,
+                    "kernel": "force_tile_kernel", "flops_per_pair": FLOPS_PER_PAIR,
+                    "force_launch_ms": force_avg_ms, "force_launches_timed": nforce,
+                    "peak_basis": peak_basis}
+        if sm_mhz:
+            roofline["frac_at_measured_clock"] = achieved_tflops / (peak_tflops * sm_mhz / sm_max_mhz)
+    else:
+        # the odd-p fast paths (--p 1 after its first pass, --p 3 always) launch no all-pairs force kernel
+        roofline = {"bound": "alu", "achieved": None, "peak": peak_tflops, "unit": "TFLOP/s", "frac": None,
+                    "traffic": None, "kernel": "force_tile_kernel", "force_launches_timed": 0,
+                    "peak_basis": peak_basis}
     line = {
         "metric": metric_name(args.workload),
         "value": value, "unit": "pair-interactions/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
         "scaling": "strong" if rows_mode else "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "ms_per_iteration": ms_per_step / iters,
-        "pct_fp32_peak": 100.0 * roofline["frac"],
+        "pct_fp32_peak": 100.0 * roofline["frac"] if roofline["frac"] is not None else None,
         "config": dict(base_config(args.workload, n, m), p=args.p, autotuned=tuned,
                        l2="flushed between steps (256 MB write)",
                        parallelism=(f"rows x{ws} (template rows split over the ranks, 13 float64 partial sums "
@@ -1029,10 +1035,11 @@ def main():
     pk = line["peaks_measured"]
     sfu = 1.0 / (1.0 / pk["mufu_ex2"]["per_clk_per_sm"] + 1.0 / pk["mufu_sqrt"]["per_clk_per_sm"])
     clk_mhz = sm_mhz or sm_max_mhz
-    got = n * nrows / (force_avg_ms * 1e-3) / (num_sms * clk_mhz * 1e6)
-    roofline["pairs_per_clk_per_sm"] = got
-    roofline["sfu_bound_pairs_per_clk_per_sm"] = sfu
-    roofline["frac_of_sfu_bound"] = got / sfu
+    if nforce > 0:
+        got = n * nrows / (force_avg_ms * 1e-3) / (num_sms * clk_mhz * 1e6)
+        roofline["pairs_per_clk_per_sm"] = got
+        roofline["sfu_bound_pairs_per_clk_per_sm"] = sfu
+        roofline["frac_of_sfu_bound"] = got / sfu
     if ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(pair, 2.0, 1)
         try:
