@@ -296,7 +296,7 @@ __device__ bool polar_newton_warp(double A, Lane3 L, double& Q) {
   if (!(n2 > 0.0) || !isfinite(n2)) return false;
   double X = A * (1.0 / sqrt(n2));
   const int r1 = (L.r + 1) % 3, r2 = (L.r + 2) % 3, c1 = (L.c + 1) % 3, c2 = (L.c + 2) % 3;
-  bool scale = true, settled = false;
+  bool scale = true;
   for (int it = 0; it < 40; ++it) {
     double C = fma(-wget(X, r1 * 3 + c2), wget(X, r2 * 3 + c1), wget(X, r1 * 3 + c1) * wget(X, r2 * 3 + c2));
     const double det = fma(wget(X, 2), wget(C, 2), fma(wget(X, 1), wget(C, 1), wget(X, 0) * wget(C, 0)));
@@ -310,8 +310,10 @@ __device__ bool polar_newton_warp(double A, Lane3 L, double& Q) {
     const float dx = (float)(Xn - X), fn = (float)Xn;
     const float dd = wsum9(dx * dx), nn = wsum9(fn * fn);
     X = Xn;
-    if (settled) break;  // one plain step after the change fell below 1e-9
-    if (dd <= 1e-18f * nn) settled = true;
+    // stop once a step changed X by at most 1e-9 of its norm: Newton's
+    // iteration converges quadratically there, so this iterate is within
+    // about (1e-9)^2 of the polar factor, below float64 rounding
+    if (dd <= 1e-18f * nn) break;
     scale = dd > 1e-4f * nn;
     if (it == 39) return false;
   }
