@@ -164,3 +164,26 @@ def test_change_mask_at_identity_pose(grid):
         np.testing.assert_array_equal(mask.cpu().numpy(), mask_ref)
         np.testing.assert_allclose(dist.cpu().numpy(), dist_ref, rtol=1e-6)
     assert mask_ref[:200].mean() > 0.5 and mask_ref[200:].mean() < 0.05
+
+
+def test_nearest_two_level_search_on_degenerate_references():
+    """The two-level nearest search over references whose grids collapse to
+    one cell along some axes (a plane, a line, coincident points), with
+    queries on, near and far from them: equal to the oracle."""
+    import torch
+    rng = np.random.default_rng(93)
+    plane = np.c_[rng.uniform(-1, 1, (3000, 2)), np.zeros(3000)].astype(np.float32)
+    line = np.c_[np.linspace(0, 1, 1500), np.linspace(0, 2, 1500), np.zeros(1500)].astype(np.float32)
+    same = np.tile(np.array([[0.5, -0.25, 2.0]], np.float32), (64, 1))
+    for X in (plane, line, same):
+        Q = np.concatenate([X[rng.choice(len(X), 200)],
+                            (X[rng.choice(len(X), 200)] + rng.normal(0, 0.05, (200, 3))).astype(np.float32),
+                            rng.uniform(-3, 3, (200, 3)).astype(np.float32)])
+        idx_ref, key_ref = O.nearest(Q, X)
+        with Gpu(X, X, tune={scgr.SCGR_TUNE_KNN_GRID_MIN: 0}) as g:
+            idx = torch.empty(len(Q), dtype=torch.int32, device="cuda")
+            key = torch.empty(len(Q), dtype=torch.float32, device="cuda")
+            scgr.scgr_nearest(g.ctx, torch.from_numpy(Q).cuda(), idx, key)
+            check("nearest, degenerate reference: indices differing from the oracle",
+                  np.count_nonzero(idx.cpu().numpy() != idx_ref), 0)
+            np.testing.assert_array_equal(key.cpu().numpy(), key_ref)

@@ -397,3 +397,16 @@ def test_injected_allocation_failure_is_reported_and_recoverable():
     finally:
         scgr.scgr_debug_fail_allocations(0)
         scgr.scgr_destroy(ctx)
+
+
+@pytest.mark.parametrize("m", [2048, 2049])
+def test_pose_parity_at_the_fused_tail_limit(m):
+    """Templates of up to 2,048 padded slots combine and update the pose in
+    one block; 2,049 points take the two-launch path.  Both match the oracle
+    after 12 iterations."""
+    sc = synth.scale_case()
+    X = sc.X[synth.subsample(sc.X, 2500, 41)]
+    Y0 = sc.Y0[synth.subsample(sc.Y0, m, 42)]
+    ores = O.register(X, Y0, O.Params(p=2.0), iterations=12)
+    with Gpu(X, Y0, p=2.0) as g:
+        pose_check(g.run(12), ores, synth.bbox_diag(X), what=f"pose after 12 iterations, {m}-point template")
