@@ -410,3 +410,23 @@ def test_pose_parity_at_the_fused_tail_limit(m):
     ores = O.register(X, Y0, O.Params(p=2.0), iterations=12)
     with Gpu(X, Y0, p=2.0) as g:
         pose_check(g.run(12), ores, synth.bbox_diag(X), what=f"pose after 12 iterations, {m}-point template")
+
+
+def test_g_equals_s_at_full_size_and_over_iterations():
+    """The g = s weighting of Sec. IV as the benchmark times it: forces of the
+    1M x 1M workload at sampled rows (seeded curvatures on both sides, per-row
+    check included), and a whole 1,000-point registration of 30 iterations
+    against the oracle."""
+    case = synth.large_case()
+    rng = np.random.default_rng(19)
+    with Gpu(case.X, case.Y0, p=2.0, g_mode=0) as g:
+        aX = synthetic_curvatures(len(case.X), 21)
+        aY = synthetic_curvatures(len(case.Y0), 22)
+        g.set_curvature(0, aX)
+        g.set_curvature(1, aY)
+        rows = np.sort(rng.choice(len(case.Y0), size=32, replace=False))
+        force_check(g, case.X, case.Y0, aX, aY, O.sigma_auto(aX), 2.0, 0, rows, what=", 1M x 1M, 32 sampled rows")
+    tiny = synth.tiny()
+    ores = O.register(tiny.X, tiny.Y0, O.Params(p=2.0, g_mode=0), iterations=30)
+    with Gpu(tiny.X, tiny.Y0, p=2.0, g_mode=0) as g:
+        pose_check(g.run(30), ores, synth.bbox_diag(tiny.X), what="pose after 30 iterations, g = s")
