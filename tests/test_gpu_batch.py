@@ -212,3 +212,15 @@ def test_full_size_batch_in_the_benchmark_configuration():
         o = O.register_from_partials(pp.X, pp.Y0, prm, iters, slim, blocks, map_partials=pool.map)
     assert close(res[order[-1]], (o["R"], o["t"], o["s"]), synth.bbox_diag(pp.X),
                  f"full-size batch, largest pair ({len(pp.X):,} x {len(pp.Y0):,}) vs oracle")
+
+
+def test_batch_with_g_equals_s_matches_single_pair_runs():
+    """The batched form with the g = s weighting of Sec. IV (mixed shapes):
+    every pair against a one-pair-per-call run of the same parameters."""
+    pairs = make_pairs([900, 2100, 400, 3300], seed=43)
+    iters = 15
+    res, _ = run_batch(pairs, iters, tuning=((scgr.SCGR_TUNE_BATCH_P, 0),), p=2.0, g_mode=0)
+    for (X, Y), r in zip(pairs, res):
+        with Gpu(X, Y, p=2.0, g_mode=0) as g:
+            single = g.run(iters)
+        assert close(r, single, synth.bbox_diag(X), "batched vs one call per pair, g = s")

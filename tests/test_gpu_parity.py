@@ -430,3 +430,15 @@ def test_g_equals_s_at_full_size_and_over_iterations():
     ores = O.register(tiny.X, tiny.Y0, O.Params(p=2.0, g_mode=0), iterations=30)
     with Gpu(tiny.X, tiny.Y0, p=2.0, g_mode=0) as g:
         pose_check(g.run(30), ores, synth.bbox_diag(tiny.X), what="pose after 30 iterations, g = s")
+
+
+@pytest.mark.parametrize("p,g_mode", [(1.5, 1), (3.0, 0)])
+def test_pose_parity_general_p_and_moments_with_g_equals_s(p, g_mode):
+    """Whole registrations through the general-p weight (p = 1.5: the distance
+    factor folded into the exponent through lg2) and through the p = 3
+    moments path with the g = s weighting: 20 iterations against the oracle."""
+    case = synth.mild(n=900)
+    ores = O.register(case.X, case.Y0, O.Params(p=p, g_mode=g_mode), iterations=20)
+    with Gpu(case.X, case.Y0, p=p, g_mode=g_mode) as g:
+        pose_check(g.run(20), ores, synth.bbox_diag(case.X),
+                   what=f"pose after 20 iterations (p={p:g}, g mode {g_mode})")
