@@ -297,6 +297,9 @@ struct ForceTuning {
 
 ForcePlan plan_force(int64_t m, int64_t npad, double p, int num_sms, const ForceTuning& tune = ForceTuning());
 int64_t force_mpad(int64_t m, const ForcePlan& fp);
+// Record tiles a force block of this plan stages at a time (a split length
+// that is not a multiple of this computes a zero-weight padded tile).
+inline int force_stage_tiles(const ForcePlan& fp) { return fp.occ == 2 ? 2 : 1; }
 
 cudaError_t launch_force(Launch L, const ForcePlan& fp, const float4* Xr, const float2* XA,
                          int ntiles, const float4* Y0r, int mpad, const DevPose* pose,

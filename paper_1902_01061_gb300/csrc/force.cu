@@ -401,11 +401,45 @@ __global__ void __launch_bounds__(128, 3)
 
 static int force_blocks_per_sm(const ForcePlan& fp);
 
-// Work split: template points per thread by size, then the number of
-// reference splits S that fills whole waves of resident blocks.  All blocks
-// do (almost) the same work, so the last wave's fill decides the tail: pick
-// the smallest S in [S_lo, S_hi] whose grid fills its last wave to >= 99%
-// (else the best fill seen).
+// Duration, in tiles, of a force grid under greedy dispatch: blocks start in
+// split-major order (grid.x fastest), each on the earliest free of `slots`
+// resident block slots; blocks of the first splits - 1 splits take d1 tiles,
+// those of the last split d2 <= d1.
+static double split_makespan(int64_t iblocks, int64_t splits, double d1, double d2, int64_t slots) {
+  const int64_t n1 = (splits - 1) * iblocks;
+  const int64_t q = n1 / slots, r = n1 % slots;
+  double fin = (double)(r > 0 ? q + 1 : q) * d1;
+  // after the long blocks: slots - r slots free at q d1, r slots at (q + 1) d1
+  const int64_t na = slots - r, nb = r;
+  double ta = (double)q * d1, tb = (double)(q + 1) * d1;
+  int64_t left = iblocks;
+  while (left > 0) {
+    if (nb == 0 || ta <= tb) {
+      left -= left < na ? left : na;
+      fin = fin > ta + d2 ? fin : ta + d2;
+      ta += d2;
+    } else {
+      left -= left < nb ? left : nb;
+      fin = fin > tb + d2 ? fin : tb + d2;
+      tb += d2;
+    }
+  }
+  return fin;
+}
+
+// Work split: template points per thread by size, then the reference split
+// length L (tiles per block).  A block stages force_stage_tiles(fp) tiles at
+// a time, so L is a multiple of that (an odd L on a two-tile stage computes
+// a padded tile: 20% more time at 35k points, where L is 5).  Each candidate
+// L is scored by the makespan of its grid under greedy dispatch plus a
+// quarter of one block's duration: blocks on different SMs finish at
+// different times, so shorter blocks leave a shorter ragged tail (over split
+// lengths 2..25 on 20k-50k point problems the score's choice was within 1% of
+// the fastest length measured).  The lowest score wins, ties to fewer
+// splits.  At most max(16, twelve waves' worth) and 128 splits, and at least
+// two tiles per split unless that leaves the grid short of one wave (small
+// problems, where a block's sequential walk over its tiles is the launch's
+// latency): then down to one tile per split.
 ForcePlan plan_force(int64_t m, int64_t npad, double p, int num_sms, const ForceTuning& tune) {
   ForcePlan fp;
   fp.pmode = (p == 1.0) ? 1 : (p == 2.0) ? (tune.rsq == 1 ? 4 : 2) : (p == 3.0) ? 3 : 0;
@@ -435,35 +469,39 @@ ForcePlan plan_force(int64_t m, int64_t npad, double p, int num_sms, const Force
   fp.ex2poly = (fp.pmode == 2 && fp.occ == 2) ? (tune.ex2poly < fp.P ? tune.ex2poly : fp.P) : 0;
   const int64_t per_block = (int64_t)fp.tpb * fp.P;
   fp.iblocks = (int)((m + per_block - 1) / per_block);
-  const int ntiles = (int)(npad / FORCE_TJ);
+  const int64_t ntiles = npad / FORCE_TJ > 0 ? npad / FORCE_TJ : 1;
   const int64_t slots = (int64_t)num_sms * force_blocks_per_sm(fp);
-  // at least 8 waves when the reference range allows it, at most 64 splits,
-  // and at least 4 tiles per split - unless even that leaves the grid short
-  // of one wave (small problems, where a block's sequential walk over its
-  // tiles is the launch's latency): then down to one tile per split
-  int64_t S_lo = (8 * slots + fp.iblocks - 1) / fp.iblocks;
-  int64_t S_hi = ntiles / 4 > 0 ? ntiles / 4 : 1;
-  if ((int64_t)fp.iblocks * S_hi < slots) S_hi = ntiles;
-  if (S_hi > 64) S_hi = 64;
-  if (S_lo > S_hi) S_lo = S_hi;
-  if (S_lo < 1) S_lo = 1;
-  if (tune.splits > 0) S_lo = S_hi = tune.splits < ntiles ? tune.splits : ntiles;
-  int64_t best_S = S_lo;
-  double best_fill = -1.0;
-  for (int64_t S = S_lo; S <= S_hi; ++S) {
-    const int64_t tps = (ntiles + S - 1) / S;
-    const int64_t splits = (ntiles + tps - 1) / tps;
-    const int64_t total = fp.iblocks * splits;
-    const int64_t waves = (total + slots - 1) / slots;
-    const double fill = (double)total / (double)(waves * slots);
-    if (fill > best_fill + 1e-12) {
-      best_fill = fill;
-      best_S = S;
+  const int64_t sub = force_stage_tiles(fp);
+  auto up = [](int64_t a, int64_t b) { return (a + b - 1) / b; };
+  int64_t L = 0;
+  if (tune.splits > 0) {
+    // an explicit split count is taken as given (lengths not rounded)
+    L = up(ntiles, tune.splits < ntiles ? tune.splits : ntiles);
+  } else {
+    int64_t S_max = up(12 * slots, fp.iblocks);
+    if (S_max < 16) S_max = 16;
+    if (S_max > 128) S_max = 128;
+    const int64_t floor_len = (int64_t)fp.iblocks * up(ntiles, 2) < slots ? sub : (sub > 2 ? sub : 2);
+    int64_t L_min = up(ntiles, S_max) > floor_len ? up(ntiles, S_max) : floor_len;
+    L_min = up(L_min, sub) * sub;
+    double best = 0.0;
+    int64_t last = -1;
+    for (int64_t S = 1; S <= S_max; ++S) {
+      const int64_t len = up(up(ntiles, S), sub) * sub;
+      if (len < L_min || len == last) continue;
+      last = len;
+      const int64_t splits = up(ntiles, len);
+      const int64_t tail = up(ntiles - (splits - 1) * len, sub) * sub;
+      const double score = split_makespan(fp.iblocks, splits, (double)len, (double)tail, slots) + 0.25 * (double)len;
+      if (L == 0 || score < best - 1e-9) {
+        best = score;
+        L = len;
+      }
     }
-    if (fill >= 0.99) break;
+    if (L == 0) L = L_min;
   }
-  fp.tiles_per_split = (int)((ntiles + best_S - 1) / best_S);
-  fp.splits = (ntiles + fp.tiles_per_split - 1) / fp.tiles_per_split;
+  fp.tiles_per_split = (int)L;
+  fp.splits = (int)up(ntiles, L);
   return fp;
 }
 

@@ -48,26 +48,22 @@ __device__ __forceinline__ void point_force(const float4* __restrict__ pbase, si
                                             const float4 y0, float ay, const PointFrame& fr, float (&acc)[13],
                                             float4* __restrict__ f4out) {
   float Wh = 0.f, Wc = 0.f, Sh[3] = {0.f, 0.f, 0.f}, Sc[3] = {0.f, 0.f, 0.f};
-  // splits in order; four loads issued together
-  int s = 0;
-  for (; s + 4 <= S; s += 4) {
-    float4 pp[4];
+  // splits in order, eight loads in flight per step (small templates leave
+  // few threads per SM, so the pass over the splits is load-latency bound)
+  for (int s = 0; s < S; s += 8) {
+    float4 pp[8];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) pp[u] = pbase[(size_t)(s + u) * pstride + i];
+    for (int u = 0; u < 8; ++u)
+      if (s + u < S) pp[u] = pbase[(size_t)(s + u) * pstride + i];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      kahan_add(Wh, Wc, pp[u].x);
-      kahan_add(Sh[0], Sc[0], pp[u].y);
-      kahan_add(Sh[1], Sc[1], pp[u].z);
-      kahan_add(Sh[2], Sc[2], pp[u].w);
+    for (int u = 0; u < 8; ++u) {
+      if (s + u < S) {
+        kahan_add(Wh, Wc, pp[u].x);
+        kahan_add(Sh[0], Sc[0], pp[u].y);
+        kahan_add(Sh[1], Sc[1], pp[u].z);
+        kahan_add(Sh[2], Sc[2], pp[u].w);
+      }
     }
-  }
-  for (; s < S; ++s) {
-    const float4 pp = pbase[(size_t)s * pstride + i];
-    kahan_add(Wh, Wc, pp.x);
-    kahan_add(Sh[0], Sc[0], pp.y);
-    kahan_add(Sh[1], Sc[1], pp.z);
-    kahan_add(Sh[2], Sc[2], pp.w);
   }
   float y[3];
   template_point(y0, fr.A, fr.b, y[0], y[1], y[2]);
