@@ -915,27 +915,31 @@ cudaError_t launch_combine_moments(Launch L, const double* mom, int m, int mpad,
 }
 
 // ---- combine: splits -> per-point force -> per-block (F, W, T) -------------
-// A block covers 256 template slots with 64 threads of 4 points each.  Per
+// A block covers 256 template slots, PPT points per thread.  Per
 // point, the split partials are added with Kahan compensation and
 // f = aY (S - Y' W) is formed with an exact product (fma) and an exact sum,
 // so f is as accurate as float allows even when S and Y' W nearly cancel;
 // f (x) c and the other block terms are FP32 products of accurate factors.  A
-// thread's four points are added in FP32, and every sum across threads and
+// thread's points are added in FP32, and every sum across threads and
 // blocks is FP64 in a fixed order.  (FP64 arithmetic per point would make
 // this kernel FP64-bound: GB300 issues FP64 at a small fraction of FP32.)
-constexpr int CMB_TPB = 64;
-constexpr int CMB_PPT = 4;  // points per thread: CMB_TPB * CMB_PPT = 256 slots per block
+// PPT = 4 points per thread (64 threads) where the grid is large; PPT = 1
+// (256 threads) for small templates, where a thread's points are sequential
+// trips to memory and few threads run per SM.
+constexpr int CMB_SLOTS = 256;           // template slots per block
+constexpr int CMB_SMALL_BLOCKS = 1024;   // grids of fewer blocks take PPT = 1
 
 // BATCH = true: block b belongs to pair cpair[b]; its 256 template slots are
-// that pair's slots (b - cblk0) * 256 + threadIdx.x + 64 k, k < 4.
-template <bool BATCH>
-__global__ void __launch_bounds__(CMB_TPB, 8)
+// that pair's slots (b - cblk0) * 256 + threadIdx.x + (256 / PPT) k, k < PPT.
+template <bool BATCH, int PPT>
+__global__ void __launch_bounds__(CMB_SLOTS / PPT, 2 * PPT)
     combine_kernel(const float4* __restrict__ partial, int S, int mpad, int m,
                    const float4* __restrict__ Y0r, const double* __restrict__ aY64, int g_mode,
                    const DevPose* __restrict__ pose, float4* __restrict__ f4out,
                    double* __restrict__ blockpart, const int* __restrict__ cpair,
                    const BatchPair* __restrict__ pairs) {
-  __shared__ double sh[CMB_TPB / 32][16];
+  constexpr int TPB = CMB_SLOTS / PPT;
+  __shared__ double sh[TPB / 32][16];
   int i0, mm, SS;
   size_t pstride;
   const float4* pbase;
@@ -945,7 +949,7 @@ __global__ void __launch_bounds__(CMB_TPB, 8)
   if (BATCH) {
     const int p = cpair[blockIdx.x];
     const BatchPair& bp = pairs[p];
-    i0 = (blockIdx.x - bp.cblk0) * (CMB_TPB * CMB_PPT);
+    i0 = (blockIdx.x - bp.cblk0) * CMB_SLOTS;
     mm = (int)bp.m;
     SS = bp.chunks;
     pstride = (size_t)bp.mpad;
@@ -954,7 +958,7 @@ __global__ void __launch_bounds__(CMB_TPB, 8)
     abase = aY64 + bp.y0;
     ps = pose + p;
   } else {
-    i0 = blockIdx.x * (CMB_TPB * CMB_PPT);
+    i0 = blockIdx.x * CMB_SLOTS;
     mm = m;
     SS = S;
     pstride = (size_t)mpad;
@@ -968,8 +972,8 @@ __global__ void __launch_bounds__(CMB_TPB, 8)
 #pragma unroll
   for (int q = 0; q < 13; ++q) acc[q] = 0.f;
 #pragma unroll
-  for (int k = 0; k < CMB_PPT; ++k) {
-    const int i = i0 + k * CMB_TPB + threadIdx.x;
+  for (int k = 0; k < PPT; ++k) {
+    const int i = i0 + k * TPB + threadIdx.x;
     if (i < mm) point_force(pbase, pstride, SS, i, ybase[i], g_mode == 1 ? (float)abase[i] : 1.f, fr, acc, f4out);
   }
   double v[16];
@@ -983,19 +987,23 @@ __global__ void __launch_bounds__(CMB_TPB, 8)
   if (threadIdx.x < 13) {
     double t = sh[0][threadIdx.x];
 #pragma unroll
-    for (int w = 1; w < CMB_TPB / 32; ++w) t += sh[w][threadIdx.x];
+    for (int w = 1; w < TPB / 32; ++w) t += sh[w][threadIdx.x];
     blockpart[(size_t)blockIdx.x * 13 + threadIdx.x] = t;
   }
 }
 
-int combine_blocks(int64_t mpad) { return (int)((mpad + CMB_TPB * CMB_PPT - 1) / (CMB_TPB * CMB_PPT)); }
+int combine_blocks(int64_t mpad) { return (int)((mpad + CMB_SLOTS - 1) / CMB_SLOTS); }
 
 cudaError_t launch_combine(Launch L, const float4* partial, int S, int mpad, int m,
                            const float4* Y0r, const double* aY64, int g_mode, const DevPose* pose,
                            float4* f4out, double* blockpart) {
-  combine_kernel<false><<<combine_blocks(mpad), CMB_TPB, 0, L.stream>>>(partial, S, mpad, m, Y0r, aY64,
-                                                                        g_mode, pose, f4out, blockpart,
-                                                                        nullptr, nullptr);
+  const int nb = combine_blocks(mpad);
+  if (nb < CMB_SMALL_BLOCKS)
+    combine_kernel<false, 1><<<nb, CMB_SLOTS, 0, L.stream>>>(partial, S, mpad, m, Y0r, aY64, g_mode, pose, f4out,
+                                                             blockpart, nullptr, nullptr);
+  else
+    combine_kernel<false, 4><<<nb, CMB_SLOTS / 4, 0, L.stream>>>(partial, S, mpad, m, Y0r, aY64, g_mode, pose,
+                                                                 f4out, blockpart, nullptr, nullptr);
   if (L.counter) ++*L.counter;
   return cudaGetLastError();
 }
@@ -1004,8 +1012,8 @@ cudaError_t launch_combine_batch(Launch L, int nblocks, const int* cpair, const 
                                  const float4* partial, const float4* Y0r, const double* aY64, int g_mode,
                                  const DevPose* poses, double* blockpart) {
   if (nblocks <= 0) return cudaSuccess;
-  combine_kernel<true><<<nblocks, CMB_TPB, 0, L.stream>>>(partial, 0, 0, 0, Y0r, aY64, g_mode, poses, nullptr,
-                                                          blockpart, cpair, pairs);
+  combine_kernel<true, 4><<<nblocks, CMB_SLOTS / 4, 0, L.stream>>>(partial, 0, 0, 0, Y0r, aY64, g_mode, poses,
+                                                                   nullptr, blockpart, cpair, pairs);
   if (L.counter) ++*L.counter;
   return cudaGetLastError();
 }
