@@ -1,8 +1,9 @@
 // Pose update in float64 (Eq. 5.5, Eq. 6, Eq. 8, Eq. 9, Eq. 12): one block
-// reduces the per-block (F, W, T) partials in a fixed order, then one thread
+// reduces the per-block (F, W, T) partials in a fixed order, then one warp
 // forms the step, the Kabsch rotation (the polar factor of C^ by Newton's
-// iteration, or a one-sided Jacobi SVD in the reflection and near-singular
-// cases), the scale, the composed pose and its re-orthonormalisation.  The pose never
+// iteration in float32 with float64 corrections, else in float64, or a
+// one-sided Jacobi SVD in the reflection and near-singular cases), the
+// scale, the composed pose and its re-orthonormalisation.  The pose never
 // leaves the device, so a run of iterations is a plain sequence of launches.
 #include <cmath>
 
@@ -321,6 +322,132 @@ __device__ bool polar_newton_warp(double A, Lane3 L, double& Q) {
   return true;
 }
 
+// Polar factor of A (lane-owned) with most of the work in float32.  On
+// GB300 a float64 instruction costs about 65 cycles whatever the number of
+// active lanes, and consecutive ones do not overlap, so the float64 work is
+// kept to the few products that need it.  Every lane first runs the same
+// scaled Newton iteration on its own float copy X of the 3x3, then two
+// corrections against A itself bring the factor to float64 accuracy.  A
+// correction writes the current factor as Q = R (I + S), R orthogonal and
+// S = (Q^T Q - I) / 2 symmetric and small, forms B = Q^T A (float64), so
+// that R^T A = (I - S) B to first order, and takes the small rotation w that
+// makes R (I + [w]x)'s transpose times A symmetric: with H = (B + B^T) / 2
+// and k = axial of the skew part of (I - S) B doubled, the symmetric-H
+// identity [w]x H + H [w]x = [(tr(H) I - H) w]x gives (tr(H) I - H) w = k.
+// Then Q <- Q + X ([w]x - S).  Only Q^T Q, Q^T A, B - B^T and the final
+// sum are float64; the rest are small quantities whose float32 rounding is
+// second order.  Each correction squares the error (float32's ~1e-7, then
+// float64 rounding).  Returns false, and the caller takes polar_newton_warp,
+// for inputs out of float32 range, det <= 0, a Frobenius condition estimate
+// above 1e3, or a correction that does not shrink.
+__device__ bool polar_float_refined_warp(double A, Lane3 L, double& Q) {
+  const float fa = (float)A;
+  float x[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) x[k] = __shfl_sync(WFULL, fa, k);
+  float n2 = 0.f;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) n2 = fmaf(x[k], x[k], n2);
+  if (!(n2 > 0.f) || !isfinite(n2)) return false;
+  const float inv = rsqrtf(n2);
+#pragma unroll
+  for (int k = 0; k < 9; ++k) x[k] *= inv;
+  bool scale = true, done = false;
+  for (int it = 0; it < 20 && !done; ++it) {
+    float c[9];  // cofactors of X, then X^-T
+    c[0] = x[4] * x[8] - x[5] * x[7];
+    c[1] = x[5] * x[6] - x[3] * x[8];
+    c[2] = x[3] * x[7] - x[4] * x[6];
+    c[3] = x[2] * x[7] - x[1] * x[8];
+    c[4] = x[0] * x[8] - x[2] * x[6];
+    c[5] = x[1] * x[6] - x[0] * x[7];
+    c[6] = x[1] * x[5] - x[2] * x[4];
+    c[7] = x[2] * x[3] - x[0] * x[5];
+    c[8] = x[0] * x[4] - x[1] * x[3];
+    const float det = fmaf(x[2], c[2], fmaf(x[1], c[1], x[0] * c[0]));
+    if (!(det > 1e-20f) || !isfinite(det)) return false;
+    const float rd = __frcp_rn(det);
+    float nx = 0.f, ny = 0.f;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      c[k] *= rd;
+      nx = fmaf(x[k], x[k], nx);
+      ny = fmaf(c[k], c[k], ny);
+    }
+    if (it == 0 && !(nx * ny <= 1e6f)) return false;
+    const float g = scale ? sqrtf(sqrtf(__fdividef(ny, nx))) : 1.f;
+    const float a = 0.5f * g, b = __fdividef(0.5f, g);
+    float dd = 0.f, nn = 0.f;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      const float xn = fmaf(a, x[k], b * c[k]);
+      const float d = xn - x[k];
+      dd = fmaf(d, d, dd);
+      nn = fmaf(xn, xn, nn);
+      x[k] = xn;
+    }
+    done = dd <= 1e-10f * nn;
+    scale = dd > 1e-4f * nn;
+  }
+  if (!done) return false;
+  const int q = L.q;
+  float mine = x[0];
+#pragma unroll
+  for (int k = 1; k < 9; ++k) mine = (q == k) ? x[k] : mine;
+  double Qd = (double)mine;
+  // A scaled by a power of two near 1 / ||A|| (exact), so that the 3x3
+  // quantities below stay near unit size
+  int e2 = 0;
+  frexpf(sqrtf(n2), &e2);
+  const double As = A * __longlong_as_double((long long)(1023 - e2) << 52);
+  const double I = (L.r == L.c) ? 1.0 : 0.0;
+  for (int step = 0; step < 2; ++step) {
+    const double E = wmul_ta(Qd, Qd, L) - I;
+    const double B = wmul_ta(Qd, As, L);
+    const double K = B - wget(B, L.c * 3 + L.r);
+    const float ef = (float)E, bf = (float)B, kf = (float)K;
+    float sm[9], bm[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      sm[k] = 0.5f * __shfl_sync(WFULL, ef, k);
+      bm[k] = __shfl_sync(WFULL, bf, k);
+    }
+    const float k21 = __shfl_sync(WFULL, kf, 7), k02 = __shfl_sync(WFULL, kf, 2), k10 = __shfl_sync(WFULL, kf, 3);
+    // entries of S B for its skew part
+    auto sb = [&](int r, int c) { return fmaf(sm[r * 3 + 2], bm[6 + c], fmaf(sm[r * 3 + 1], bm[3 + c], sm[r * 3] * bm[c])); };
+    const float kp0 = k21 - (sb(2, 1) - sb(1, 2));
+    const float kp1 = k02 - (sb(0, 2) - sb(2, 0));
+    const float kp2 = k10 - (sb(1, 0) - sb(0, 1));
+    // M = tr(H) I - H, H = (B + B^T) / 2
+    const float tr = bm[0] + bm[4] + bm[8];
+    const float m00 = tr - bm[0], m11 = tr - bm[4], m22 = tr - bm[8];
+    const float m01 = -0.5f * (bm[1] + bm[3]), m02 = -0.5f * (bm[2] + bm[6]), m12 = -0.5f * (bm[5] + bm[7]);
+    // adj(M) (symmetric) and det M
+    const float a00 = m11 * m22 - m12 * m12, a01 = m02 * m12 - m01 * m22, a02 = m01 * m12 - m02 * m11;
+    const float a11 = m00 * m22 - m02 * m02, a12 = m01 * m02 - m00 * m12, a22 = m00 * m11 - m01 * m01;
+    const float detM = fmaf(m02, a02, fmaf(m01, a01, m00 * a00));
+    if (!(detM > 0.f) || !isfinite(detM)) return false;
+    const float rdm = __frcp_rn(detM);
+    const float w0 = rdm * fmaf(a02, kp2, fmaf(a01, kp1, a00 * kp0));
+    const float w1 = rdm * fmaf(a12, kp2, fmaf(a11, kp1, a01 * kp0));
+    const float w2 = rdm * fmaf(a22, kp2, fmaf(a12, kp1, a02 * kp0));
+    const float wn = fmaf(w2, w2, fmaf(w1, w1, w0 * w0));
+    if (!(wn <= (step == 0 ? 1e-8f : 1e-20f))) return false;
+    // D = [w]x - S, and this lane's entry of X D
+    const float d[9] = {-sm[0],      -w2 - sm[1], w1 - sm[2],  w2 - sm[3], -sm[4],
+                        -w0 - sm[5], -w1 - sm[6], w0 - sm[7], -sm[8]};
+    float p = 0.f;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      const float xd = fmaf(x[(k / 3) * 3 + 2], d[6 + k % 3], fmaf(x[(k / 3) * 3 + 1], d[3 + k % 3], x[(k / 3) * 3] * d[k % 3]));
+      p = (q == k) ? xd : p;
+    }
+    Qd += (double)p;
+  }
+  Q = Qd;
+  return true;
+}
+
 // Warp form of reorthonormalise: two Newton-Schulz steps; false (the caller
 // takes the SVD route) when R^T R is further than 1e-6 from I.
 __device__ bool reorth_warp(double R, Lane3 L, double& out) {
@@ -384,10 +511,11 @@ __device__ void finalize_update(const double (&v)[13], DevPose* ps, const DevSta
   }
   // Eq. 6: C^ = U S V^T, dd = sign det(V U^T), R_inc = V diag(1, 1, dd) U^T.
   // For det C^ > 0 (dd = 1) that is Q^T, Q the orthogonal polar factor of C^
-  // (C^ = (U V^T)(V S V^T)), taken by Newton's iteration; the SVD handles
-  // det C^ <= 0, near-singular C^ and the degenerate case.
+  // (C^ = (U V^T)(V S V^T)), taken by Newton's iteration (in float32 with
+  // float64 corrections, else all in float64); the SVD handles det C^ <= 0,
+  // near-singular C^ and the degenerate case.
   double Rinc, Qp;
-  if (polar_newton_warp(Ch, L, Qp)) {
+  if (polar_float_refined_warp(Ch, L, Qp) || polar_newton_warp(Ch, L, Qp)) {
     Rinc = wget(Qp, L.c * 3 + L.r);
   } else {
     double* scr = &sh[0][0];

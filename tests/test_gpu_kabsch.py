@@ -1,8 +1,12 @@
 """One pose update on the GPU from given totals (scgr_step_apply) against the
 oracle's update from the same totals (Eq. 5.5, Eq. 6, Eq. 8, Eq. 9).  The
 totals are chosen so that C^ = S_yy + kappa T takes each branch of the
-Kabsch step: det C^ > 0 (the polar factor by Newton's iteration), det C^ < 0
-(the reflection fix of Eq. 6 through the SVD), and a nearly rank-2 C^."""
+Kabsch step: det C^ > 0 with a moderate condition number (the polar factor
+by Newton's iteration in float32 with two float64 corrections, including a
+170 degree rotation), a condition number near 1e4 (beyond the float32
+iteration's limit of about 1e3: Newton's iteration in float64), det C^ < 0
+(the reflection fix of Eq. 6 through the SVD), and a nearly rank-2 C^
+(beyond the float64 iteration's limit: the SVD)."""
 import numpy as np
 import pytest
 
@@ -35,10 +39,16 @@ def chat_target(Syy, kind):
         return rotation([1.0, 2.0, -0.5], 20.0) @ Syy @ np.diag([1.0, 1.0, -1.0])
     if kind == "rank2":            # smallest singular value 1e-9 of the largest
         return rotation([0.0, 1.0, 1.0], 50.0) @ U @ np.diag([S[0], S[1], 1e-9 * S[0]]) @ Vt
+    if kind == "halfturn":         # a polar factor far from the identity
+        return rotation([-0.2, 0.7, 0.4], 170.0) @ Syy
+    if kind == "cond3e2":          # within the float32 iteration's range
+        return rotation([0.6, 0.1, -0.3], 25.0) @ U @ np.diag([S[0], 0.4 * S[0], S[0] / 300.0]) @ Vt
+    if kind == "cond1e4":          # beyond it: the float64 iteration
+        return rotation([0.6, 0.1, -0.3], 25.0) @ U @ np.diag([S[0], 0.4 * S[0], 1e-4 * S[0]]) @ Vt
     raise ValueError(kind)
 
 
-@pytest.mark.parametrize("kind", ["identity", "rotated", "reflected", "rank2"])
+@pytest.mark.parametrize("kind", ["identity", "rotated", "halfturn", "cond3e2", "cond1e4", "reflected", "rank2"])
 def test_step_from_totals_matches_oracle(kind):
     case = synth.mild(n=700)
     Y = case.Y0.astype(np.float64)
