@@ -307,7 +307,7 @@ scgr_status scgr_forces(scgr_ctx* c, float* f4_dev) {
   if (fs != SCGR_OK) return fs;
   const int mloc = (int)(c->rows >= 0 ? c->rows : c->m);
   SCGR_CK(c, launch_combine(c->L(), (const float4*)c->partial.p, c->fp.splits, (int)c->mpad, mloc,
-                            (const float4*)c->Y0r.p, (const double*)c->aY64.p + c->row0, c->prm.g_mode, c->pose,
+                            (const float4*)c->Y0r.p, (const float*)c->aY32.p + c->row0, c->prm.g_mode, c->pose,
                             (float4*)f4_dev, (double*)c->blockpart.p));
   return SCGR_OK;
 }

@@ -148,7 +148,7 @@ scgr_status scgr_batch_run(scgr_ctx* c, int npairs, const int64_t* ref_off, cons
                                     (const DevPose*)c->bposes.p, c->qexp, (float4*)c->bpartial.p, CT, pgrid,
                                     (int*)c->bnext.p));
       SCGR_CK(c, launch_combine_batch(LL, cb, (const int*)c->bcpair.p, dpairs, (const float4*)c->bpartial.p,
-                                      (const float4*)c->bY0r.p, (const double*)c->baY64.p, c->prm.g_mode,
+                                      (const float4*)c->bY0r.p, (const float*)c->baY32.p, c->prm.g_mode,
                                       (const DevPose*)c->bposes.p, (double*)c->bblockpart.p));
       SCGR_CK(c, launch_finalize_multi(LL, (const double*)c->bblockpart.p, dpairs, npairs, (DevPose*)c->bposes.p,
                                        (const DevStats*)c->bstats.p, sp, c->errword));

@@ -39,7 +39,7 @@ scgr_status scgr_potential(scgr_ctx* c, const double pose7[7], double* U_out, do
   SCGR_CK(c, launch_force(L, fu, (const float4*)c->Xr.p, (const float2*)c->XA.p, ntiles, (const float4*)c->Y0r.p,
                           (int)c->mpad, c->pose_eval, (float)(0.5 * eU), (float4*)c->partial.p));
   SCGR_CK(c, launch_combine(L, (const float4*)c->partial.p, fu.splits, (int)c->mpad, (int)c->m,
-                            (const float4*)c->Y0r.p, (const double*)c->aY64.p, c->prm.g_mode, c->pose_eval,
+                            (const float4*)c->Y0r.p, (const float*)c->aY32.p, c->prm.g_mode, c->pose_eval,
                             nullptr, (double*)c->blockpart.p));
   SCGR_CK(c, launch_column_sum13(L, (const double*)c->blockpart.p, nb, c->aux));
   if (grad_pose7 || grad_xyz_dev) {

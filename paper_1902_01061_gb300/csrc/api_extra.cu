@@ -80,7 +80,7 @@ scgr_status scgr_step_partials(scgr_ctx* c, double out13[13]) {
   scgr_status fs = force_launch(c);
   if (fs != SCGR_OK) return fs;
   SCGR_CK(c, launch_combine(c->L(), (const float4*)c->partial.p, c->fp.splits, (int)c->mpad, mloc,
-                            (const float4*)c->Y0r.p, (const double*)c->aY64.p + c->row0, c->prm.g_mode, c->pose,
+                            (const float4*)c->Y0r.p, (const float*)c->aY32.p + c->row0, c->prm.g_mode, c->pose,
                             nullptr, (double*)c->blockpart.p));
   SCGR_CK(c, launch_column_sum13(c->L(), (const double*)c->blockpart.p, combine_blocks(c->mpad), c->aux));
   SCGR_CK(c, cudaMemcpyAsync(out13, c->aux, 13 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
@@ -116,7 +116,7 @@ scgr_status scgr_step_partials_dev(scgr_ctx* c, double* out13_dev) {
   scgr_status fs = force_launch(c);
   if (fs != SCGR_OK) return fs;
   SCGR_CK(c, launch_combine(c->L(), (const float4*)c->partial.p, c->fp.splits, (int)c->mpad, mloc,
-                            (const float4*)c->Y0r.p, (const double*)c->aY64.p + c->row0, c->prm.g_mode, c->pose,
+                            (const float4*)c->Y0r.p, (const float*)c->aY32.p + c->row0, c->prm.g_mode, c->pose,
                             nullptr, (double*)c->blockpart.p));
   SCGR_CK(c, launch_column_sum13(c->L(), (const double*)c->blockpart.p, combine_blocks(c->mpad), out13_dev));
   return SCGR_OK;

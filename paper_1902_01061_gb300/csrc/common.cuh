@@ -32,11 +32,21 @@ struct DevPose {
   double ybs[3];   // template mean minus reference mean at this pose
   float A[9];      // float32 map used by the force kernel: Y' = Y0 A + b
   float b[3];      //   with A = s R and b = t - xbar (frame centred on xbar)
+  float ych[3];    // ybs as a float pair ych + ycl, read by the per-point
+  float ycl[3];    //   combine kernels (set together with ybs by set_ybs)
   int it;          // next iteration index of Eq. 12
   int E;           // Eq. 12 horizon
   int degenerate;  // iterations with a rank < 2 cross-covariance
   int pad;
 };
+
+// ybs[c] = v and its float pair (ych + ycl = v to about 2^-48 relative).
+__device__ __forceinline__ void set_ybs(DevPose* ps, int c, double v) {
+  ps->ybs[c] = v;
+  const float h = (float)v;
+  ps->ych[c] = h;
+  ps->ycl[c] = (float)(v - (double)h);
+}
 
 // Cloud statistics of the scale model (Sec. III-B) and sigma of Eq. 3.
 struct DevStats {
@@ -306,12 +316,12 @@ cudaError_t launch_force(Launch L, const ForcePlan& fp, const float4* Xr, const 
                          float qexp, float4* partial);
 int combine_blocks(int64_t mpad);
 cudaError_t launch_combine(Launch L, const float4* partial, int S, int mpad, int m,
-                           const float4* Y0r, const double* aY64, int g_mode,
+                           const float4* Y0r, const float* aY32, int g_mode,
                            const DevPose* pose, float4* f4out, double* blockpart);
 cudaError_t launch_pose_init(Launch L, DevPose* pose, const DevStats* stats, int E);
 constexpr int FUSED_MAX_SLOTS = 2048;  // templates up to this many padded slots: combine_finalize_kernel
 cudaError_t launch_combine_finalize(Launch L, const float4* partial, int S, int mpad, int m, const float4* Y0r,
-                                    const double* aY64, int g_mode, DevPose* pose, const DevStats* stats,
+                                    const float* aY32, int g_mode, DevPose* pose, const DevStats* stats,
                                     StepParams sp, int* err);
 cudaError_t launch_finalize(Launch L, const double* blockpart, int nblocks, DevPose* pose,
                             const DevStats* stats, StepParams sp, int* err);
@@ -333,7 +343,7 @@ cudaError_t force_batch_slots(int pmode, int P, int* slots);
 int batch_block_threads(int P);
 bool batch_pair_shape4(int64_t m);
 cudaError_t launch_combine_batch(Launch L, int nblocks, const int* cpair, const BatchPair* pairs,
-                                 const float4* partial, const float4* Y0r, const double* aY64, int g_mode,
+                                 const float4* partial, const float4* Y0r, const float* aY32, int g_mode,
                                  const DevPose* poses, double* blockpart);
 cudaError_t launch_finalize_multi(Launch L, const double* blockpart, const BatchPair* pairs, int npairs,
                                   DevPose* poses, const DevStats* stats, StepParams sp, int* err);

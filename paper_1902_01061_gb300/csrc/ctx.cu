@@ -322,12 +322,12 @@ scgr_status enqueue_iterations(scgr_ctx* c, int iters) {
     if (c->mpad <= FUSED_MAX_SLOTS) {
       // small templates: combine and finalize in one block (one launch less per iteration)
       SCGR_CK(c, launch_combine_finalize(c->L(), (const float4*)c->partial.p, c->fp.splits, (int)c->mpad, (int)c->m,
-                                         (const float4*)c->Y0r.p, (const double*)c->aY64.p, c->prm.g_mode, c->pose,
+                                         (const float4*)c->Y0r.p, (const float*)c->aY32.p, c->prm.g_mode, c->pose,
                                          c->stats, sp, c->errword));
       continue;
     }
     SCGR_CK(c, launch_combine(c->L(), (const float4*)c->partial.p, c->fp.splits, (int)c->mpad, (int)c->m,
-                              (const float4*)c->Y0r.p, (const double*)c->aY64.p, c->prm.g_mode, c->pose,
+                              (const float4*)c->Y0r.p, (const float*)c->aY32.p, c->prm.g_mode, c->pose,
                               nullptr, (double*)c->blockpart.p));
     SCGR_CK(c, launch_finalize(c->L(), (const double*)c->blockpart.p, nb, c->pose, c->stats, sp, c->errword));
   }

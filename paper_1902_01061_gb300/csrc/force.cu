@@ -934,7 +934,7 @@ constexpr int CMB_SMALL_BLOCKS = 1024;   // grids of fewer blocks take PPT = 1
 template <bool BATCH, int PPT>
 __global__ void __launch_bounds__(CMB_SLOTS / PPT, 2 * PPT)
     combine_kernel(const float4* __restrict__ partial, int S, int mpad, int m,
-                   const float4* __restrict__ Y0r, const double* __restrict__ aY64, int g_mode,
+                   const float4* __restrict__ Y0r, const float* __restrict__ aY32, int g_mode,
                    const DevPose* __restrict__ pose, float4* __restrict__ f4out,
                    double* __restrict__ blockpart, const int* __restrict__ cpair,
                    const BatchPair* __restrict__ pairs) {
@@ -944,7 +944,7 @@ __global__ void __launch_bounds__(CMB_SLOTS / PPT, 2 * PPT)
   size_t pstride;
   const float4* pbase;
   const float4* ybase;
-  const double* abase;
+  const float* abase;
   const DevPose* ps;
   if (BATCH) {
     const int p = cpair[blockIdx.x];
@@ -955,7 +955,7 @@ __global__ void __launch_bounds__(CMB_SLOTS / PPT, 2 * PPT)
     pstride = (size_t)bp.mpad;
     pbase = partial + bp.pbase;
     ybase = Y0r + bp.ybase;
-    abase = aY64 + bp.y0;
+    abase = aY32 + bp.y0;
     ps = pose + p;
   } else {
     i0 = blockIdx.x * CMB_SLOTS;
@@ -964,7 +964,7 @@ __global__ void __launch_bounds__(CMB_SLOTS / PPT, 2 * PPT)
     pstride = (size_t)mpad;
     pbase = partial;
     ybase = Y0r;
-    abase = aY64;
+    abase = aY32;
     ps = pose;
   }
   const PointFrame fr(ps);
@@ -974,7 +974,7 @@ __global__ void __launch_bounds__(CMB_SLOTS / PPT, 2 * PPT)
 #pragma unroll
   for (int k = 0; k < PPT; ++k) {
     const int i = i0 + k * TPB + threadIdx.x;
-    if (i < mm) point_force(pbase, pstride, SS, i, ybase[i], g_mode == 1 ? (float)abase[i] : 1.f, fr, acc, f4out);
+    if (i < mm) point_force(pbase, pstride, SS, i, ybase[i], g_mode == 1 ? abase[i] : 1.f, fr, acc, f4out);
   }
   double v[16];
 #pragma unroll
@@ -995,24 +995,24 @@ __global__ void __launch_bounds__(CMB_SLOTS / PPT, 2 * PPT)
 int combine_blocks(int64_t mpad) { return (int)((mpad + CMB_SLOTS - 1) / CMB_SLOTS); }
 
 cudaError_t launch_combine(Launch L, const float4* partial, int S, int mpad, int m,
-                           const float4* Y0r, const double* aY64, int g_mode, const DevPose* pose,
+                           const float4* Y0r, const float* aY32, int g_mode, const DevPose* pose,
                            float4* f4out, double* blockpart) {
   const int nb = combine_blocks(mpad);
   if (nb < CMB_SMALL_BLOCKS)
-    combine_kernel<false, 1><<<nb, CMB_SLOTS, 0, L.stream>>>(partial, S, mpad, m, Y0r, aY64, g_mode, pose, f4out,
+    combine_kernel<false, 1><<<nb, CMB_SLOTS, 0, L.stream>>>(partial, S, mpad, m, Y0r, aY32, g_mode, pose, f4out,
                                                              blockpart, nullptr, nullptr);
   else
-    combine_kernel<false, 4><<<nb, CMB_SLOTS / 4, 0, L.stream>>>(partial, S, mpad, m, Y0r, aY64, g_mode, pose,
+    combine_kernel<false, 4><<<nb, CMB_SLOTS / 4, 0, L.stream>>>(partial, S, mpad, m, Y0r, aY32, g_mode, pose,
                                                                  f4out, blockpart, nullptr, nullptr);
   if (L.counter) ++*L.counter;
   return cudaGetLastError();
 }
 
 cudaError_t launch_combine_batch(Launch L, int nblocks, const int* cpair, const BatchPair* pairs,
-                                 const float4* partial, const float4* Y0r, const double* aY64, int g_mode,
+                                 const float4* partial, const float4* Y0r, const float* aY32, int g_mode,
                                  const DevPose* poses, double* blockpart) {
   if (nblocks <= 0) return cudaSuccess;
-  combine_kernel<true, 4><<<nblocks, CMB_SLOTS / 4, 0, L.stream>>>(partial, 0, 0, 0, Y0r, aY64, g_mode, poses,
+  combine_kernel<true, 4><<<nblocks, CMB_SLOTS / 4, 0, L.stream>>>(partial, 0, 0, 0, Y0r, aY32, g_mode, poses,
                                                                    nullptr, blockpart, cpair, pairs);
   if (L.counter) ++*L.counter;
   return cudaGetLastError();

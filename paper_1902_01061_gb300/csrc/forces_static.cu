@@ -141,7 +141,7 @@ extern "C" scgr_status scgr_forces_static(const float* x_dev, int64_t n, const f
   if (e == cudaSuccess) e = launch_pose_init(L, pose, stats, 1);
   if (e == cudaSuccess)
     e = launch_force(L, fp, Xr, XA, ntiles, Y0r, (int)mpad, pose, (float)((p - 1.0) * 0.5), partial);
-  if (e == cudaSuccess) e = launch_combine(L, partial, fp.splits, (int)mpad, (int)m, Y0r, ay_dev, g_mode, pose, reinterpret_cast<float4*>(f4_dev), blockpart);
+  if (e == cudaSuccess) e = launch_combine(L, partial, fp.splits, (int)mpad, (int)m, Y0r, a32y, g_mode, pose, reinterpret_cast<float4*>(f4_dev), blockpart);
   int herr = 0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);

@@ -23,7 +23,8 @@ __device__ __forceinline__ void kahan_add(float& s, float& c, float x) {
 }
 
 // The pose's float32 map (A, b) and the template mean in the centred frame
-// as a float pair (ch + cl).
+// as a float pair (ch + cl), all stored with the pose (no float64 work per
+// thread).
 struct PointFrame {
   float A[9], b[3], ch[3], cl[3];
   __device__ __forceinline__ explicit PointFrame(const DevPose* ps) {
@@ -32,9 +33,8 @@ struct PointFrame {
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
       b[q] = ps->b[q];
-      const double yb = ps->ybs[q];
-      ch[q] = (float)yb;
-      cl[q] = (float)(yb - (double)ch[q]);
+      ch[q] = ps->ych[q];
+      cl[q] = ps->ycl[q];
     }
   }
 };

@@ -101,12 +101,6 @@ __device__ __forceinline__ double det3(const double* M) {
          M[2] * (M[3] * M[7] - M[4] * M[6]);
 }
 
-// Z = X Y (3x3 row-major)
-__device__ __forceinline__ void mul3(const double* X, const double* Y, double* Z) {
-  for (int r = 0; r < 3; ++r)
-    for (int c = 0; c < 3; ++c) Z[r * 3 + c] = X[r * 3] * Y[c] + X[r * 3 + 1] * Y[3 + c] + X[r * 3 + 2] * Y[6 + c];
-}
-
 // Nearest orthogonal matrix U V^T of R = U S V^T.
 __device__ void polar3(const double* R, double* out) {
   double U[9], S[3], V[9];
@@ -116,86 +110,6 @@ __device__ void polar3(const double* R, double* out) {
       out[r * 3 + c] = U[r * 3] * V[c * 3] + U[r * 3 + 1] * V[c * 3 + 1] + U[r * 3 + 2] * V[c * 3 + 2];
 }
 
-// Orthogonal polar factor Q of A (A = Q H, H symmetric positive definite)
-// for det A > 0 by Newton's iteration X <- (g X + X^-T / g) / 2 with
-// Frobenius-norm scaling g = (|X^-1| / |X|)^(1/2) while far from the limit
-// (Higham, "Computing the polar decomposition -- with applications", 1986).
-// X^-T is the cofactor matrix over the determinant.  Each step is a short
-// chain of FP64 operations, where a Jacobi SVD needs several square roots and
-// divisions per rotation; on GB300, whose FP64 unit is narrow, that chain
-// length is what one finalize thread waits on.  Returns false (the caller
-// then takes the SVD) when det A <= 0, when |A|_F |A^-1|_F > 1e6, or when the
-// iteration has not settled in 40 steps.
-__device__ bool polar_newton(const double* A, double* Q) {
-  double X[9];
-  for (int q = 0; q < 9; ++q) X[q] = A[q];
-  bool scale = true, settled = false;
-  for (int it = 0; it < 40; ++it) {
-    double C[9];
-    C[0] = X[4] * X[8] - X[5] * X[7];
-    C[1] = X[5] * X[6] - X[3] * X[8];
-    C[2] = X[3] * X[7] - X[4] * X[6];
-    C[3] = X[2] * X[7] - X[1] * X[8];
-    C[4] = X[0] * X[8] - X[2] * X[6];
-    C[5] = X[1] * X[6] - X[0] * X[7];
-    C[6] = X[1] * X[5] - X[2] * X[4];
-    C[7] = X[2] * X[3] - X[0] * X[5];
-    C[8] = X[0] * X[4] - X[1] * X[3];
-    const double det = X[0] * C[0] + X[1] * C[1] + X[2] * C[2];
-    if (!(det > 0.0) || !isfinite(det)) return false;
-    const double id = 1.0 / det;
-    double nx = 0.0, ny = 0.0;
-    for (int q = 0; q < 9; ++q) {
-      C[q] *= id;  // now X^-T
-      nx += X[q] * X[q];
-      ny += C[q] * C[q];
-    }
-    if (it == 0 && !(nx * ny <= 1e12)) return false;
-    const double g = scale ? sqrt(sqrt(ny / nx)) : 1.0;
-    const double ig = 1.0 / g;
-    double diff = 0.0, nn = 0.0;
-    for (int q = 0; q < 9; ++q) {
-      const double xn = 0.5 * (g * X[q] + ig * C[q]);
-      diff += (xn - X[q]) * (xn - X[q]);
-      nn += xn * xn;
-      X[q] = xn;
-    }
-    if (settled) break;                   // one plain step after the change fell below 1e-9
-    if (diff <= 1e-18 * nn) settled = true;
-    scale = diff > 1e-4 * nn;
-    if (it == 39) return false;
-  }
-  for (int q = 0; q < 9; ++q) Q[q] = X[q];
-  return true;
-}
-
-// Re-orthonormalise a rotation that is orthogonal to rounding error:
-// Newton-Schulz steps R <- R (3 I - R^T R) / 2, quadratically convergent to
-// the orthogonal polar factor; the SVD route when R is further off.
-__device__ void reorthonormalise(const double* Rin, double* out) {
-  double R[9];
-  for (int q = 0; q < 9; ++q) R[q] = Rin[q];
-  for (int step = 0; step < 2; ++step) {
-    double M[9];
-    double dev = 0.0;
-    for (int a = 0; a < 3; ++a)
-      for (int b = 0; b < 3; ++b) {
-        const double g = R[a] * R[b] + R[3 + a] * R[3 + b] + R[6 + a] * R[6 + b];  // (R^T R)_ab
-        const double e = g - (a == b ? 1.0 : 0.0);
-        dev = fmax(dev, fabs(e));
-        M[a * 3 + b] = (a == b ? 1.0 : 0.0) - 0.5 * e;
-      }
-    if (step == 0 && !(dev <= 1e-6)) {
-      polar3(Rin, out);
-      return;
-    }
-    double Rn[9];
-    mul3(R, M, Rn);
-    for (int q = 0; q < 9; ++q) R[q] = Rn[q];
-  }
-  for (int q = 0; q < 9; ++q) out[q] = R[q];
-}
-
 // Derived float32 map and template mean for the current pose.
 __device__ void refresh_pose(DevPose* ps, const DevStats* st) {
   for (int q = 0; q < 9; ++q) ps->A[q] = (float)(ps->s * ps->R[q]);
@@ -203,7 +117,7 @@ __device__ void refresh_pose(DevPose* ps, const DevStats* st) {
     ps->b[c] = (float)(ps->t[c] - st->xbar[c]);
     const double yb = ps->s * (st->ybar0[0] * ps->R[c] + st->ybar0[1] * ps->R[3 + c] +
                                st->ybar0[2] * ps->R[6 + c]) + ps->t[c];
-    ps->ybs[c] = yb - st->xbar[c];
+    set_ybs(ps, c, yb - st->xbar[c]);
   }
 }
 
@@ -286,12 +200,19 @@ __device__ __forceinline__ double wrcp(double x) {
   return fma(r, fma(-x, r, 1.0), r);
 }
 
-// Warp form of polar_newton (same iteration and exits): Q's entry in each
-// lane.  The input is first scaled to unit Frobenius norm, which leaves the
-// polar factor unchanged and keeps the FP32 norms below in range.  The
-// scaling factor g and the stop test use FP32 sums: any positive weights
-// (a X + b X^-T) / 2 keep the polar factor, so they only steer convergence;
-// the last steps use a = b = 1 exactly.
+// Orthogonal polar factor Q of A (A = Q H, H symmetric positive definite)
+// for det A > 0 by Newton's iteration X <- (g X + X^-T / g) / 2 with
+// Frobenius-norm scaling g = (|X^-1| / |X|)^(1/2) while far from the limit
+// (Higham, "Computing the polar decomposition -- with applications", 1986),
+// in float64 with the 3x3 spread over the warp: Q's entry in each lane.
+// X^-T is the cofactor matrix over the determinant.  The input is first
+// scaled to unit Frobenius norm, which leaves the polar factor unchanged and
+// keeps the FP32 norms below in range.  The scaling factor g and the stop
+// test use FP32 sums: any positive weights (a X + b X^-T) / 2 keep the polar
+// factor, so they only steer convergence; the last steps use a = b = 1
+// exactly.  Returns false (the caller then takes the SVD) when det A <= 0,
+// when |A|_F |A^-1|_F > 1e6, or when the iteration has not settled in 40
+// steps.
 __device__ bool polar_newton_warp(double A, Lane3 L, double& Q) {
   const double n2 = wsum9d(A * A);
   if (!(n2 > 0.0) || !isfinite(n2)) return false;
@@ -448,16 +369,16 @@ __device__ bool polar_float_refined_warp(double A, Lane3 L, double& Q) {
   return true;
 }
 
-// Warp form of reorthonormalise: two Newton-Schulz steps; false (the caller
-// takes the SVD route) when R^T R is further than 1e-6 from I.
+// Warp form of reorthonormalise for the product of the pose's rotation and
+// the increment, both orthogonal to float64 rounding: one Newton-Schulz step
+// brings R^T R - I back to rounding (a second changes nothing above it);
+// false (the caller takes the SVD route) when R^T R is further than 1e-6
+// from I.
 __device__ bool reorth_warp(double R, Lane3 L, double& out) {
   const double I = (L.r == L.c) ? 1.0 : 0.0;
-  for (int step = 0; step < 2; ++step) {
-    const double e = wmul_ta(R, R, L) - I;
-    if (step == 0 && !(wmax9(fabsf((float)e)) <= 1e-6f)) return false;
-    R = wmul(R, fma(-0.5, e, I), L);
-  }
-  out = R;
+  const double e = wmul_ta(R, R, L) - I;
+  if (!(wmax9(fabsf((float)e)) <= 1e-6f)) return false;
+  out = wmul(R, fma(-0.5, e, I), L);
   return true;
 }
 
@@ -479,25 +400,30 @@ __device__ void finalize_update(const double (&v)[13], DevPose* ps, const DevSta
   const double Tq = v[4 + L.q];  // T[a][b] = sum_i f_i[a] (Y_i - ybar)[b]
   const int it = ps->it;
   const double E = (double)ps->E;
-  // Eq. 12, 0-based iteration index
-  const double G = 0.1 * sp.G1 + 0.9 * sp.G1 / (1.0 + exp(-((double)it - E / 2.0)));
-  double kappa;
+  // Eq. 12, 0-based iteration index: G / G1 = 0.1 + 0.9 / (1 + e), written
+  // over one division (each float64 division is a chain of about ten
+  // float64 instructions, about 65 cycles each on GB300)
+  const double e1 = 1.0 + exp(-((double)it - E / 2.0));
+  const double gnum = fma(0.1, e1, 0.9);  // (G / G1) (1 + e)
+  double kappa, dq;                       // dc = dq v_c
   bool bad = false;
   if (sp.step_mode == 0) {
+    // kappa = eta0 (G / G1) M / W, and Eq. 5.5's d = kappa v / M needs no M
     if (!(W > 0.0) || !isfinite(W)) bad = true;
-    kappa = bad ? 0.0 : sp.eta0 * (G / sp.G1) * (double)sp.M / W;
+    dq = bad ? 0.0 : sp.eta0 * gnum / (e1 * W);
+    kappa = dq * (double)sp.M;
   } else {
-    kappa = G * sp.time * sp.time;
+    kappa = sp.G1 * gnum / e1 * sp.time * sp.time;
+    dq = kappa / (double)sp.M;
   }
   const double s = ps->s;
   const double Rq = ps->R[L.q];
-  // template mean at this pose (every lane, all three components)
-  double yb[3], tt[3];
-  for (int c = 0; c < 3; ++c) {
-    tt[c] = ps->t[c];
-    yb[c] = fma(s, fma(st->ybar0[2], ps->R[6 + c], fma(st->ybar0[1], ps->R[3 + c], st->ybar0[0] * ps->R[c])), tt[c]);
-  }
-  const double dc = kappa * v[L.c] / (double)sp.M;  // Eq. 5.5, unit masses, v = 0 (component c)
+  // template mean at this pose, component L.c in each lane, and t - ybar
+  const double tc = ps->t[L.c];
+  const double ybc =
+      fma(s, fma(st->ybar0[2], ps->R[6 + L.c], fma(st->ybar0[1], ps->R[3 + L.c], st->ybar0[0] * ps->R[L.c])), tc);
+  const double tmy = tc - ybc;
+  const double dc = dq * v[L.c];  // Eq. 5.5, unit masses, v = 0 (component c)
   // C^ = Y_D^T Y_c = s^2 R^T S0 R + kappa T   (Eq. 6 with the displaced cloud)
   const double SR = wmul(st->S0[L.q], Rq, L);
   const double Ch = fma(kappa, Tq, s * s * wmul_ta(Rq, SR, L));
@@ -546,10 +472,11 @@ __device__ void finalize_update(const double (&v)[13], DevPose* ps, const DevSta
   if (sp.scale_mode == 0) cs = sqrt(st->eX / eY);
   else if (sp.scale_mode == 1) cs = st->eX / eY;
   // Eq. 8, Eq. 9: Y(t+1) = c (Y - ybar) R_inc + ybar + d, composed into the pose
-  double acc = (tt[0] - yb[0]) * wget(Rinc, L.c);
-  acc = fma(tt[1] - yb[1], wget(Rinc, 3 + L.c), acc);
-  acc = fma(tt[2] - yb[2], wget(Rinc, 6 + L.c), acc);
-  const double tn = fma(cs, acc, yb[L.c] + dc);  // component c
+  // (lanes 0, 1, 2 hold t - ybar of components 0, 1, 2)
+  double acc = wget(tmy, 0) * wget(Rinc, L.c);
+  acc = fma(wget(tmy, 1), wget(Rinc, 3 + L.c), acc);
+  acc = fma(wget(tmy, 2), wget(Rinc, 6 + L.c), acc);
+  const double tn = fma(cs, acc, ybc + dc);  // component c
   const double RR = wmul(Rq, Rinc, L);
   double Rn;
   if (!reorth_warp(RR, L, Rn)) {
@@ -580,7 +507,7 @@ __device__ void finalize_update(const double (&v)[13], DevPose* ps, const DevSta
   if (lane < 3) {
     ps->t[lane] = tn;
     ps->b[lane] = (float)(tn - st->xbar[lane]);
-    ps->ybs[lane] = ybs;
+    set_ybs(ps, lane, ybs);
   }
   if (lane == 0) {
     ps->s = sn;
@@ -623,7 +550,7 @@ __device__ void finalize_body(const double* __restrict__ blockpart, int nblocks,
 // pose.  One launch per iteration instead of two, and no per-block partials.
 __global__ void __launch_bounds__(RED_THREADS)
     combine_finalize_kernel(const float4* __restrict__ partial, int S, int mpad, int m,
-                            const float4* __restrict__ Y0r, const double* __restrict__ aY64, int g_mode,
+                            const float4* __restrict__ Y0r, const float* __restrict__ aY32, int g_mode,
                             DevPose* ps, const DevStats* __restrict__ st, StepParams sp, int* err) {
   __shared__ double sh[13][RED_THREADS];
   float acc[13];
@@ -632,7 +559,7 @@ __global__ void __launch_bounds__(RED_THREADS)
   {
     const PointFrame fr(ps);
     for (int i = threadIdx.x; i < m; i += RED_THREADS)
-      point_force(partial, (size_t)mpad, S, i, Y0r[i], g_mode == 1 ? (float)aY64[i] : 1.f, fr, acc, nullptr);
+      point_force(partial, (size_t)mpad, S, i, Y0r[i], g_mode == 1 ? aY32[i] : 1.f, fr, acc, nullptr);
   }
   double w[16];
 #pragma unroll
@@ -659,9 +586,9 @@ __global__ void __launch_bounds__(RED_THREADS)
 }
 
 cudaError_t launch_combine_finalize(Launch L, const float4* partial, int S, int mpad, int m, const float4* Y0r,
-                                    const double* aY64, int g_mode, DevPose* pose, const DevStats* stats,
+                                    const float* aY32, int g_mode, DevPose* pose, const DevStats* stats,
                                     StepParams sp, int* err) {
-  combine_finalize_kernel<<<1, RED_THREADS, 0, L.stream>>>(partial, S, mpad, m, Y0r, aY64, g_mode, pose, stats, sp,
+  combine_finalize_kernel<<<1, RED_THREADS, 0, L.stream>>>(partial, S, mpad, m, Y0r, aY32, g_mode, pose, stats, sp,
                                                            err);
   if (L.counter) ++*L.counter;
   return cudaGetLastError();

@@ -62,7 +62,7 @@ __global__ void pose_from7_kernel(const double* __restrict__ pose7, DevPose* ps,
     ps->b[c] = (float)(ps->t[c] - st->xbar[c]);
     const double yb = ps->s * (st->ybar0[0] * ps->R[c] + st->ybar0[1] * ps->R[3 + c] +
                                st->ybar0[2] * ps->R[6 + c]) + ps->t[c];
-    ps->ybs[c] = yb - st->xbar[c];
+    set_ybs(ps, c, yb - st->xbar[c]);
   }
   ps->it = 0;
   ps->E = 1;
