@@ -382,6 +382,11 @@ SCGR_EXPORT scgr_status scgr_step_apply_dev(scgr_ctx* ctx, const double* parts_d
                                          coarse cells of 4 x 4 x 4 fine cells that skip empty ones and ones
                                          beyond the best distance so far; 1 fine shells only.  The result
                                          is the same */
+#define SCGR_TUNE_FUSED_TAIL 13      /* 1 (default): for templates of at most 2,048 padded slots one launch
+                                         per iteration combines the split partials and updates the pose
+                                         (one block); 0: the combine kernel and the finalize kernel, as for
+                                         larger templates.  The two group the float32 per-point terms
+                                         differently before the float64 sums, so poses agree to rounding */
 #define SCGR_TUNE_REUSE_POSE_FREE 6   /* 1 (default): odd integer p skips the per-iteration all-pairs pass.
                                          p = 1: the pair weights do not depend on the pose, so scgr_run
                                          computes the force sums once per call and reuses them

@@ -454,6 +454,12 @@ scgr_status scgr_set_tuning(scgr_ctx* c, int key, int value) {
     c->nearest_levels = value;
     return SCGR_OK;
   }
+  if (key == SCGR_TUNE_FUSED_TAIL) {
+    if (value != 0 && value != 1) return fail(c, SCGR_ERR_INVALID_ARG, "value must be 0 or 1");
+    c->fused_tail = value;
+    drop_graph(c);
+    return SCGR_OK;
+  }
   if (key == SCGR_TUNE_REUSE_POSE_FREE) {
     if (value != 0 && value != 1) return fail(c, SCGR_ERR_INVALID_ARG, "value must be 0 or 1");
     c->reuse_pose_free = value;

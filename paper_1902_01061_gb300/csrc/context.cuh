@@ -90,6 +90,7 @@ struct scgr_ctx {
   GridSpec rgspec{}, rcgspec{};
   bool rgrid_ok = false;
   int nearest_levels = 2;       // 2: two-level nearest search (default), 1: fine shells only (tunable)
+  int fused_tail = 1;           // 1: one combine-finalize launch for small templates (tunable)
   cudaGraph_t bgraph = nullptr;
   cudaGraphExec_t bgexec = nullptr;
 

@@ -319,7 +319,7 @@ scgr_status enqueue_iterations(scgr_ctx* c, int iters) {
       scgr_status fs = force_launch(c);
       if (fs != SCGR_OK) return fs;
     }
-    if (c->mpad <= FUSED_MAX_SLOTS) {
+    if (c->fused_tail && c->mpad <= FUSED_MAX_SLOTS) {
       // small templates: combine and finalize in one block (one launch less per iteration)
       SCGR_CK(c, launch_combine_finalize(c->L(), (const float4*)c->partial.p, c->fp.splits, (int)c->mpad, (int)c->m,
                                          (const float4*)c->Y0r.p, (const float*)c->aY32.p, c->prm.g_mode, c->pose,

@@ -43,10 +43,9 @@ struct PointFrame {
 // at stride pstride: the splits added in order with Kahan compensation, then
 // f = aY (S - Y' W) from an exact product and an exact two-sum, so f is as
 // accurate as float allows even when S and Y' W nearly cancel; W_i = aY W.
-// Adds f, W_i and f (x) (Y' - ybar') to acc[13]; optionally stores (f, W_i).
-__device__ __forceinline__ void point_force(const float4* __restrict__ pbase, size_t pstride, int S, int i,
-                                            const float4 y0, float ay, const PointFrame& fr, float (&acc)[13],
-                                            float4* __restrict__ f4out) {
+// Returns (f, W_i).
+__device__ __forceinline__ float4 point_fw(const float4* __restrict__ pbase, size_t pstride, int S, int i,
+                                           const float4 y0, float ay, const PointFrame& fr) {
   float Wh = 0.f, Wc = 0.f, Sh[3] = {0.f, 0.f, 0.f}, Sc[3] = {0.f, 0.f, 0.f};
   // splits in order, eight loads in flight per step (small templates leave
   // few threads per SM, so the pass over the splits is load-latency bound)
@@ -82,19 +81,38 @@ __device__ __forceinline__ void point_force(const float4* __restrict__ pbase, si
     const float D = __fadd_rn(dh, __fadd_rn(__fsub_rn(dl, pe), __fmaf_rn(y[a], Wc, -Sc[a])));
     f[a] = ay * D;
   }
-  const float Wi = ay * (Wh - Wc);
+  return make_float4(f[0], f[1], f[2], ay * (Wh - Wc));
+}
+
+// Adds a point's f, W_i and f (x) (Y' - ybar') to acc[13] (fw = point_fw's
+// result for the template record y0).  The additions are explicitly rounded,
+// so the compiler cannot fuse point_fw's last products into them where both
+// are inlined together: every kernel adds the same rounded per-point terms,
+// whether fw comes straight from point_fw or through shared memory.
+__device__ __forceinline__ void point_acc(const float4 fw, const float4 y0, const PointFrame& fr, float (&acc)[13]) {
+  float y[3];
+  template_point(y0, fr.A, fr.b, y[0], y[1], y[2]);
+  const float f[3] = {fw.x, fw.y, fw.z};
   float c[3];
 #pragma unroll
   for (int q = 0; q < 3; ++q) c[q] = (y[q] - fr.ch[q]) - fr.cl[q];
-  acc[0] += f[0];
-  acc[1] += f[1];
-  acc[2] += f[2];
-  acc[3] += Wi;
+  acc[0] = __fadd_rn(acc[0], f[0]);
+  acc[1] = __fadd_rn(acc[1], f[1]);
+  acc[2] = __fadd_rn(acc[2], f[2]);
+  acc[3] = __fadd_rn(acc[3], fw.w);
 #pragma unroll
   for (int a = 0; a < 3; ++a)
 #pragma unroll
     for (int bb = 0; bb < 3; ++bb) acc[4 + 3 * a + bb] = fmaf(f[a], c[bb], acc[4 + 3 * a + bb]);
-  if (f4out) f4out[i] = make_float4(f[0], f[1], f[2], Wi);
+}
+
+// point_fw then point_acc; optionally stores (f, W_i) to f4out[i].
+__device__ __forceinline__ void point_force(const float4* __restrict__ pbase, size_t pstride, int S, int i,
+                                            const float4 y0, float ay, const PointFrame& fr, float (&acc)[13],
+                                            float4* __restrict__ f4out) {
+  const float4 fw = point_fw(pbase, pstride, S, i, y0, ay, fr);
+  point_acc(fw, y0, fr, acc);
+  if (f4out) f4out[i] = fw;
 }
 
 // Reduce 16 doubles over a warp by recursive halving: lane L ends with the

@@ -543,30 +543,44 @@ __device__ void finalize_body(const double* __restrict__ blockpart, int nblocks,
 }
 
 // Combine and finalize in one block, for templates of at most
-// FUSED_MAX_SLOTS padded slots (the latency regime of small problems): each
-// thread forms the force of its slots from their split partials
-// (point_force, as the combine kernel), the 13 sums are reduced per warp
-// (float64) and across the warps in order by warp 0, and warp 0 updates the
-// pose.  One launch per iteration instead of two, and no per-block partials.
-__global__ void __launch_bounds__(RED_THREADS)
+// FUSED_MAX_SLOTS padded slots (the latency regime of small problems).
+// 1. FUSED_THREADS threads form the points' (f, W_i) from their split
+//    partials (point_fw) into shared memory: a thread's points are
+//    sequential trips to memory, so more threads than the sums below use
+//    shorten that chain.
+// 2. The first RED_THREADS threads add them up (thread t: points t,
+//    t + RED_THREADS, ... in order, through point_acc), the order a
+//    RED_THREADS-thread pass over the points would take.
+// 3. The 13 sums are reduced per warp (float64) and across the warps in
+//    order by warp 0, and warp 0 updates the pose.
+// One launch per iteration instead of two, and no per-block partials.
+constexpr int FUSED_THREADS = 512;
+
+__global__ void __launch_bounds__(FUSED_THREADS, 1)
     combine_finalize_kernel(const float4* __restrict__ partial, int S, int mpad, int m,
                             const float4* __restrict__ Y0r, const float* __restrict__ aY32, int g_mode,
                             DevPose* ps, const DevStats* __restrict__ st, StepParams sp, int* err) {
-  __shared__ double sh[13][RED_THREADS];
+  // (f, W_i) per point in steps 1-2; the float64 sums and scratch from step 3
+  __shared__ __align__(16) unsigned char smem[FUSED_MAX_SLOTS * sizeof(float4)];
+  static_assert(FUSED_MAX_SLOTS * sizeof(float4) >= sizeof(double) * 13 * RED_THREADS, "scratch too small");
+  float4* fws = reinterpret_cast<float4*>(smem);
+  double(*sh)[RED_THREADS] = reinterpret_cast<double(*)[RED_THREADS]>(smem);
+  const PointFrame fr(ps);
+  for (int i = threadIdx.x; i < m; i += FUSED_THREADS)
+    fws[i] = point_fw(partial, (size_t)mpad, S, i, Y0r[i], g_mode == 1 ? aY32[i] : 1.f, fr);
+  __syncthreads();
+  if (threadIdx.x >= RED_THREADS) return;  // all of ps read
   float acc[13];
 #pragma unroll
   for (int q = 0; q < 13; ++q) acc[q] = 0.f;
-  {
-    const PointFrame fr(ps);
-    for (int i = threadIdx.x; i < m; i += RED_THREADS)
-      point_force(partial, (size_t)mpad, S, i, Y0r[i], g_mode == 1 ? aY32[i] : 1.f, fr, acc, nullptr);
-  }
+  for (int i = threadIdx.x; i < m; i += RED_THREADS) point_acc(fws[i], Y0r[i], fr, acc);
   double w[16];
 #pragma unroll
   for (int q = 0; q < 13; ++q) w[q] = (double)acc[q];
   w[13] = w[14] = w[15] = 0.0;
   warp_reduce16(w);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __syncthreads();  // every (f, W_i) read: smem holds the float64 sums from here
   // even lanes hold quantities 0..15 after the reduction; 13..15 are padding
   // and have no row in sh
   if ((lane & 1) == 0) {
@@ -588,8 +602,8 @@ __global__ void __launch_bounds__(RED_THREADS)
 cudaError_t launch_combine_finalize(Launch L, const float4* partial, int S, int mpad, int m, const float4* Y0r,
                                     const float* aY32, int g_mode, DevPose* pose, const DevStats* stats,
                                     StepParams sp, int* err) {
-  combine_finalize_kernel<<<1, RED_THREADS, 0, L.stream>>>(partial, S, mpad, m, Y0r, aY32, g_mode, pose, stats, sp,
-                                                           err);
+  combine_finalize_kernel<<<1, FUSED_THREADS, 0, L.stream>>>(partial, S, mpad, m, Y0r, aY32, g_mode, pose, stats,
+                                                             sp, err);
   if (L.counter) ++*L.counter;
   return cudaGetLastError();
 }

@@ -46,6 +46,7 @@ SCGR_TUNE_BATCH_PERSISTENT = 10
 SCGR_TUNE_FORCE_RSQRT = 9
 SCGR_TUNE_FORCE_EX2POLY = 11
 SCGR_TUNE_NEAREST_LEVELS = 12
+SCGR_TUNE_FUSED_TAIL = 13
 
 
 class scgr_params(Structure):

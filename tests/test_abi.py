@@ -21,6 +21,20 @@ def test_header_declares_entry_points():
     assert "scgr_run" in names and "scgr_forces" in names and len(names) >= 20
 
 
+def test_binding_constants_match_the_header():
+    """Every integer SCGR_* constant of the binding has the header's value,
+    and every tuning knob the header defines is in the binding."""
+    from paper_1902_01061_gb300 import scgr
+    defined = {k: int(v) for k, v in re.findall(r"#define\s+(SCGR_\w+)\s+(-?\d+)\b", open(HEADER).read())}
+    knobs = [k for k in defined if k.startswith("SCGR_TUNE_")]
+    assert len(knobs) >= 13
+    for k in knobs:
+        assert hasattr(scgr, k), k
+    for k, v in defined.items():
+        if hasattr(scgr, k):
+            assert getattr(scgr, k) == v, k
+
+
 def test_library_exports_every_declared_symbol(scgr_lib):
     from paper_1902_01061_gb300 import scgr
     out = subprocess.run(["nm", "-D", "--defined-only", scgr.LIB_PATH], capture_output=True, text=True).stdout

@@ -412,6 +412,35 @@ def test_pose_parity_at_the_fused_tail_limit(m):
         pose_check(g.run(12), ores, synth.bbox_diag(X), what=f"pose after 12 iterations, {m}-point template")
 
 
+@pytest.mark.parametrize("which,p,g_mode", [("tiny", 2.0, 1), ("mild", 1.5, 0), ("fused_limit", 2.0, 1)])
+def test_fused_tail_matches_two_launches(which, p, g_mode):
+    """A registration whose iterations end in the one-block combine-finalize
+    launch and one through the combine and finalize kernels
+    (SCGR_TUNE_FUSED_TAIL = 0) differ only in how the float32 per-point
+    terms are grouped before the float64 sums: after 40 iterations their
+    poses and moved clouds agree to rounding."""
+    if which == "fused_limit":
+        sc = synth.scale_case()
+        X = sc.X[synth.subsample(sc.X, 2500, 41)]
+        Y0 = sc.Y0[synth.subsample(sc.Y0, 2048, 42)]
+    else:
+        case = synth.tiny() if which == "tiny" else synth.mild()
+        X, Y0 = case.X, case.Y0
+    out = []
+    for fused in (1, 0):
+        with Gpu(X, Y0, p=p, g_mode=g_mode, tune={scgr.SCGR_TUNE_FUSED_TAIL: fused}) as g:
+            R, t, s = g.run(40).as_numpy()
+            out.append((R, t, s, g.moved()))
+    (R1, t1, s1, m1), (R0, t0, s0, m0) = out
+    diag = synth.bbox_diag(X)
+    check(f"fused vs two-launch tail ({which}): max |R difference|", np.abs(R1 - R0).max(), 1e-6)
+    check(f"fused vs two-launch tail ({which}): max |t difference| / bbox diagonal", np.abs(t1 - t0).max() / diag,
+          1e-6)
+    check(f"fused vs two-launch tail ({which}): |s difference| / s", abs(s1 - s0) / s0, 1e-8)
+    check(f"fused vs two-launch tail ({which}): moved cloud, max abs difference / bbox diagonal",
+          np.abs(m1 - m0).max() / diag, 1e-5)
+
+
 def test_g_equals_s_at_full_size_and_over_iterations():
     """The g = s weighting of Sec. IV as the benchmark times it: forces of the
     1M x 1M workload at sampled rows (seeded curvatures on both sides, per-row
