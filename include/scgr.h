@@ -341,8 +341,13 @@ SCGR_EXPORT scgr_status scgr_step_apply_dev(scgr_ctx* ctx, const double* parts_d
 
 /* Tuning knobs (set by the autotuner; defaults are sensible). */
 #define SCGR_TUNE_BATCH_CHUNK_TILES 1 /* reference tiles (256 points) per batched work item, default 16 */
-#define SCGR_TUNE_KNN_GRID_MIN 2      /* clouds of at least this many points use the exact grid kNN
-                                         (default 65536; 0: always); the result is identical */
+#define SCGR_TUNE_KNN_GRID_MIN 2      /* clouds of at least this many points use the exact grid kNN in
+                                         scgr_compute_descriptors (default 20000, where the two cost the
+                                         same on GB300; 0: always); the result is identical */
+#define SCGR_TUNE_NEAREST_GRID_MIN 14 /* references of at least this many points answer scgr_nearest and
+                                         scgr_change_mask through the exact grid search (default 65536:
+                                         below it the brute force is faster, also for queries far off
+                                         the surface; 0: always); the result is identical */
 #define SCGR_TUNE_FORCE_P 3           /* force kernel template points per thread: 0 auto, 1, 2, 4 */
 #define SCGR_TUNE_FORCE_TPB 4         /* force kernel threads per block: 0 auto, 128, 256 */
 #define SCGR_TUNE_FORCE_SPLITS 5      /* force kernel reference splits: 0 auto (wave-filling), >= 1 */

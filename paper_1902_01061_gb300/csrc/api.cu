@@ -471,6 +471,11 @@ scgr_status scgr_set_tuning(scgr_ctx* c, int key, int value) {
     c->knn_grid_min = value;
     return SCGR_OK;
   }
+  if (key == SCGR_TUNE_NEAREST_GRID_MIN) {
+    if (value < 0) return fail(c, SCGR_ERR_INVALID_ARG, "grid threshold must be >= 0");
+    c->nearest_grid_min = value;
+    return SCGR_OK;
+  }
   if (key == SCGR_TUNE_BATCH_P) {
     if (value != 0 && value != 1 && value != 2 && value != 4)
       return fail(c, SCGR_ERR_INVALID_ARG, "batch points per thread must be 0 (mixed), 1, 2 or 4");

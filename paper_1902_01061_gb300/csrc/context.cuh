@@ -80,7 +80,8 @@ struct scgr_ctx {
   int batch_chunk_tiles = 16;   // reference tiles per batched work item (tunable)
   int batch_P = 1;              // template points per thread in the batched force kernel (tunable)
   int batch_persistent = 0;     // 1: persistent batched force kernel with a work queue (tunable)
-  int64_t knn_grid_min = 65536; // clouds with at least this many points use the grid kNN (tunable)
+  int64_t knn_grid_min = 20000; // clouds with at least this many points use the grid kNN (tunable)
+  int64_t nearest_grid_min = 65536; // references with at least this many points: grid nearest search (tunable)
   ForceTuning ftune;            // force-plan overrides (tunable)
   int reuse_pose_free = 1;      // p = 1: one force pass per scgr_run (tunable)
   DevBuf gcell, gcount, gstart, gcursor, gblock, gsorted, gsidx, gbb, cd_key, cd_moved, wstore, wupart, wpartial,

@@ -188,7 +188,7 @@ scgr_status knn_cloud(scgr_ctx* c, const float4* P, int n, int32_t* out) {
 }
 
 // Nearest reference point of nq external queries (float32 [nq][3] on the
-// device): brute force below knn_grid_min reference points, else the exact
+// device): brute force below nearest_grid_min reference points, else the exact
 // two-level grid search over the reference (the same result): fine cells
 // around the query, then coarse cells that skip empty space.  The
 // reference's two grids are built on the first query after
@@ -198,7 +198,7 @@ scgr_status knn_cloud(scgr_ctx* c, const float4* P, int n, int32_t* out) {
 scgr_status nearest_reference(scgr_ctx* c, const float* q3, int nq, int32_t* idx_out, float* key_out) {
   const float4* X4 = (const float4*)c->X4.p;
   const int n = (int)c->n;
-  if ((int64_t)n < c->knn_grid_min) {
+  if ((int64_t)n < c->nearest_grid_min) {
     SCGR_CK(c, launch_nearest(c->L(), X4, n, q3, nq, idx_out, key_out));
     return SCGR_OK;
   }

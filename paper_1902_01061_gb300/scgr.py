@@ -47,6 +47,7 @@ SCGR_TUNE_FORCE_RSQRT = 9
 SCGR_TUNE_FORCE_EX2POLY = 11
 SCGR_TUNE_NEAREST_LEVELS = 12
 SCGR_TUNE_FUSED_TAIL = 13
+SCGR_TUNE_NEAREST_GRID_MIN = 14
 
 
 class scgr_params(Structure):

@@ -79,7 +79,7 @@ def test_nearest_bit_exact(grid):
     far = (3.0 * Q[:100] + np.float32(2.5)).astype(np.float32)
     Q = np.concatenate([Q, far, X[:40], X[3000:3010]]).astype(np.float32)
     idx_ref, key_ref = O.nearest(Q, X)
-    tune = {scgr.SCGR_TUNE_KNN_GRID_MIN: 0} if grid else {scgr.SCGR_TUNE_KNN_GRID_MIN: 1 << 30}
+    tune = {scgr.SCGR_TUNE_NEAREST_GRID_MIN: 0 if grid else 1 << 30}
     with Gpu(X, X, tune=tune) as g:
         idx = torch.empty(len(Q), dtype=torch.int32, device="cuda")
         key = torch.empty(len(Q), dtype=torch.float32, device="cuda")
@@ -100,7 +100,7 @@ def test_nearest_grid_at_full_size():
     Qd = torch.from_numpy(Q).cuda()
     out = {}
     for name, gmin in (("grid", 65536), ("brute", 1 << 30)):
-        with Gpu(big.X, big.Y0[:64], tune={scgr.SCGR_TUNE_KNN_GRID_MIN: gmin}) as g:
+        with Gpu(big.X, big.Y0[:64], tune={scgr.SCGR_TUNE_NEAREST_GRID_MIN: gmin}) as g:
             idx = torch.empty(len(Q), dtype=torch.int32, device="cuda")
             key = torch.empty(len(Q), dtype=torch.float32, device="cuda")
             scgr.scgr_nearest(g.ctx, Qd, idx, key)
@@ -131,7 +131,7 @@ def test_nearest_two_level_search_off_surface_queries():
     Qd = torch.from_numpy(Q).cuda()
     out = {}
     for name, gmin, levels in (("two-level", 65536, 2), ("fine", 65536, 1), ("brute", 1 << 30, 2)):
-        with Gpu(big.X, big.Y0[:64], tune={scgr.SCGR_TUNE_KNN_GRID_MIN: gmin,
+        with Gpu(big.X, big.Y0[:64], tune={scgr.SCGR_TUNE_NEAREST_GRID_MIN: gmin,
                                            scgr.SCGR_TUNE_NEAREST_LEVELS: levels}) as g:
             idx = torch.empty(len(Q), dtype=torch.int32, device="cuda")
             key = torch.empty(len(Q), dtype=torch.float32, device="cuda")
@@ -157,7 +157,7 @@ def test_change_mask_at_identity_pose(grid):
     Y0[:200] += np.float32(0.2)                      # a part that moved
     thr = 0.05
     mask_ref, dist_ref = O.change_mask(Y0, X, thr)
-    with Gpu(X, Y0, tune={scgr.SCGR_TUNE_KNN_GRID_MIN: 0 if grid else 1 << 30}) as g:
+    with Gpu(X, Y0, tune={scgr.SCGR_TUNE_NEAREST_GRID_MIN: 0 if grid else 1 << 30}) as g:
         mask = torch.empty(len(Y0), dtype=torch.uint8, device="cuda")
         dist = torch.empty(len(Y0), dtype=torch.float32, device="cuda")
         scgr.scgr_change_mask(g.ctx, thr, mask, dist)
@@ -180,7 +180,7 @@ def test_nearest_two_level_search_on_degenerate_references():
                             (X[rng.choice(len(X), 200)] + rng.normal(0, 0.05, (200, 3))).astype(np.float32),
                             rng.uniform(-3, 3, (200, 3)).astype(np.float32)])
         idx_ref, key_ref = O.nearest(Q, X)
-        with Gpu(X, X, tune={scgr.SCGR_TUNE_KNN_GRID_MIN: 0}) as g:
+        with Gpu(X, X, tune={scgr.SCGR_TUNE_NEAREST_GRID_MIN: 0}) as g:
             idx = torch.empty(len(Q), dtype=torch.int32, device="cuda")
             key = torch.empty(len(Q), dtype=torch.float32, device="cuda")
             scgr.scgr_nearest(g.ctx, torch.from_numpy(Q).cuda(), idx, key)
