@@ -325,7 +325,7 @@ def oracle_runs():
         O.register_from_partials(t.X, t.Y0, prm, 100, {"aX": d["aX"], "aY": d["aY"], "sigma": d["sigma"]}, blocks,
                                  map_partials=pool.map)
         allc = time.perf_counter() - t0
-        out["config1_tiny"] = {
+        out["tiny_1k"] = {
             "workload": "1,000 x 1,000 points, p=2, k=16, 100 iterations (descriptors + iterations)",
             "s_single_thread": one, "s_all_cores": allc, "cores": cores,
             "pair_interactions_per_s_single_thread": 1000 * 1000 * 100 / one}
@@ -342,7 +342,7 @@ def oracle_runs():
     O.forces_rows(sc.Y0, sc.X, d2["aY"], d2["aX"], d2["sigma"], 2.0, 1, rows)
     it_one = (time.perf_counter() - t0) * len(sc.Y0) / len(rows)
     n2, m2 = len(sc.X), len(sc.Y0)
-    out["config2_scale"] = {
+    out["scale_35k"] = {
         "workload": f"{n2:,} x {m2:,} points, p=2, k=16, 200 iterations",
         "descriptors_s": desc_s, "s_per_iteration_all_cores": it_all, "s_per_iteration_single_thread": it_one,
         "extrapolated_s_all_cores": desc_s + 200 * it_all, "extrapolated_s_single_thread": desc_s + 200 * it_one,
