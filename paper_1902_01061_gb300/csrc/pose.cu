@@ -382,12 +382,18 @@ __device__ bool reorth_warp(double R, Lane3 L, double& out) {
   return true;
 }
 
-// Rows up to which warp 0 adds the per-block partials by itself: lane q
-// (q < 13) adds column q over the rows in order, and the totals are shared
-// by shuffles.  A warp-wide float64 instruction occupies the scheduler's
-// float64 unit for tens of cycles on GB300, so for a few rows this is far
-// cheaper than the block-wide tree (about 150 such instructions).
-constexpr int FINALIZE_WARP_ROWS = 64;
+// Column sums of the per-block partials.  A float64 instruction costs about
+// 65 cycles on GB300 whatever the number of active lanes, and dependent ones
+// do not overlap, so the sums are arranged by the length of the dependent
+// chain in one lane (lane q < 13 adds column q):
+// * up to FINALIZE_WARP_ROWS rows, warp 0 adds them alone, in order;
+// * up to FINALIZE_SPLIT_ROWS, each of the 8 warps adds every 8th row (warp
+//   w: rows w, w + 8, ...) and warp 0 adds the 8 warp sums in order, a chain
+//   of rows / 8 + 8 additions instead of rows;
+// * beyond that, each thread adds its rows and a block-wide tree follows
+//   (about 150 float64 instructions however many rows there are).
+constexpr int FINALIZE_WARP_ROWS = 16;
+constexpr int FINALIZE_SPLIT_ROWS = 512;
 
 // Warp 0 forms the update from the 13 totals v (the same in every lane of
 // warp 0; F[3], W, T[3][3]); lane (r, c) owns entry (r, c) of each 3x3.
@@ -528,6 +534,21 @@ __device__ void finalize_body(const double* __restrict__ blockpart, int nblocks,
       for (int b = 0; b < nblocks; ++b) col += blockpart[(size_t)b * 13 + lane];
 #pragma unroll
     for (int q = 0; q < 13; ++q) v[q] = __shfl_sync(WFULL, col, q);
+  } else if (nblocks <= FINALIZE_SPLIT_ROWS) {
+    constexpr int NW = RED_THREADS / 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    double col = 0.0;
+    if (lane < 13)
+      for (int b = warp; b < nblocks; b += NW) col += blockpart[(size_t)b * 13 + lane];
+    if (lane < 13) sh[lane][warp] = col;
+    __syncthreads();
+    if (threadIdx.x >= 32) return;
+    double tot = 0.0;
+    if (lane < 13)
+      for (int k = 0; k < NW; ++k) tot += sh[lane][k];
+    __syncwarp();  // every lane has read its sums: sh is scratch from here on
+#pragma unroll
+    for (int q = 0; q < 13; ++q) v[q] = __shfl_sync(WFULL, tot, q);
   } else {
 #pragma unroll
     for (int q = 0; q < 13; ++q) v[q] = 0.0;
