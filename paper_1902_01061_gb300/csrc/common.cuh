@@ -292,6 +292,8 @@ struct ForcePlan {
   int ex2poly;    // p = 2, occ 2 only: number of template points per thread (0..2) whose second packed pair
                   // update of each 4-point step evaluates 2^-e on the FP32 pipe instead of the special-function
                   // unit (a fraction ex2poly / (2 P) of the pairs)
+  int half;       // 1: each reference split is half a tile (splits = 2 ntiles; 1 point x 128 threads, problems
+                  // whose one-tile grid fills less than half a wave)
 };
 
 // Overrides of the force plan (0: automatic), set by the autotuner.

@@ -202,11 +202,14 @@ struct RunningSums {
 // one float4 partial per template point to outbase[0 .. P*TPB).  SUB record
 // tiles of TJ points are staged together (sT holds SUB*TJ points per row);
 // a stage past t1 is filled with zero-weight entries (-L = +inf).
-template <int P, int PM, int TPB, int TJ, bool KS, int SUB, int EXO = 0>
+// HALF (one tile, SUB = 1): the block takes entries [jlo, jlo + TJ / 2) of
+// its tile, half the dependent steps per thread for the smallest problems.
+template <int P, int PM, int TPB, int TJ, bool KS, int SUB, int EXO = 0, bool HALF = false>
 __device__ __forceinline__ void force_block(float (&sT)[6][TJ * SUB], float* sk, const float* __restrict__ Xr,
                                             const float* __restrict__ XA, int t0, int t1,
                                             const float4* __restrict__ Y0r, int ibase, const DevPose* ps,
-                                            float qexp, float4* __restrict__ outbase) {
+                                            float qexp, float4* __restrict__ outbase, int jlo = 0) {
+  static_assert(!HALF || SUB == 1, "half tiles stage one tile at a time");
   const int tid = threadIdx.x;
   float A[9], b[3];
 #pragma unroll
@@ -262,8 +265,9 @@ __device__ __forceinline__ void force_block(float (&sT)[6][TJ * SUB], float* sk,
     // two 4-point steps per unrolled body; one for the 4-point shape with
     // shared-memory sums (its 16 pair updates per step fill 112 registers)
     constexpr int UNR = (KS && P >= 4) ? 1 : 2;
+    constexpr int JN = HALF ? TJ / 2 : TJ * SUB;
 #pragma unroll UNR
-    for (int jq = 0; jq < TJ * SUB; jq += 4) {
+    for (int jq = HALF ? jlo : 0; jq < (HALF ? jlo : 0) + JN; jq += 4) {
       const ulonglong2 X = *reinterpret_cast<const ulonglong2*>(&sT[0][jq]);
       const ulonglong2 Yv = *reinterpret_cast<const ulonglong2*>(&sT[1][jq]);
       const ulonglong2 Z = *reinterpret_cast<const ulonglong2*>(&sT[2][jq]);
@@ -313,7 +317,8 @@ __device__ __forceinline__ void batch_item(const int4 it, const BatchPair* __res
 // chunk} of a batch of independent problems (items[], pairs[], one pose per
 // pair); tiles_per_split is then the chunk length in tiles.
 // KS, SUB: running sums in shared memory, record tiles staged SUB at a time.
-template <int P, int PM, int TPB, int TJ, int MINB, bool BATCH, bool KS = false, int SUB = 1, int EXO = 0>
+template <int P, int PM, int TPB, int TJ, int MINB, bool BATCH, bool KS = false, int SUB = 1, int EXO = 0,
+          bool HALF = false>
 __global__ void __launch_bounds__(TPB, MINB)
     force_tile_kernel(const float* __restrict__ Xr, const float* __restrict__ XA, int ntiles,
                       int tiles_per_split, const float4* __restrict__ Y0r, int mpad,
@@ -324,16 +329,23 @@ __global__ void __launch_bounds__(TPB, MINB)
   int ibase, t0, t1;
   const DevPose* ps;
   float4* outbase;
+  int jlo = 0;
   if (BATCH) {
     batch_item<P, TPB>(items[blockIdx.x], pairs, tiles_per_split, pose, partial, ibase, t0, t1, ps, outbase);
   } else {
     ibase = blockIdx.x * (TPB * P);
-    t0 = blockIdx.y * tiles_per_split;
-    t1 = min(ntiles, t0 + tiles_per_split);
+    if (HALF) {  // split y: half y % 2 of tile y / 2
+      t0 = blockIdx.y >> 1;
+      t1 = t0 + 1;
+      jlo = (blockIdx.y & 1) * (TJ / 2);
+    } else {
+      t0 = blockIdx.y * tiles_per_split;
+      t1 = min(ntiles, t0 + tiles_per_split);
+    }
     ps = pose;
     outbase = partial + (size_t)blockIdx.y * mpad + ibase;
   }
-  force_block<P, PM, TPB, TJ, KS, SUB, EXO>(sT, sK, Xr, XA, t0, t1, Y0r, ibase, ps, qexp, outbase);
+  force_block<P, PM, TPB, TJ, KS, SUB, EXO, HALF>(sT, sK, Xr, XA, t0, t1, Y0r, ibase, ps, qexp, outbase, jlo);
 }
 
 // Persistent form of the batched pass: a grid of resident blocks takes work
@@ -439,7 +451,8 @@ static double split_makespan(int64_t iblocks, int64_t splits, double d1, double 
 // splits.  At most max(16, twelve waves' worth) and 128 splits, and at least
 // two tiles per split unless that leaves the grid short of one wave (small
 // problems, where a block's sequential walk over its tiles is the launch's
-// latency): then down to one tile per split.
+// latency): then down to one tile per split, and to half a tile (fp.half)
+// where even that grid fills less than half a wave.
 ForcePlan plan_force(int64_t m, int64_t npad, double p, int num_sms, const ForceTuning& tune) {
   ForcePlan fp;
   fp.pmode = (p == 1.0) ? 1 : (p == 2.0) ? (tune.rsq == 1 ? 4 : 2) : (p == 3.0) ? 3 : 0;
@@ -502,6 +515,15 @@ ForcePlan plan_force(int64_t m, int64_t npad, double p, int num_sms, const Force
   }
   fp.tiles_per_split = (int)L;
   fp.splits = (int)up(ntiles, L);
+  // the smallest problems (1 point x 128 threads, one tile per split, the
+  // grid under half a wave): split every tile in two, halving the dependent
+  // steps of each thread
+  fp.half = 0;
+  if (tune.splits == 0 && L == 1 && fp.P == 1 && fp.tpb == 128 && fp.occ == 0 &&
+      2 * (int64_t)fp.iblocks * ntiles <= slots) {
+    fp.half = 1;
+    fp.splits = (int)(2 * ntiles);
+  }
   return fp;
 }
 
@@ -512,12 +534,12 @@ int64_t force_mpad(int64_t m, const ForcePlan& fp) {
   return (mp + 255) / 256 * 256;
 }
 
-template <int P, int PM, int TPB, int MINB, bool KS, int SUB, int EXO>
+template <int P, int PM, int TPB, int MINB, bool KS, int SUB, int EXO, bool HALF = false>
 static void launch_force_t(cudaStream_t st, const ForcePlan& fp, const float4* Xr,
                            const float2* XA, int ntiles, const float4* Y0r, int mpad,
                            const DevPose* pose, float qexp, float4* partial) {
   dim3 grid(fp.iblocks, fp.splits);
-  force_tile_kernel<P, PM, TPB, FORCE_TJ, MINB, false, KS, SUB, EXO><<<grid, TPB, 0, st>>>(
+  force_tile_kernel<P, PM, TPB, FORCE_TJ, MINB, false, KS, SUB, EXO, HALF><<<grid, TPB, 0, st>>>(
       reinterpret_cast<const float*>(Xr), reinterpret_cast<const float*>(XA), ntiles,
       fp.tiles_per_split, Y0r, mpad, pose, qexp, partial, nullptr, nullptr);
 }
@@ -567,6 +589,12 @@ struct LaunchShape {
   int operator()() const {
     // the FP32-pipe exponential exists for p = 2 (sqrt form) only
     constexpr int E = PM == 2 ? EXO : 0;
+    if constexpr (P == 1 && TPB == 128 && MINB == 2 && !KS && SUB == 1) {
+      if (fp.half) {
+        launch_force_t<P, PM, TPB, MINB, KS, SUB, E, true>(st, fp, Xr, XA, ntiles, Y0r, mpad, pose, qexp, partial);
+        return 0;
+      }
+    }
     launch_force_t<P, PM, TPB, MINB, KS, SUB, E>(st, fp, Xr, XA, ntiles, Y0r, mpad, pose, qexp, partial);
     return 0;
   }

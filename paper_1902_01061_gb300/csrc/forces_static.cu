@@ -120,6 +120,7 @@ extern "C" scgr_status scgr_forces_static(const float* x_dev, int64_t n, const f
   ForcePlan fp = plan_force(m, npad, p, num_sms);
   const int ntiles = (int)(npad / fp.tile_j);
   if (fp.splits > STATIC_MAX_SPLITS) {
+    fp.half = 0;
     const int sub = force_stage_tiles(fp);
     fp.tiles_per_split = ((ntiles + STATIC_MAX_SPLITS - 1) / STATIC_MAX_SPLITS + sub - 1) / sub * sub;
     fp.splits = (ntiles + fp.tiles_per_split - 1) / fp.tiles_per_split;

@@ -159,18 +159,18 @@ def test_p3_moment_path_matches_all_pairs_and_oracle():
     assert (na, nb) == (0, iters)        # one moments pass replaces the 25 all-pairs force launches
 
 
-def test_small_problem_splits_reference_down_to_single_tiles():
-    """A problem too small to fill one wave with four reference tiles per
-    block (the 1,000-point case: 8 template blocks, 4 tiles) splits the
-    reference range down to one tile per block, and the forces keep oracle
-    parity."""
+def test_small_problem_splits_reference_down_to_half_tiles():
+    """A problem whose one-tile-per-block grid fills less than half a wave
+    (the 1,000-point case: 8 template blocks, 4 tiles) splits every
+    reference tile in two (8 splits of 128 points), and the forces keep
+    oracle parity."""
     case = synth.tiny()
     d = O.descriptors(case.X, case.Y0, O.Params(p=2.0))
     f_ref, W_ref = O.forces(case.Y0, case.X, d["aY"], d["aX"], d["sigma"], 2.0, 1)
     with Gpu(case.X, case.Y0, p=2.0) as g:
         plan = scgr.scgr_get_plan(g.ctx)
-        assert plan["splits"] == 4 and plan["iblocks"] == 8, plan
+        assert plan["splits"] == 8 and plan["iblocks"] == 8, plan
         f4 = g.forces()
-    check("force f_i, 1000 x 1000 with one tile per split: relative L2", rel_l2(f4[:, :3], f_ref), 1e-5)
-    check_rows("force rows, 1000 x 1000 with one tile per split", f4, f_ref, W_ref, case.Y0, case.X,
+    check("force f_i, 1000 x 1000 with half a tile per split: relative L2", rel_l2(f4[:, :3], f_ref), 1e-5)
+    check_rows("force rows, 1000 x 1000 with half a tile per split", f4, f_ref, W_ref, case.Y0, case.X,
                d["aY"], d["aX"], d["sigma"], 2.0, 1)
