@@ -408,6 +408,15 @@ SCGR_EXPORT scgr_status scgr_set_tuning(scgr_ctx* ctx, int key, int value);
  * reference splits, template blocks, occupancy variant}.  STATE before
  * descriptors. */
 SCGR_EXPORT scgr_status scgr_get_plan(scgr_ctx* ctx, int out[5]);
+/* The automatic force plan for n reference and m template points at
+ * distance exponent p on a GPU with num_sms SMs where the planned kernel
+ * keeps blocks_per_sm blocks resident (host-only arithmetic, no device
+ * call; a context queries the device for blocks_per_sm).  out = {points per
+ * thread, threads per block, occupancy variant, reference splits, tiles of
+ * 256 reference points per split, template blocks, half-tile splits (0/1)}.
+ * INVALID_ARG for n, m < 1, p < 1, num_sms < 1 or blocks_per_sm < 1. */
+SCGR_EXPORT scgr_status scgr_plan_preview(int64_t n, int64_t m, double p, int num_sms, int blocks_per_sm,
+                                          int out[7]);
 
 /* Throughput microbenchmark of the units that bound the force kernel (no
  * paper counterpart; roofline evidence).  kind: 0 scalar FFMA, 1 packed

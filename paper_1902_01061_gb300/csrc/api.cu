@@ -416,6 +416,21 @@ scgr_status scgr_get_plan(scgr_ctx* c, int out[5]) {
   return SCGR_OK;
 }
 
+scgr_status scgr_plan_preview(int64_t n, int64_t m, double p, int num_sms, int blocks_per_sm, int out[7]) {
+  if (!out || n < 1 || m < 1 || !(p >= 1.0) || !std::isfinite(p) || num_sms < 1 || blocks_per_sm < 1)
+    return SCGR_ERR_INVALID_ARG;
+  const int64_t npad = (n + FORCE_TJ - 1) / FORCE_TJ * FORCE_TJ;
+  const ForcePlan fp = plan_force(m, npad, p, num_sms, ForceTuning(), blocks_per_sm);
+  out[0] = fp.P;
+  out[1] = fp.tpb;
+  out[2] = fp.occ;
+  out[3] = fp.splits;
+  out[4] = fp.tiles_per_split;
+  out[5] = fp.iblocks;
+  out[6] = fp.half;
+  return SCGR_OK;
+}
+
 scgr_status scgr_set_tuning(scgr_ctx* c, int key, int value) {
   if (!c) return SCGR_ERR_INVALID_ARG;
   c->err.clear();

@@ -307,7 +307,9 @@ struct ForceTuning {
   int ex2poly = 0; // see ForcePlan::ex2poly
 };
 
-ForcePlan plan_force(int64_t m, int64_t npad, double p, int num_sms, const ForceTuning& tune = ForceTuning());
+// blocks_per_sm > 0 replaces the device's occupancy query (host-only planning)
+ForcePlan plan_force(int64_t m, int64_t npad, double p, int num_sms, const ForceTuning& tune = ForceTuning(),
+                     int blocks_per_sm = 0);
 int64_t force_mpad(int64_t m, const ForcePlan& fp);
 // Record tiles a force block of this plan stages at a time (a split length
 // that is not a multiple of this computes a zero-weight padded tile).

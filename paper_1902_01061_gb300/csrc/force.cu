@@ -453,7 +453,7 @@ static double split_makespan(int64_t iblocks, int64_t splits, double d1, double 
 // problems, where a block's sequential walk over its tiles is the launch's
 // latency): then down to one tile per split, and to half a tile (fp.half)
 // where even that grid fills less than half a wave.
-ForcePlan plan_force(int64_t m, int64_t npad, double p, int num_sms, const ForceTuning& tune) {
+ForcePlan plan_force(int64_t m, int64_t npad, double p, int num_sms, const ForceTuning& tune, int blocks_per_sm) {
   ForcePlan fp;
   fp.pmode = (p == 1.0) ? 1 : (p == 2.0) ? (tune.rsq == 1 ? 4 : 2) : (p == 3.0) ? 3 : 0;
   fp.tile_j = FORCE_TJ;
@@ -483,7 +483,7 @@ ForcePlan plan_force(int64_t m, int64_t npad, double p, int num_sms, const Force
   const int64_t per_block = (int64_t)fp.tpb * fp.P;
   fp.iblocks = (int)((m + per_block - 1) / per_block);
   const int64_t ntiles = npad / FORCE_TJ > 0 ? npad / FORCE_TJ : 1;
-  const int64_t slots = (int64_t)num_sms * force_blocks_per_sm(fp);
+  const int64_t slots = (int64_t)num_sms * (blocks_per_sm > 0 ? blocks_per_sm : force_blocks_per_sm(fp));
   const int64_t sub = force_stage_tiles(fp);
   auto up = [](int64_t a, int64_t b) { return (a + b - 1) / b; };
   int64_t L = 0;

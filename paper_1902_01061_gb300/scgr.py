@@ -32,7 +32,7 @@ EXPORTED = (
     "scgr_potential", "scgr_batch_run", "scgr_set_tuning", "scgr_set_row_range", "scgr_step_partials",
     "scgr_step_apply", "scgr_get_plan", "scgr_microbench", "scgr_set_neighbourhood", "scgr_nearest",
     "scgr_change_mask", "scgr_force_vjp", "scgr_potential_stored", "scgr_debug_fail_allocations",
-    "scgr_step_partials_dev", "scgr_step_apply_dev",
+    "scgr_step_partials_dev", "scgr_step_apply_dev", "scgr_plan_preview",
 )
 SCGR_TUNE_BATCH_CHUNK_TILES = 1
 SCGR_TUNE_KNN_GRID_MIN = 2
@@ -377,6 +377,14 @@ def scgr_get_plan(ctx) -> dict:
     out = (c_int * 5)()
     _check(load().scgr_get_plan(ctx, out), ctx)
     return {"P": out[0], "tpb": out[1], "splits": out[2], "iblocks": out[3], "occ": out[4]}
+
+
+def scgr_plan_preview(n: int, m: int, p: float, num_sms: int, blocks_per_sm: int) -> dict:
+    out = (c_int * 7)()
+    _check(load().scgr_plan_preview(c_int64(int(n)), c_int64(int(m)), c_double(float(p)), int(num_sms),
+                                    int(blocks_per_sm), out))
+    return {"P": out[0], "tpb": out[1], "occ": out[2], "splits": out[3], "tiles_per_split": out[4],
+            "iblocks": out[5], "half": out[6]}
 
 
 def scgr_set_tuning(ctx, key: int, value: int) -> None:
